@@ -1,0 +1,662 @@
+/*
+ * Plain FP64 CPU oracle for the Link-and-Code search path and for the graph build that
+ * produces the indexes it is checked on (Douze, Sablayrolles, Jegou, "Link and code: Fast
+ * indexing with graphs and compact regression codes", CVPR 2018).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product (the C-ABI library, its kernels or its
+ * Python binding) may include, link or call this file.  It shares no code with them.  Only
+ * the tests, the package entry point's smoke check and the benchmark's CPU-baseline leg use
+ * it, through ctypes.
+ *
+ * Everything is single-threaded, in double precision, written for reading rather than
+ * speed: sets are plain arrays scanned linearly, and each step follows the paper's order.
+ *
+ *   orc_search      Section 4.1 (two-stage search) over the HNSW structure of Section 2:
+ *                   rotation, ADC tables, greedy descent of the upper levels, best-first
+ *                   search of level 0, shortlist, refinement with the regression codebook
+ *                   (Section 4.3, reconstruction beta^T G(x)), exact L2 and top-k.
+ *   orc_build_graph HNSW insertion (Section 2 and Section 5.1: added by batches, distances
+ *                   from the exact vector being inserted to the decoded indexed vectors).
+ *
+ * Ordering: every comparison is on the pair (distance, id), smaller id first on equal
+ * distances.  orc_search also records, per query, the smallest relative gap between the two
+ * distances of any comparison that decided its result: which node is expanded next (against
+ * the runner-up and against the best node left outside the result set), when the walk ends,
+ * where it moves on an upper level, the shortlist boundary and the order of the k returned.
+ * A GPU run in FP32 may legitimately decide such a comparison the other way when that gap is
+ * below its rounding error; every other comparison can change only the order inside the
+ * result set, never the nodes expanded.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_KBETA 8      /* neighbours in G(x), Section 4.2 */
+#define ORC_NBETA 256    /* regression codebook size B, Section 4.3 */
+
+/* ------------------------------------------------------------------------------------ */
+/* Sub-space split: M contiguous blocks; the first (d mod M) have ceil(d/M) dimensions.    */
+/* ------------------------------------------------------------------------------------ */
+static void split_offsets(int d, int M, int *off, int *len)
+{
+    int base = d / M, extra = d % M, o = 0;
+    for (int j = 0; j < M; j++) {
+        len[j] = base + (j < extra ? 1 : 0);
+        off[j] = o;
+        o += len[j];
+    }
+}
+
+/* Key order: (distance, id) lexicographic. */
+static int key_less(double da, int32_t ia, double db, int32_t ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+typedef struct {
+    double gap;                 /* smallest relative gap seen so far */
+    const uint8_t *codes1;      /* to recognise exact ties between identical code rows */
+    int M1;
+} gap_rec;
+
+static void note_gap(gap_rec *g, double a, int32_t ia, double b, int32_t ib, int walk)
+{
+    if (ia == ib) return;
+    if (a == b) {
+        /* Identical code rows give identical sums on any hardware; that tie is decided
+           by id on both sides.  Any other exact tie is treated as unresolved. */
+        if (walk && memcmp(g->codes1 + (int64_t)ia * g->M1, g->codes1 + (int64_t)ib * g->M1,
+                           (size_t)g->M1) == 0)
+            return;
+        g->gap = 0.0;
+        return;
+    }
+    double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+    double r = fabs(a - b) / m;
+    if (r < g->gap) g->gap = r;
+}
+
+static int cmp_note(gap_rec *g, double da, int32_t ia, double db, int32_t ib, int walk)
+{
+    note_gap(g, da, ia, db, ib, walk);
+    return key_less(da, ia, db, ib);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Search                                                                               */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    int64_t N;
+    int d, M1, M2, deg, deg_up, max_level;
+    int32_t ep;
+    const float *R, *C1, *C2, *B;
+    const uint8_t *codes1, *codes2, *beta;
+    const int32_t *adj0, *upper_off, *upper_adj;
+} orc_index;
+
+/* Walk distance by ADC (Section 4.1): the sum over level-1 sub-spaces of table entries,
+   i.e. || y' - c1(x) ||^2 with the query unquantised and the database vector coded. */
+static double adc(const orc_index *ix, const double *lut, int32_t e)
+{
+    const uint8_t *c = ix->codes1 + (int64_t)e * ix->M1;
+    double s = 0.0;
+    for (int j = 0; j < ix->M1; j++) s += lut[j * 256 + c[j]];
+    return s;
+}
+
+/* Decoded vector q(x) = c1(x) + c2(x - c1(x)) of the two-level codec (Section 3.3 / 4.1),
+   in the rotated space. */
+static void decode2(const orc_index *ix, const int *off1, const int *len1, const int *off2,
+                    const int *len2, int32_t v, double *out)
+{
+    const uint8_t *a = ix->codes1 + (int64_t)v * ix->M1;
+    const uint8_t *b = ix->codes2 + (int64_t)v * ix->M2;
+    for (int j = 0; j < ix->M1; j++)
+        for (int t = off1[j]; t < off1[j] + len1[j]; t++)
+            out[t] = (double)ix->C1[(int64_t)a[j] * ix->d + t];
+    for (int j = 0; j < ix->M2; j++)
+        for (int t = off2[j]; t < off2[j] + len2[j]; t++)
+            out[t] += (double)ix->C2[(int64_t)b[j] * ix->d + t];
+}
+
+int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1,
+               const float *C2, const uint8_t *codes1, const uint8_t *codes2,
+               const uint8_t *beta, const float *B, int deg, const int32_t *adj0, int deg_up,
+               const int32_t *upper_off, const int32_t *upper_adj, int32_t ep, int max_level,
+               int64_t nq, const float *Q, int k, int ef, int shortlist,
+               int32_t *ids, double *dists, int32_t *stats, double *min_gap,
+               int32_t *w_ids, double *w_dists, int32_t *w_size)
+{
+    orc_index ix = {N, d, M1, M2, deg, deg_up, max_level, ep, R, C1, C2, B,
+                    codes1, codes2, beta, adj0, upper_off, upper_adj};
+    int efp = ef > k ? ef : k;                               /* ef' = max(efSearch, k) */
+    int off1[256], len1[256], off2[256], len2[256];
+    if (M1 > 256 || M2 > 256 || k < 1) return -1;
+    split_offsets(d, M1, off1, len1);
+    split_offsets(d, M2, off2, len2);
+
+    double *yr = malloc(sizeof(double) * d);
+    double *lut = malloc(sizeof(double) * 256 * M1);
+    char *visited = N > 0 ? calloc((size_t)N, 1) : NULL;
+    int32_t *touched = malloc(sizeof(int32_t) * (N > 0 ? N : 1));
+    int64_t cap = (int64_t)efp * 4 + (int64_t)deg * 4 + 16;
+    double *cd = malloc(sizeof(double) * cap);               /* candidate set C */
+    int32_t *ci = malloc(sizeof(int32_t) * cap);
+    double *wd = malloc(sizeof(double) * (efp + 1));         /* result set W */
+    int32_t *wi = malloc(sizeof(int32_t) * (efp + 1));
+    double *xh = malloc(sizeof(double) * d * (ORC_KBETA + 1));
+    double *yh = malloc(sizeof(double) * d);
+    double *rd = malloc(sizeof(double) * (efp + 1));
+    int32_t *ri = malloc(sizeof(int32_t) * (efp + 1));
+
+    for (int64_t q = 0; q < nq; q++) {
+        const float *y = Q + q * d;
+        gap_rec g = {INFINITY, codes1, M1};
+        int32_t n_dist = 0, n_expand = 0, n_up = 0;
+        int wn = 0, ntouch = 0;
+
+        /* Rotation y' = R y (orthogonal, so L2 distances are unchanged). */
+        for (int t = 0; t < d; t++) {
+            double s = 0.0;
+            for (int u = 0; u < d; u++) s += (double)R[(int64_t)t * d + u] * (double)y[u];
+            yr[t] = s;
+        }
+        /* ADC tables LUT[j][c] = || y'^j - C1_j[c] ||^2, in difference form. */
+        for (int j = 0; j < M1; j++)
+            for (int c = 0; c < 256; c++) {
+                double s = 0.0;
+                for (int t = off1[j]; t < off1[j] + len1[j]; t++) {
+                    double diff = yr[t] - (double)C1[(int64_t)c * d + t];
+                    s += diff * diff;
+                }
+                lut[j * 256 + c] = s;
+            }
+
+        if (N > 0) {
+            /* Greedy descent through levels max_level..1 (Section 2). */
+            int32_t cur = ep;
+            double dcur = adc(&ix, lut, cur);
+            if (max_level >= 1) n_up++;
+            for (int l = max_level; l >= 1; l--) {
+                for (;;) {
+                    const int32_t *row = upper_adj + ((int64_t)upper_off[cur] + l - 1) * deg_up;
+                    int32_t best = -1, second = -1;
+                    double dbest = 0.0, dsecond = 0.0;
+                    for (int s = 0; s < deg_up; s++) {
+                        int32_t e = row[s];
+                        if (e < 0) continue;
+                        double de = adc(&ix, lut, e);
+                        n_up++;
+                        if (best < 0 || key_less(de, e, dbest, best)) {
+                            second = best; dsecond = dbest;
+                            best = e; dbest = de;
+                        } else if (second < 0 || key_less(de, e, dsecond, second)) {
+                            second = e; dsecond = de;
+                        }
+                    }
+                    /* deciding comparisons: the best neighbour against the runner-up,
+                       and against the current node */
+                    if (second >= 0) note_gap(&g, dbest, best, dsecond, second, 1);
+                    if (best >= 0 && cmp_note(&g, dbest, best, dcur, cur, 1)) {
+                        cur = best;
+                        dcur = dbest;
+                    } else {
+                        break;
+                    }
+                }
+            }
+
+            /* Best-first search of level 0 from the seed, result set of size ef'. */
+            int64_t cn = 0;
+            double d0 = adc(&ix, lut, cur);
+            n_dist = 1;
+            visited[cur] = 1;
+            touched[ntouch++] = cur;
+            cd[cn] = d0; ci[cn] = cur; cn++;
+            wd[0] = d0; wi[0] = cur; wn = 1;
+            /* best node scored so far that is not in W (rejected or evicted); W is always
+               the ef' best scored nodes, so this is the (ef'+1)-th best */
+            double od0 = INFINITY;
+            int32_t oid = -1;
+            int ended_by_break = 0;
+            while (cn > 0) {
+                /* c = nearest element of C; its order against the runner-up decides
+                   which element is expanded first */
+                int64_t bc = 0, b2 = -1;
+                for (int64_t s = 1; s < cn; s++) {
+                    if (key_less(cd[s], ci[s], cd[bc], ci[bc])) { b2 = bc; bc = s; }
+                    else if (b2 < 0 || key_less(cd[s], ci[s], cd[b2], ci[b2])) b2 = s;
+                }
+                if (b2 >= 0) note_gap(&g, cd[bc], ci[bc], cd[b2], ci[b2], 1);
+                double dc = cd[bc];
+                int32_t c = ci[bc];
+                cd[bc] = cd[cn - 1]; ci[bc] = ci[cn - 1]; cn--;
+                /* f = furthest element of W */
+                int bf = 0;
+                for (int s = 1; s < wn; s++)
+                    if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
+                if (key_less(wd[bf], wi[bf], dc, c)) {                 /* c further than f */
+                    note_gap(&g, wd[bf], wi[bf], dc, c, 1);
+                    ended_by_break = 1;
+                    break;
+                }
+                /* c is expanded next: decided against the runner-up in C (above) and
+                   against the best node outside W */
+                if (oid >= 0) note_gap(&g, dc, c, od0, oid, 1);
+                n_expand++;
+                const int32_t *row = adj0 + (int64_t)c * deg;
+                for (int s = 0; s < deg; s++) {
+                    int32_t e = row[s];
+                    if (e < 0 || visited[e]) continue;
+                    visited[e] = 1;
+                    touched[ntouch++] = e;
+                    double de = adc(&ix, lut, e);
+                    n_dist++;
+                    bf = 0;
+                    for (int u = 1; u < wn; u++)
+                        if (key_less(wd[bf], wi[bf], wd[u], wi[u])) bf = u;
+                    int take = wn < efp || key_less(de, e, wd[bf], wi[bf]);
+                    if (!take && key_less(de, e, od0, oid < 0 ? INT32_MAX : oid)) {
+                        od0 = de; oid = e;
+                    }
+                    if (take) {
+                        if (cn == cap) {
+                            cap *= 2;
+                            cd = realloc(cd, sizeof(double) * cap);
+                            ci = realloc(ci, sizeof(int32_t) * cap);
+                        }
+                        cd[cn] = de; ci[cn] = e; cn++;
+                        wd[wn] = de; wi[wn] = e; wn++;
+                        if (wn > efp) {                      /* evict the furthest */
+                            int s1 = 0;
+                            for (int u = 1; u < wn; u++)
+                                if (key_less(wd[s1], wi[s1], wd[u], wi[u])) s1 = u;
+                            if (key_less(wd[s1], wi[s1], od0, oid < 0 ? INT32_MAX : oid)) {
+                                od0 = wd[s1]; oid = wi[s1];
+                            }
+                            wd[s1] = wd[wn - 1]; wi[s1] = wi[wn - 1]; wn--;
+                        }
+                    }
+                }
+            }
+            /* termination: had the best node outside W ranked inside it, the walk would
+               have continued */
+            if (!ended_by_break && oid >= 0) {
+                int bf = 0;
+                for (int s = 1; s < wn; s++)
+                    if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
+                note_gap(&g, wd[bf], wi[bf], od0, oid, 1);
+            }
+            for (int s = 0; s < ntouch; s++) visited[touched[s]] = 0;
+
+            /* sort W by (distance, id) */
+            for (int a = 0; a < wn; a++) {
+                int m = a;
+                for (int b2 = a + 1; b2 < wn; b2++)
+                    if (key_less(wd[b2], wi[b2], wd[m], wi[m])) m = b2;
+                double td = wd[a]; wd[a] = wd[m]; wd[m] = td;
+                int32_t ti = wi[a]; wi[a] = wi[m]; wi[m] = ti;
+            }
+        }
+
+        if (w_size) w_size[q] = wn;
+        if (w_ids)
+            for (int s = 0; s < efp; s++) {
+                w_ids[q * efp + s] = s < wn ? wi[s] : -1;
+                w_dists[q * efp + s] = s < wn ? wd[s] : INFINITY;
+            }
+
+        int32_t *oi = ids + q * k;
+        double *od = dists + q * k;
+        for (int s = 0; s < k; s++) { oi[s] = -1; od[s] = INFINITY; }
+
+        if (shortlist < 0) {
+            /* no refinement: top-k of W by walk distance; the order of the k returned
+               and the k-th against the (k+1)-th decide the output */
+            for (int s = 0; s < k && s < wn; s++) {
+                oi[s] = wi[s]; od[s] = wd[s];
+                if (s + 1 < wn) note_gap(&g, wd[s], wi[s], wd[s + 1], wi[s + 1], 1);
+            }
+        } else {
+            /* Shortlist R = the R best of W (at most 10 refined by default, Sec. 5.1);
+               the R-th against the (R+1)-th decides its membership */
+            int Rn = shortlist > 0 ? shortlist : 10;
+            if (Rn < k) Rn = k;
+            if (Rn > wn) Rn = wn;
+            if (Rn > 0 && Rn < wn) note_gap(&g, wd[Rn - 1], wi[Rn - 1], wd[Rn], wi[Rn], 1);
+            /* Refined reconstruction y^ = sum_j beta_j q(v_j), G = [q(x), q(g1..g8)] */
+            for (int r = 0; r < Rn; r++) {
+                int32_t i = wi[r];
+                const float *bv = B + (int64_t)beta[i] * (ORC_KBETA + 1);
+                for (int t = 0; t < d; t++) yh[t] = 0.0;
+                for (int j = 0; j <= ORC_KBETA; j++) {
+                    int32_t v = j == 0 ? i : adj0[(int64_t)i * deg + (j - 1)];
+                    if (j > 0 && (j - 1 >= deg || v < 0)) continue;     /* zero column */
+                    decode2(&ix, off1, len1, off2, len2, v, xh);
+                    for (int t = 0; t < d; t++) yh[t] += (double)bv[j] * xh[t];
+                }
+                /* Exact squared L2 to the refined reconstruction */
+                double s = 0.0;
+                for (int t = 0; t < d; t++) {
+                    double diff = yr[t] - yh[t];
+                    s += diff * diff;
+                }
+                rd[r] = s;
+                ri[r] = i;
+            }
+            for (int a = 0; a < Rn; a++) {
+                int m = a;
+                for (int b2 = a + 1; b2 < Rn; b2++)
+                    if (key_less(rd[b2], ri[b2], rd[m], ri[m])) m = b2;
+                double td = rd[a]; rd[a] = rd[m]; rd[m] = td;
+                int32_t ti = ri[a]; ri[a] = ri[m]; ri[m] = ti;
+            }
+            /* the order of the k returned, and the k-th against the (k+1)-th */
+            for (int s = 0; s < k && s < Rn; s++) {
+                oi[s] = ri[s]; od[s] = rd[s];
+                if (s + 1 < Rn) note_gap(&g, rd[s], ri[s], rd[s + 1], ri[s + 1], 0);
+            }
+        }
+        if (stats) {
+            stats[q * 3 + 0] = n_dist;
+            stats[q * 3 + 1] = n_expand;
+            stats[q * 3 + 2] = n_up;
+        }
+        if (min_gap) min_gap[q] = g.gap;
+    }
+    free(yr); free(lut); free(visited); free(touched); free(cd); free(ci);
+    free(wd); free(wi); free(xh); free(yh); free(rd); free(ri);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Graph build                                                                          */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * Inputs: xr = exact vectors (rotated), xh = their two-level decodings, both [N][d];
+ * levels[i] = the level of node i.  Points are inserted in id order, in batches: a batch
+ * of size b = max(1, min(batch_max, n / batch_div)) starts when n nodes are in the graph;
+ * every point of the batch searches the graph as it stood at the start of the batch, then
+ * the links are applied in id order.  With batch_max = 1 every batch holds one point and
+ * this is plain sequential insertion.
+ *
+ * Distances: from the point being inserted, exact-to-decoded (Section 4.1: the vector to
+ * insert is not quantised, the indexed ones are); between two indexed points, decoded to
+ * decoded.  Each row is kept sorted by (decoded-to-decoded distance to its owner, id).
+ * Neighbour selection is the shrinking heuristic of HNSW (Section 2): a candidate is kept
+ * unless an already kept neighbour is closer to it than the base point is.
+ */
+typedef struct {
+    int32_t *id;   /* [rows][M] */
+    double *dist;  /* [rows][M] */
+    int32_t *cnt;  /* [rows] */
+    int M;
+} rowset;
+
+static double l2(const double *a, const double *b, int d)
+{
+    double s = 0.0;
+    for (int t = 0; t < d; t++) {
+        double x = a[t] - b[t];
+        s += x * x;
+    }
+    return s;
+}
+
+typedef struct {
+    int64_t N;
+    int d;
+    const double *xr, *xh;
+    rowset lev0, up;
+    const int32_t *upper_off;
+} orc_graph;
+
+static int32_t *row_ids(orc_graph *g, int l, int32_t v, int *cnt, int *M)
+{
+    if (l == 0) {
+        *cnt = g->lev0.cnt[v]; *M = g->lev0.M;
+        return g->lev0.id + (int64_t)v * g->lev0.M;
+    }
+    int64_t r = (int64_t)g->upper_off[v] + l - 1;
+    *cnt = g->up.cnt[r]; *M = g->up.M;
+    return g->up.id + r * g->up.M;
+}
+
+/* Best-first search of one level from `entry`, keeping the ef closest: the same layer
+   search as the query path, with exact-to-decoded distances.  Output sorted by key. */
+static int search_layer(orc_graph *g, const double *x, int32_t entry, int ef, int l,
+                        char *visited, int32_t *touched, double *cd, int32_t *ci,
+                        double *wd, int32_t *wi)
+{
+    int64_t cn = 0, nt = 0;
+    int wn = 0;
+    double d0 = l2(x, g->xh + (int64_t)entry * g->d, g->d);
+    visited[entry] = 1; touched[nt++] = entry;
+    cd[cn] = d0; ci[cn] = entry; cn++;
+    wd[0] = d0; wi[0] = entry; wn = 1;
+    while (cn > 0) {
+        int64_t bc = 0;
+        for (int64_t s = 1; s < cn; s++)
+            if (key_less(cd[s], ci[s], cd[bc], ci[bc])) bc = s;
+        double dc = cd[bc];
+        int32_t c = ci[bc];
+        cd[bc] = cd[cn - 1]; ci[bc] = ci[cn - 1]; cn--;
+        int bf = 0;
+        for (int s = 1; s < wn; s++)
+            if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
+        if (key_less(wd[bf], wi[bf], dc, c)) break;
+        int cnt, M;
+        int32_t *row = row_ids(g, l, c, &cnt, &M);
+        for (int s = 0; s < cnt; s++) {
+            int32_t e = row[s];
+            if (visited[e]) continue;
+            visited[e] = 1; touched[nt++] = e;
+            double de = l2(x, g->xh + (int64_t)e * g->d, g->d);
+            bf = 0;
+            for (int u = 1; u < wn; u++)
+                if (key_less(wd[bf], wi[bf], wd[u], wi[u])) bf = u;
+            if (wn < ef || key_less(de, e, wd[bf], wi[bf])) {
+                cd[cn] = de; ci[cn] = e; cn++;
+                wd[wn] = de; wi[wn] = e; wn++;
+                if (wn > ef) {
+                    bf = 0;
+                    for (int u = 1; u < wn; u++)
+                        if (key_less(wd[bf], wi[bf], wd[u], wi[u])) bf = u;
+                    wd[bf] = wd[wn - 1]; wi[bf] = wi[wn - 1]; wn--;
+                }
+            }
+        }
+    }
+    for (int64_t s = 0; s < nt; s++) visited[touched[s]] = 0;
+    for (int a = 0; a < wn; a++) {
+        int m = a;
+        for (int b = a + 1; b < wn; b++)
+            if (key_less(wd[b], wi[b], wd[m], wi[m])) m = b;
+        double td = wd[a]; wd[a] = wd[m]; wd[m] = td;
+        int32_t ti = wi[a]; wi[a] = wi[m]; wi[m] = ti;
+    }
+    return wn;
+}
+
+/* Shrinking heuristic: candidates (cd, ci) sorted by key w.r.t. the base point; keep e
+   unless some kept k has ||x^_e - x^_k||^2 < dist(base, e).  At most M kept. */
+static int heuristic(orc_graph *g, const double *cd, const int32_t *ci, int n, int M,
+                     int32_t *out)
+{
+    int kept = 0;
+    for (int s = 0; s < n && kept < M; s++) {
+        const double *xe = g->xh + (int64_t)ci[s] * g->d;
+        int good = 1;
+        for (int u = 0; u < kept; u++)
+            if (l2(xe, g->xh + (int64_t)out[u] * g->d, g->d) < cd[s]) { good = 0; break; }
+        if (good) out[kept++] = ci[s];
+    }
+    return kept;
+}
+
+/* Insert (id, dist) into a row kept sorted by (dist, id); on overflow, re-select the
+   row's members plus the newcomer with the heuristic. */
+static void add_link(orc_graph *g, int l, int32_t owner, int32_t x)
+{
+    rowset *rs = l == 0 ? &g->lev0 : &g->up;
+    int64_t r = l == 0 ? owner : (int64_t)g->upper_off[owner] + l - 1;
+    int32_t *id = rs->id + r * rs->M;
+    double *ds = rs->dist + r * rs->M;
+    int n = rs->cnt[r];
+    double dx = l2(g->xh + (int64_t)owner * g->d, g->xh + (int64_t)x * g->d, g->d);
+    for (int s = 0; s < n; s++) if (id[s] == x) return;
+    /* merged candidate list, sorted */
+    double cd[257];
+    int32_t ci[257];
+    int m = 0, ins = 0;
+    for (int s = 0; s < n; s++) {
+        if (!ins && key_less(dx, x, ds[s], id[s])) { cd[m] = dx; ci[m] = x; m++; ins = 1; }
+        cd[m] = ds[s]; ci[m] = id[s]; m++;
+    }
+    if (!ins) { cd[m] = dx; ci[m] = x; m++; }
+    if (m <= rs->M) {
+        for (int s = 0; s < m; s++) { id[s] = ci[s]; ds[s] = cd[s]; }
+        rs->cnt[r] = m;
+        return;
+    }
+    int32_t keep[256];
+    int kn = heuristic(g, cd, ci, m, rs->M, keep);
+    /* keep[] is in candidate order, i.e. still sorted by key */
+    int s2 = 0;
+    for (int s = 0; s < m && s2 < kn; s++)
+        if (ci[s] == keep[s2]) { id[s2] = ci[s]; ds[s2] = cd[s]; s2++; }
+    rs->cnt[r] = kn;
+}
+
+int orc_build_graph(int64_t N, int d, const double *xr, const double *xh,
+                    const int32_t *levels, int deg, int deg_up, int efc, int batch_max,
+                    int batch_div, int32_t *adj0, const int32_t *upper_off,
+                    int64_t n_upper_rows, int32_t *upper_adj, int32_t *ep_out,
+                    int32_t *maxlev_out)
+{
+    if (deg > 256 || deg_up > 256 || efc < 1) return -1;
+    orc_graph g;
+    g.N = N; g.d = d; g.xr = xr; g.xh = xh; g.upper_off = upper_off;
+    g.lev0.M = deg;
+    g.lev0.id = malloc(sizeof(int32_t) * (N > 0 ? N : 1) * deg);
+    g.lev0.dist = malloc(sizeof(double) * (N > 0 ? N : 1) * deg);
+    g.lev0.cnt = calloc((size_t)(N > 0 ? N : 1), sizeof(int32_t));
+    g.up.M = deg_up;
+    g.up.id = malloc(sizeof(int32_t) * (n_upper_rows > 0 ? n_upper_rows : 1) * deg_up);
+    g.up.dist = malloc(sizeof(double) * (n_upper_rows > 0 ? n_upper_rows : 1) * deg_up);
+    g.up.cnt = calloc((size_t)(n_upper_rows > 0 ? n_upper_rows : 1), sizeof(int32_t));
+
+    char *visited = calloc((size_t)(N > 0 ? N : 1), 1);
+    int32_t *touched = malloc(sizeof(int32_t) * (N > 0 ? N : 1));
+    int64_t cap = N + 1;   /* C never holds more than the visited nodes */
+    double *cd = malloc(sizeof(double) * cap);
+    int32_t *ci = malloc(sizeof(int32_t) * cap);
+    double *wd = malloc(sizeof(double) * (efc + 1));
+    int32_t *wi = malloc(sizeof(int32_t) * (efc + 1));
+
+    int32_t ep = -1;
+    int maxlev = -1;
+    int64_t n = 0;
+    int maxbatch = batch_max > 0 ? batch_max : 1;
+    /* per batch member: selected neighbours per level (levels are below 32) */
+    int Mx = deg > deg_up ? deg : deg_up;
+    int32_t *sel = malloc(sizeof(int32_t) * (int64_t)maxbatch * 32 * Mx);
+    int *seln = malloc(sizeof(int) * (int64_t)maxbatch * 32);
+
+    while (n < N) {
+        int64_t b = batch_div > 0 ? n / batch_div : 1;
+        if (b > batch_max) b = batch_max;
+        if (b < 1) b = 1;
+        if (n + b > N) b = N - n;
+        if (n == 0) b = 1;
+        int ml0 = maxlev;
+        int32_t ep0 = ep;
+        for (int64_t u = 0; u < b; u++) {
+            int64_t x = n + u;
+            const double *xv = xr + x * d;
+            int Lx = levels[x];
+            for (int l = 0; l < 32; l++) seln[u * 32 + l] = 0;
+            if (ep0 < 0) continue;
+            int32_t cur = ep0;
+            double dcur = l2(xv, xh + (int64_t)cur * d, d);
+            for (int l = ml0; l > Lx; l--) {
+                for (;;) {
+                    int cnt, M;
+                    int32_t *row = row_ids(&g, l, cur, &cnt, &M);
+                    int32_t best = -1;
+                    double dbest = 0.0;
+                    for (int s = 0; s < cnt; s++) {
+                        double de = l2(xv, xh + (int64_t)row[s] * d, d);
+                        if (best < 0 || key_less(de, row[s], dbest, best)) {
+                            best = row[s]; dbest = de;
+                        }
+                    }
+                    if (best >= 0 && key_less(dbest, best, dcur, cur)) { cur = best; dcur = dbest; }
+                    else break;
+                }
+            }
+            for (int l = (Lx < ml0 ? Lx : ml0); l >= 0; l--) {
+                int wn = search_layer(&g, xv, cur, efc, l, visited, touched, cd, ci, wd, wi);
+                int M = l == 0 ? deg : deg_up;
+                seln[u * 32 + l] = heuristic(&g, wd, wi, wn, M, sel + ((int64_t)u * 32 + l) * Mx);
+                cur = wi[0];
+            }
+        }
+        /* links, in id order */
+        for (int64_t u = 0; u < b; u++) {
+            int64_t x = n + u;
+            int Lx = levels[x];
+            for (int l = 0; l <= Lx && l <= ml0; l++) {
+                int32_t *sx = sel + ((int64_t)u * 32 + l) * Mx;
+                int cnt = seln[u * 32 + l];
+                /* the new node's own row, sorted by decoded-to-decoded distance */
+                rowset *rs = l == 0 ? &g.lev0 : &g.up;
+                int64_t r = l == 0 ? x : (int64_t)upper_off[x] + l - 1;
+                int m = 0;
+                for (int s = 0; s < cnt; s++) {
+                    double dv = l2(xh + x * d, xh + (int64_t)sx[s] * d, d);
+                    int p = m;
+                    while (p > 0 && key_less(dv, sx[s], rs->dist[r * rs->M + p - 1],
+                                             rs->id[r * rs->M + p - 1])) {
+                        rs->dist[r * rs->M + p] = rs->dist[r * rs->M + p - 1];
+                        rs->id[r * rs->M + p] = rs->id[r * rs->M + p - 1];
+                        p--;
+                    }
+                    rs->dist[r * rs->M + p] = dv;
+                    rs->id[r * rs->M + p] = sx[s];
+                    m++;
+                }
+                rs->cnt[r] = m;
+            }
+        }
+        for (int64_t u = 0; u < b; u++) {
+            int64_t x = n + u;
+            int Lx = levels[x];
+            for (int l = 0; l <= Lx && l <= ml0; l++) {
+                int32_t *sx = sel + ((int64_t)u * 32 + l) * Mx;
+                for (int s = 0; s < seln[u * 32 + l]; s++) add_link(&g, l, sx[s], (int32_t)x);
+            }
+        }
+        for (int64_t u = 0; u < b; u++) {
+            int64_t x = n + u;
+            if (levels[x] > maxlev) { maxlev = levels[x]; ep = (int32_t)x; }
+        }
+        n += b;
+    }
+
+    for (int64_t i = 0; i < N; i++)
+        for (int s = 0; s < deg; s++)
+            adj0[i * deg + s] = s < g.lev0.cnt[i] ? g.lev0.id[i * deg + s] : -1;
+    for (int64_t r = 0; r < n_upper_rows; r++)
+        for (int s = 0; s < deg_up; s++)
+            upper_adj[r * deg_up + s] = s < g.up.cnt[r] ? g.up.id[r * deg_up + s] : -1;
+    *ep_out = ep;
+    *maxlev_out = maxlev < 0 ? 0 : maxlev;
+
+    free(g.lev0.id); free(g.lev0.dist); free(g.lev0.cnt);
+    free(g.up.id); free(g.up.dist); free(g.up.cnt);
+    free(visited); free(touched); free(cd); free(ci); free(wd); free(wi);
+    free(sel); free(seln);
+    return 0;
+}

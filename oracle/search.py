@@ -1,0 +1,65 @@
+"""Search of the oracle (wrapper of ``orc_search`` in lc_oracle.c) and brute-force k-NN.
+
+Test infrastructure only (see the package docstring).
+
+The search follows Section 4.1's two-stage strategy over the HNSW structure of Section 2:
+the walk scores database vectors by ADC from their level-1 codes, and the shortlist of the
+best walk results is re-ranked with the refined reconstruction beta_b^T G(x) of Section 4.3
+(q = c1 + c2 being the two-level decoding).  ``shortlist`` = 0 refines max(k, 10) vectors
+(Section 5.1, "at most 10" when k <= 10), a positive value refines max(shortlist, k), and a
+negative value skips the refinement and returns the walk's own top-k.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from ._clib import lib, ptr
+
+
+def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: bool = False):
+    """Returns dict(ids [nq][k] int32, dists [nq][k] float64, stats [nq][3] int32 =
+    (n_dist, n_expand, n_dist_upper), gap [nq] = smallest relative gap of a deciding
+    comparison, and with ``return_w`` the final result set W sorted by (dist, id))."""
+    Q = np.ascontiguousarray(Q, np.float32)
+    nq = Q.shape[0]
+    efp = max(ef, k)
+    ids = np.empty((nq, k), np.int32)
+    dists = np.empty((nq, k), np.float64)
+    stats = np.empty((nq, 3), np.int32)
+    gap = np.empty(nq, np.float64)
+    w_ids = np.empty((nq, efp), np.int32) if return_w else None
+    w_d = np.empty((nq, efp), np.float64) if return_w else None
+    w_n = np.empty(nq, np.int32) if return_w else None
+    N = ix.codes1.shape[0]
+    rc = lib().orc_search(
+        N, ix.d, ix.M1, ix.M2, ptr(ix.R), ptr(ix.C1), ptr(ix.C2), ptr(ix.codes1),
+        ptr(ix.codes2), ptr(ix.beta), ptr(ix.B), ix.adj0.shape[1], ptr(ix.adj0),
+        ix.upper_adj.shape[1], ptr(ix.upper_off),
+        ptr(ix.upper_adj) if ix.upper_adj.shape[0] > 0 else None, ix.ep, ix.max_level,
+        nq, ptr(Q), k, ef, shortlist, ptr(ids), ptr(dists), ptr(stats), ptr(gap),
+        ptr(w_ids), ptr(w_d), ptr(w_n))
+    if rc != 0:
+        raise RuntimeError(f"orc_search failed ({rc})")
+    out = dict(ids=ids, dists=dists, stats=stats, gap=gap)
+    if return_w:
+        out.update(w_ids=w_ids, w_dists=w_d, w_size=w_n)
+    return out
+
+
+def knn(X: np.ndarray, Q: np.ndarray, k: int, chunk: int = 256):
+    """Exact k nearest neighbours of each query in X under squared L2, float64, by
+    exhaustive comparison (Section 2's problem statement).  Ties go to the smaller id."""
+    X = np.asarray(X, np.float64)
+    Q = np.asarray(Q, np.float64)
+    ids = np.empty((Q.shape[0], k), np.int64)
+    ds = np.empty((Q.shape[0], k))
+    for a in range(0, Q.shape[0], chunk):
+        q = Q[a:a + chunk]
+        D = np.empty((q.shape[0], X.shape[0]))
+        for b in range(0, X.shape[0], 65536):
+            diff = q[:, None, :] - X[None, b:b + 65536, :]
+            D[:, b:b + 65536] = np.einsum("qnd,qnd->qn", diff, diff)
+        order = np.lexsort((np.broadcast_to(np.arange(X.shape[0]), D.shape), D), axis=1)[:, :k]
+        ids[a:a + chunk] = order
+        ds[a:a + chunk] = np.take_along_axis(D, order, axis=1)
+    return ids, ds
