@@ -1,0 +1,177 @@
+/*
+ * lc.h - C ABI of the GB300 Link-and-Code library (liblc.so).
+ *
+ * Link and Code (Douze, Sablayrolles, Jegou, CVPR 2018) indexes vectors with a
+ * two-level product-quantisation code and an HNSW-style neighbour graph, and refines
+ * the distance estimate of short-listed candidates by regression from their graph
+ * neighbours' codes.  This library builds such an index on the host and answers k-NN
+ * queries on the GPU.
+ *
+ * Conventions (every entry point):
+ *   - Returns lc_status and never aborts.  Arguments are checked before any device work;
+ *     on error nothing is written to the caller's outputs and lc_last_error() gives a
+ *     message (per calling thread).
+ *   - The library owns the index and every device allocation it makes.  The caller owns
+ *     its own buffers; the library never frees or retains them past the call (for an
+ *     asynchronous search: past completion of the work queued on the given stream).
+ *   - Row-major arrays: [n][d] means n rows of d contiguous elements.
+ *   - Ordering of results is by (distance, id), smaller id first on equal distances.
+ *   - An index is not safe for concurrent mutation; concurrent lc_search calls on one
+ *     index from several host threads are not supported (serialise them).
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lc_index lc_index;   /* opaque; created by lc_create/lc_load, freed by lc_free */
+
+typedef enum {
+    LC_OK = 0,
+    LC_ERR_ARG = 1,       /* invalid argument (null pointer, size, parameter out of range) */
+    LC_ERR_OOM = 2,       /* host or device allocation failed */
+    LC_ERR_STATE = 3,     /* call not valid in the index's current state */
+    LC_ERR_CUDA = 4,      /* a CUDA runtime call failed (no device, launch error, ...) */
+    LC_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    LC_ERR_BUDGET = 6,    /* a request can never fit the serving memory budget */
+    LC_ERR_IO = 7,        /* file could not be read or written, or has a bad format */
+    LC_ERR_CAPACITY = 8   /* a per-query work table overflowed (search too wide) */
+} lc_status;
+
+/* Index parameters.  Section 4.1: HNSW with degree 32 at the upper levels and a size ratio
+ * of 30 between levels; Section 3.3/4.1: two-level codec, (O)PQ level 1 and a residual PQ
+ * level 2, 8 bits per sub-quantiser; Section 4.3: regression over self + k = 8 neighbours
+ * with a 256-entry codebook; Section 5: codebook trained on 250k vectors, 10 iterations. */
+typedef struct {
+    int d;                 /* vector dimension, 1..256 */
+    int M1;                /* level-1 sub-quantisers: 16, 32 or 64 (bytes per vector) */
+    int M2;                /* level-2 (residual) sub-quantisers, 1..256, M2 <= d */
+    int use_opq;           /* 1: learn an OPQ rotation for level 1; 0: identity */
+    int deg;               /* level-0 degree; must be 32 */
+    int deg_upper;         /* upper-level degree; must be 32 */
+    int level_ratio;       /* size ratio between consecutive levels (30) */
+    int ef_construction;   /* beam width of the insertion search (40) */
+    int beta_train_n;      /* vectors used to train the regression codebook (250000) */
+    int beta_iters;        /* EM iterations of the codebook training (10) */
+    int kmeans_iters;      /* Lloyd iterations of each PQ k-means (25) */
+    int opq_iters;         /* alternations of the OPQ training (10) */
+    int batch_max;         /* largest insertion batch (4096); 1 = sequential insertion */
+    int n_threads;         /* host threads for train/add; 0 = all hardware threads */
+    uint64_t seed;         /* seeds every random choice of the build */
+} lc_params;
+
+/* Fills *p with the defaults above for dimension d and code sizes M1, M2. */
+void lc_default_params(lc_params *p, int d, int M1, int M2);
+
+/* Search modes. */
+enum { LC_MODE_PLAIN = 0 };           /* exact best-first walk, one expansion at a time */
+/* Precision of the per-query ADC tables kept in shared memory. */
+enum { LC_LUT_FP32 = 0 };
+
+/* Search parameters (Section 2 search, Section 4.1 two-stage strategy). */
+typedef struct {
+    int k;           /* neighbours returned per query, 1..256 */
+    int ef;          /* efSearch: size of the result set W of the walk; ef' = max(ef, k) <= 1024 */
+    int shortlist;   /* 0: refine max(k, 10) candidates (Section 5.1 refines at most 10);
+                        > 0: refine max(shortlist, k) (at most 256); < 0: no refinement,
+                        return the walk's own top-k by ADC distance */
+    int lut_prec;    /* LC_LUT_FP32 */
+    int mode;        /* LC_MODE_PLAIN */
+    int visited_log; /* 0: automatic; 10..14: the per-query visited table in shared memory has
+                        2^visited_log entries (ids beyond half of it go to a table in global
+                        memory, 2^16 entries per query in flight; beyond half of that the
+                        query fails with LC_ERR_CAPACITY) */
+} lc_search_params;
+
+void lc_default_search_params(lc_search_params *p, int k, int ef);
+
+/* Creates an empty index.  *out receives the handle.  Errors: LC_ERR_ARG (bad params),
+ * LC_ERR_OOM. */
+lc_status lc_create(const lc_params *params, lc_index **out);
+
+/* Trains the codec on nt host vectors xt [nt][d] (float32): the OPQ rotation (if enabled)
+ * and the level-1 PQ (Section 3.3, 5.1 "systematically perform a rotation"), then the
+ * residual level-2 PQ on x' - c1(x') (Section 3.3, 4.1).  Host computation.  Errors:
+ * LC_ERR_ARG (nt < 256 or null), LC_ERR_STATE (already trained). */
+lc_status lc_train(lc_index *ix, const float *xt, int64_t nt);
+
+/* Adds n host vectors x [n][d] (float32), ids continuing from the current count.  Encodes
+ * them with the two-level codec, inserts them into the HNSW graph by batches (Section 2,
+ * 5.1; the inserted vector is compared exactly with the decoded indexed vectors, Section
+ * 4.1), trains the regression codebook on the first call (Section 4.3, EM from a k-means
+ * initialisation), and assigns each new vector the codeword minimising
+ * ||x - beta^T G(x)||^2 (Section 4.3).  Host computation.  Errors: LC_ERR_ARG,
+ * LC_ERR_STATE (not trained), LC_ERR_OOM. */
+lc_status lc_add(lc_index *ix, const float *x, int64_t n);
+
+/* k-NN search for nq queries q [nq][d] (float32): ADC walk over the nested graphs, then
+ * re-rank of the shortlist with the refined reconstruction (Section 4.1, 4.3).
+ * Outputs: ids [nq][k] (int32, -1 where fewer than k results), dists [nq][k] (float32
+ * squared L2 to the refined reconstruction, or the ADC distance when shortlist < 0; +inf
+ * with id -1), stats [nq][3] (int32: distinct nodes scored at level 0, level-0
+ * expansions, evaluations on the upper levels; may be NULL).
+ * Pointers may all be host memory or all device memory (checked with
+ * cudaPointerGetAttributes).  Device pointers: the work is queued on `stream` (a
+ * cudaStream_t, NULL = the default stream) and the call returns without waiting.  Host
+ * pointers: the call copies through the device and returns when the results are written.
+ * The index is uploaded to the current device on the first search.
+ * Errors: LC_ERR_ARG, LC_ERR_STATE (empty codec), LC_ERR_CUDA, LC_ERR_OOM,
+ * LC_ERR_CAPACITY (host pointers only: some query's visited set overflowed; device
+ * pointers report it as stats n_dist = -1 for that query). */
+lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
+                    int32_t *ids, float *dists, int32_t *stats, void *stream);
+
+/* Replaces the index's content with caller-provided host arrays (copied): rotation R
+ * [d][d] (y' = R y), level-1 and level-2 centroids C1, C2 [256][d] (full width: row c holds
+ * centroid c of every sub-space in that sub-space's coordinates), codes1 [n][M1],
+ * codes2 [n][M2], beta [n] (codeword ids), regression codebook B [256][9], level-0
+ * adjacency adj0 [n][32] (-1 padded, first 8 entries = the neighbours of G(x)), levels [n],
+ * upper_adj [sum(levels)][32] (node i with level L >= 1 owns L consecutive rows, levels 1..L,
+ * in id order), entry point ep (a node of maximal level).  Sub-space split: M blocks of
+ * contiguous dimensions, the first (d mod M) of size ceil(d/M).  The index becomes trained
+ * and searchable.  Errors: LC_ERR_ARG (shapes, ids out of range), LC_ERR_OOM. */
+lc_status lc_import(lc_index *ix, int64_t n, const float *R, const float *C1, const float *C2,
+                    const uint8_t *codes1, const uint8_t *codes2, const uint8_t *beta,
+                    const float *B, const int32_t *adj0, const int32_t *levels,
+                    const int32_t *upper_adj, int32_t ep);
+
+/* Number of indexed vectors (0 for a null handle). */
+int64_t lc_size(const lc_index *ix);
+
+/* Rows of upper adjacency (sum of node levels). */
+int64_t lc_upper_rows(const lc_index *ix);
+
+/* Copies the index arrays out to caller host buffers with the layouts of lc_import (any
+ * pointer may be NULL to skip it).  *ep receives the entry point.  Errors: LC_ERR_STATE. */
+lc_status lc_export(const lc_index *ix, float *R, float *C1, float *C2, uint8_t *codes1,
+                    uint8_t *codes2, uint8_t *beta, float *B, int32_t *adj0, int32_t *levels,
+                    int32_t *upper_adj, int32_t *ep);
+
+/* Writes the index to a file (versioned binary format) / reads one into a new handle.
+ * Errors: LC_ERR_IO, LC_ERR_STATE (save of an untrained index), LC_ERR_OOM. */
+lc_status lc_save(const lc_index *ix, const char *path);
+lc_status lc_load(const char *path, lc_index **out);
+
+/* Kernel timing: after lc_profile(ix, 1) every lc_search records CUDA events on its stream
+ * around the walk kernel and the refinement kernel; lc_profile_read waits for the last
+ * profiled search and returns the two durations in milliseconds (refine_ms = 0 without
+ * refinement).  Uploads the index if needed.  Errors: LC_ERR_STATE (nothing profiled yet),
+ * LC_ERR_CUDA. */
+lc_status lc_profile(lc_index *ix, int enable);
+lc_status lc_profile_read(lc_index *ix, float *walk_ms, float *refine_ms);
+
+/* Frees the index and its device memory (NULL is a no-op). */
+void lc_free(lc_index *ix);
+
+/* Message of the last error on this thread ("" if none).  Valid until the next call. */
+const char *lc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LC_H */

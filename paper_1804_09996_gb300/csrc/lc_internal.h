@@ -1,0 +1,67 @@
+// Internal declarations shared by the translation units of liblc.so (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lc.h"
+
+namespace lc {
+
+constexpr int KSUB = 256;     // centroids per sub-quantiser (8-bit codes)
+constexpr int KBETA = 8;      // neighbours in G(x)
+constexpr int NBETA = 256;    // regression codebook size
+constexpr int DEG = 32;       // graph degree at every level
+constexpr int MAX_LEVEL = 15; // level cap
+constexpr int MAX_EF = 1024;  // largest ef' = max(efSearch, k)
+constexpr int MAX_K = 256;
+constexpr int MAX_SHORTLIST = 256;
+
+void set_error(const char *fmt, ...);
+
+// Sub-space split: M contiguous blocks, the first (d mod M) of ceil(d/M) dimensions.
+void splits(int d, int M, std::vector<int> &off, std::vector<int> &len);
+
+// Device copy of an index (owned by lc_index, defined in lc_search.cu).
+struct DeviceIndex;
+void device_free(DeviceIndex *dv);
+
+}  // namespace lc
+
+struct lc_index {
+    lc_params p{};
+    bool trained = false;
+    bool has_codebook = false;          // regression codebook present
+    int64_t n = 0;
+    std::vector<float> R;               // [d][d], y' = R y
+    std::vector<float> C1, C2;          // [256][d] full-width centroids
+    std::vector<uint8_t> codes1, codes2, beta;
+    std::vector<float> B;               // [256][9]
+    std::vector<int32_t> adj0;          // [n][32]
+    std::vector<float> adj0_d;          // build-side: distance of each row entry to its owner
+    std::vector<int32_t> levels;        // [n]
+    std::vector<int64_t> upper_off;     // [n], first upper row of a node or -1
+    std::vector<int32_t> upper_adj;     // [rows][32]
+    std::vector<float> upper_d;         // build-side distances of upper rows
+    std::vector<float> xh;              // build-side decoded vectors q(x) [n][d] (rotated space)
+    int32_t ep = -1;
+    int max_level = -1;
+    // device copy, uploaded on the first search after a change
+    lc::DeviceIndex *dev = nullptr;
+    bool dev_dirty = true;
+};
+
+namespace lc {
+// Host build (lc_build.cpp).
+lc_status build_train(lc_index *ix, const float *xt, int64_t nt);
+lc_status build_add(lc_index *ix, const float *x, int64_t n);
+void decode_all(const lc_index *ix, std::vector<float> &xh);
+int n_threads(const lc_params &p);
+
+// Device search (lc_search.cu).
+lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
+                 int32_t *ids, float *dists, int32_t *stats, void *stream);
+lc_status profile_enable(lc_index *ix, int on);
+lc_status profile_read(lc_index *ix, float *walk_ms, float *refine_ms);
+}  // namespace lc

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of liblc.so: the entry points of include/lc.h under the same names,
+with argument marshalling only (numpy arrays for host memory, torch tensors for device
+memory).  Every step of the search runs in the library's CUDA kernels; if the library is
+not built this module raises instead of doing the work any other way.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblc.so")
+
+LC_OK, LC_ERR_ARG, LC_ERR_OOM, LC_ERR_STATE, LC_ERR_CUDA = 0, 1, 2, 3, 4
+LC_ERR_TIMEOUT, LC_ERR_BUDGET, LC_ERR_IO, LC_ERR_CAPACITY = 5, 6, 7, 8
+LC_MODE_PLAIN = 0
+LC_LUT_FP32 = 0
+
+EXPORTED = [
+    "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_search",
+    "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
+    "lc_profile_read", "lc_free", "lc_last_error",
+]
+
+
+class LcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lc status {status}: {message}")
+        self.status = status
+        self.message = message
+
+
+class lc_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in (
+        "d", "M1", "M2", "use_opq", "deg", "deg_upper", "level_ratio", "ef_construction",
+        "beta_train_n", "beta_iters", "kmeans_iters", "opq_iters", "batch_max", "n_threads")] + [
+        ("seed", ctypes.c_uint64)]
+
+
+class lc_search_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log")]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library.  Raises if it has not been built (``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() "
+                           "(the search has no other implementation)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    sig = {
+        "lc_default_params": (None, [P, I, I, I]),
+        "lc_default_search_params": (None, [P, I, I]),
+        "lc_create": (I, [P, P]),
+        "lc_train": (I, [P, P, I64]),
+        "lc_add": (I, [P, P, I64]),
+        "lc_search": (I, [P, P, I64, P, P, P, P, P]),
+        "lc_import": (I, [P, I64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int32]),
+        "lc_size": (I64, [P]),
+        "lc_upper_rows": (I64, [P]),
+        "lc_export": (I, [P, P, P, P, P, P, P, P, P, P, P, P]),
+        "lc_save": (I, [P, ctypes.c_char_p]),
+        "lc_load": (I, [ctypes.c_char_p, P]),
+        "lc_profile": (I, [P, I]),
+        "lc_profile_read": (I, [P, P, P]),
+        "lc_free": (None, [P]),
+        "lc_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def lc_last_error() -> str:
+    return lib().lc_last_error().decode()
+
+
+def _check(status: int):
+    if status != LC_OK:
+        raise LcError(status, lc_last_error())
+
+
+def _ptr(a):
+    """Address of a C-contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(a)!r}")
+
+
+def lc_default_params(d: int, M1: int, M2: int, **overrides) -> lc_params:
+    p = lc_params()
+    lib().lc_default_params(ctypes.byref(p), d, M1, M2)
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def lc_default_search_params(k: int, ef: int, **overrides) -> lc_search_params:
+    p = lc_search_params()
+    lib().lc_default_search_params(ctypes.byref(p), k, ef)
+    for key, v in overrides.items():
+        setattr(p, key, v)
+    return p
+
+
+def lc_create(params: lc_params) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().lc_create(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def lc_train(ix, xt: np.ndarray):
+    xt = np.ascontiguousarray(xt, np.float32)
+    _check(lib().lc_train(ix, _ptr(xt), xt.shape[0]))
+
+
+def lc_add(ix, x: np.ndarray):
+    x = np.ascontiguousarray(x, np.float32)
+    _check(lib().lc_add(ix, _ptr(x), x.shape[0]))
+
+
+def lc_search(ix, q, nq: int, sp: lc_search_params, ids, dists, stats=None, stream=None):
+    """q [nq][d] float32, ids [nq][k] int32, dists [nq][k] float32, stats [nq][3] int32 or
+    None: all numpy (host) or all torch CUDA tensors (device; queued on ``stream``, a
+    torch.cuda.Stream, an integer handle, or None for the current default stream)."""
+    s = stream
+    if s is not None and hasattr(s, "cuda_stream"):
+        s = s.cuda_stream
+    _check(lib().lc_search(ix, _ptr(q), nq, ctypes.byref(sp), _ptr(ids), _ptr(dists), _ptr(stats),
+                           ctypes.c_void_p(s) if s else None))
+
+
+def lc_import(ix, n, R, C1, C2, codes1, codes2, beta, B, adj0, levels, upper_adj, ep: int):
+    arrs = [np.ascontiguousarray(R, np.float32), np.ascontiguousarray(C1, np.float32),
+            np.ascontiguousarray(C2, np.float32), np.ascontiguousarray(codes1, np.uint8),
+            np.ascontiguousarray(codes2, np.uint8), np.ascontiguousarray(beta, np.uint8),
+            np.ascontiguousarray(B, np.float32), np.ascontiguousarray(adj0, np.int32),
+            np.ascontiguousarray(levels, np.int32), np.ascontiguousarray(upper_adj, np.int32)]
+    ptrs = [_ptr(a) if a.size else None for a in arrs]
+    for i in range(3):          # rotation and codebooks are never empty
+        ptrs[i] = _ptr(arrs[i])
+    ptrs[6] = _ptr(arrs[6])
+    _check(lib().lc_import(ix, n, *ptrs, ep))
+
+
+def lc_size(ix) -> int:
+    return int(lib().lc_size(ix))
+
+
+def lc_upper_rows(ix) -> int:
+    return int(lib().lc_upper_rows(ix))
+
+
+def lc_export(ix, d: int, M1: int, M2: int) -> dict:
+    n, rows = lc_size(ix), lc_upper_rows(ix)
+    out = dict(R=np.empty((d, d), np.float32), C1=np.empty((256, d), np.float32),
+               C2=np.empty((256, d), np.float32), codes1=np.empty((n, M1), np.uint8),
+               codes2=np.empty((n, M2), np.uint8), beta=np.empty(n, np.uint8),
+               B=np.empty((256, 9), np.float32), adj0=np.empty((n, 32), np.int32),
+               levels=np.empty(n, np.int32), upper_adj=np.empty((rows, 32), np.int32))
+    ep = ctypes.c_int32()
+    order = ["R", "C1", "C2", "codes1", "codes2", "beta", "B", "adj0", "levels", "upper_adj"]
+    _check(lib().lc_export(ix, *[_ptr(out[k]) if out[k].size else None for k in order], ctypes.byref(ep)))
+    out["ep"] = int(ep.value)
+    return out
+
+
+def lc_save(ix, path: str):
+    _check(lib().lc_save(ix, path.encode()))
+
+
+def lc_load(path: str) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().lc_load(path.encode(), ctypes.byref(h)))
+    return h
+
+
+def lc_profile(ix, enable: bool):
+    _check(lib().lc_profile(ix, 1 if enable else 0))
+
+
+def lc_profile_read(ix):
+    """(walk_ms, refine_ms) of the last profiled search."""
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(lib().lc_profile_read(ix, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def lc_free(ix):
+    if ix:
+        lib().lc_free(ix)

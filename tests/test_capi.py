@@ -1,0 +1,119 @@
+"""C ABI checks that need no GPU: the library loads and exports every entry point that
+include/lc.h declares; argument and state errors are reported as statuses; import, export
+and the file format round-trip; the host build (train + add) produces a well-formed index."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1804_09996_gb300 import lc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1804_09996_gb300 import build
+    build.build()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "lc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lc_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = lc.lib()
+    names = header_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(lc.EXPORTED) == names
+
+
+def test_param_validation():
+    with pytest.raises(lc.LcError) as e:
+        lc.lc_create(lc.lc_default_params(96, 24, 16))
+    assert e.value.status == lc.LC_ERR_ARG and "M1" in e.value.message
+    with pytest.raises(lc.LcError):
+        lc.lc_create(lc.lc_default_params(96, 32, 16, deg=16))
+    with pytest.raises(lc.LcError):
+        lc.lc_create(lc.lc_default_params(300, 32, 16))
+
+
+def test_state_errors_without_gpu():
+    h = lc.lc_create(lc.lc_default_params(16, 16, 8, use_opq=0))
+    try:
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_add(h, np.zeros((3, 16), np.float32))
+        assert e.value.status == lc.LC_ERR_STATE
+        q = np.zeros((1, 16), np.float32)
+        ids = np.zeros((1, 1), np.int32)
+        ds = np.zeros((1, 1), np.float32)
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_search(h, q, 1, lc.lc_default_search_params(1, 8), ids, ds)
+        assert e.value.status == lc.LC_ERR_STATE
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_search(h, q, 1, lc.lc_default_search_params(0, 8), ids, ds)
+        assert e.value.status == lc.LC_ERR_ARG
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_search(h, q, 1, lc.lc_default_search_params(4, 2000), ids, ds)
+        assert e.value.status == lc.LC_ERR_ARG
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_train(h, np.zeros((10, 16), np.float32))
+        assert e.value.status == lc.LC_ERR_ARG
+    finally:
+        lc.lc_free(h)
+
+
+def _import(ix):
+    h = lc.lc_create(lc.lc_default_params(ix.d, ix.M1, ix.M2))
+    lc.lc_import(h, ix.N, ix.R, ix.C1, ix.C2, ix.codes1, ix.codes2, ix.beta, ix.B, ix.adj0,
+                 ix.levels, ix.upper_adj, ix.ep)
+    return h
+
+
+def test_import_export_and_file_roundtrip(mix3k, tmp_path):
+    ix, _, _ = mix3k
+    h = _import(ix)
+    try:
+        ex = lc.lc_export(h, ix.d, ix.M1, ix.M2)
+        for k in ("R", "C1", "C2", "codes1", "codes2", "beta", "B", "adj0", "levels", "upper_adj"):
+            assert np.array_equal(ex[k], getattr(ix, k)), k
+        assert ex["ep"] == ix.ep
+        path = str(tmp_path / "ix.lc")
+        lc.lc_save(h, path)
+        h2 = lc.lc_load(path)
+        try:
+            ex2 = lc.lc_export(h2, ix.d, ix.M1, ix.M2)
+            for k in ex:
+                assert np.array_equal(np.asarray(ex[k]), np.asarray(ex2[k])), k
+        finally:
+            lc.lc_free(h2)
+    finally:
+        lc.lc_free(h)
+    bad = tmp_path / "bad.lc"
+    bad.write_bytes(b"not an index")
+    with pytest.raises(lc.LcError) as e:
+        lc.lc_load(str(bad))
+    assert e.value.status == lc.LC_ERR_IO
+
+
+def test_import_rejects_bad_graphs(mix3k):
+    ix, _, _ = mix3k
+    h = lc.lc_create(lc.lc_default_params(ix.d, ix.M1, ix.M2))
+    try:
+        adj = ix.adj0.copy()
+        adj[5, 0] = ix.N + 3
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_import(h, ix.N, ix.R, ix.C1, ix.C2, ix.codes1, ix.codes2, ix.beta, ix.B, adj,
+                         ix.levels, ix.upper_adj, ix.ep)
+        assert e.value.status == lc.LC_ERR_ARG
+        ep_bad = int(np.flatnonzero(ix.levels == 0)[0])
+        with pytest.raises(lc.LcError):
+            lc.lc_import(h, ix.N, ix.R, ix.C1, ix.C2, ix.codes1, ix.codes2, ix.beta, ix.B, ix.adj0,
+                         ix.levels, ix.upper_adj, ep_bad)
+    finally:
+        lc.lc_free(h)

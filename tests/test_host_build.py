@@ -1,0 +1,111 @@
+"""The library's host build (lc_train / lc_add) checked on the CPU against the oracle and
+against properties the paper fixes: PQ codes are the brute-force argmin under the
+library's own codebooks, the OPQ rotation is orthogonal, the graph has HNSW's structure,
+codeword 0 is e0 and every vector's codeword minimises its refinement loss, and searching
+the library-built index (with the oracle) finds neighbours as well as the oracle's own
+build does."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import codec, refine
+from oracle.graph import upper_offsets
+from oracle.index import OracleIndex
+from paper_1804_09996_gb300 import datagen as dg
+from paper_1804_09996_gb300 import lc
+from test_oracle_graph import check_structure
+
+
+@pytest.fixture(scope="module")
+def libbuilt():
+    from paper_1804_09996_gb300 import build
+    build.build()
+    d, M1, M2 = 96, 32, 31
+    xt = dg.gaussian_mixture(6000, d, 256, stream=dg.STREAM_TRAIN)
+    xb = dg.gaussian_mixture(4000, d, 256, stream=dg.STREAM_BASE)
+    xq = dg.gaussian_mixture(300, d, 256, stream=dg.STREAM_QUERY)
+    h = lc.lc_create(lc.lc_default_params(d, M1, M2, use_opq=1, opq_iters=4, kmeans_iters=10,
+                                          batch_max=256))
+    lc.lc_train(h, xt)
+    lc.lc_add(h, xb)
+    ex = lc.lc_export(h, d, M1, M2)
+    lc.lc_free(h)
+    off, _ = upper_offsets(ex["levels"])
+    ix = OracleIndex(d=d, M1=M1, M2=M2, R=ex["R"], C1=ex["C1"], C2=ex["C2"], codes1=ex["codes1"],
+                     codes2=ex["codes2"], beta=ex["beta"], B=ex["B"], adj0=ex["adj0"], upper_off=off,
+                     upper_adj=ex["upper_adj"], ep=ex["ep"], max_level=int(ex["levels"].max()),
+                     levels=ex["levels"])
+    xr = xb.astype(np.float64) @ ix.R.astype(np.float64).T
+    ix.extra.update(xr=xr, xh=ix.decoded())
+    return ix, xt, xb, xq
+
+
+def test_rotation_orthogonal(libbuilt):
+    ix = libbuilt[0]
+    R = ix.R.astype(np.float64)
+    assert np.abs(R @ R.T - np.eye(ix.d)).max() < 1e-5
+
+
+def test_codes_are_argmin_under_library_codebooks(libbuilt):
+    ix, _, xb, _ = libbuilt
+    xr = ix.extra["xr"][:500]
+    c1 = codec.pq_encode(xr, ix.C1.astype(np.float64), ix.M1)
+    agree1 = (c1 == ix.codes1[:500]).mean()
+    res = xr - codec.pq_decode(ix.codes1[:500], ix.C1.astype(np.float64), ix.M1)
+    c2 = codec.pq_encode(res, ix.C2.astype(np.float64), ix.M2)
+    agree2 = (c2 == ix.codes2[:500]).mean()
+    # FP32 (library) vs FP64 (oracle) argmin may only differ on near-ties
+    assert agree1 > 0.999 and agree2 > 0.999, (agree1, agree2)
+
+
+def test_graph_structure(libbuilt):
+    check_structure(libbuilt[0])
+
+
+def test_codewords_minimise_refinement_loss(libbuilt):
+    ix = libbuilt[0]
+    assert np.array_equal(ix.B[0], refine.e0().astype(np.float32))
+    xh, xr = ix.extra["xh"], ix.extra["xr"]
+    idx = np.arange(800)
+    G = refine.gmatrix(xh, ix.adj0, idx)
+    best = refine.assign_codewords(G, xr[idx], ix.B.astype(np.float64))
+    L = refine.losses(G, xr[idx], ix.B.astype(np.float64))
+    got = L[np.arange(len(idx)), ix.beta[idx].astype(np.int64)]
+    # the library's choice is the oracle's argmin, or ties with it to rounding
+    assert np.all(got <= L[np.arange(len(idx)), best] * (1 + 1e-5) + 1e-9)
+    assert (best == ix.beta[idx]).mean() > 0.98
+    base = ((xr - xh) ** 2).sum(1)
+    refined = refine.losses_assigned(refine.gmatrix(xh, ix.adj0, np.arange(ix.N)), xr, ix.B.astype(np.float64),
+                                     ix.beta.astype(np.int64))
+    assert np.all(refined <= base * (1 + 1e-5) + 1e-9)
+
+
+def test_library_index_searches_as_well_as_oracle_build(libbuilt):
+    ix, xt, xb, xq = libbuilt
+    gt, _ = oracle.knn(xb, xq, 1)
+    r_lib = oracle.search(ix, xq, k=10, ef=64)
+    oix = oracle.build_index(xt, xb, 32, 31, True, opq_outer=4, codec_niter=10, batch_max=256)
+    r_orc = oracle.search(oix, xq, k=10, ef=64)
+    rl = (r_lib["ids"][:, 0] == gt[:, 0]).mean()
+    ro = (r_orc["ids"][:, 0] == gt[:, 0]).mean()
+    assert rl > 0.6 and abs(rl - ro) < 0.08, (rl, ro)
+
+
+def test_add_in_two_calls_keeps_ids_and_structure():
+    d = 32
+    xt = dg.gaussian_mixture(2000, d, 32, stream=dg.STREAM_TRAIN)
+    xb = dg.gaussian_mixture(1500, d, 32, stream=dg.STREAM_BASE)
+    h = lc.lc_create(lc.lc_default_params(d, 16, 8, use_opq=0, kmeans_iters=5))
+    try:
+        lc.lc_train(h, xt)
+        lc.lc_add(h, xb[:700])
+        lc.lc_add(h, xb[700:])
+        assert lc.lc_size(h) == 1500
+        ex = lc.lc_export(h, d, 16, 8)
+        ref = codec.pq_encode(xb.astype(np.float64), ex["C1"].astype(np.float64), 16)
+        assert (ref == ex["codes1"]).mean() > 0.999
+        adj = ex["adj0"]
+        assert ((adj >= -1) & (adj < 1500)).all()
+        assert (adj[700:] >= 0).sum(1).min() >= 1
+    finally:
+        lc.lc_free(h)

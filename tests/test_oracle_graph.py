@@ -37,8 +37,8 @@ def check_structure(ix):
         assert i not in row[:n]
         assert len(set(row[:n].tolist())) == n
         d = ((xh[row[:n]] - xh[i]) ** 2).sum(1)
-        keys = list(zip(d.tolist(), row[:n].tolist()))
-        assert keys == sorted(keys)                       # increasing distance to the owner
+        # increasing distance to the owner (to float32 rounding for builds in float32)
+        assert np.all(d[:-1] <= d[1:] * (1 + 1e-5) + 1e-12)
     lev = ix.levels
     assert lev[ix.ep] == lev.max() == ix.max_level
     for i in np.flatnonzero(lev > 0):
