@@ -1,0 +1,382 @@
+"""Benchmark: QPS at fixed 1-recall@1 of the Link-and-Code search on one GB300.
+
+Workload (default): 1,000,000 database vectors, d = 96, drawn from a mixture of 1,024
+Gaussians and L2-normalised (a stand-in for Deep1B descriptors, which are not available
+here); OPQ32 level-1 codes + residual PQ31 + 1-byte regression codeword = 64 B/vector;
+degree-32 graph; 10,000 queries per step, k = 10, efSearch = 64, plain mode (FP32 tables).
+The index is built by the library's host build (lc_train + lc_add) before timing.
+
+A step = one lc_search of the 10k queries with inputs already resident on the GPU (walk
+kernel + refinement kernel).  L2 is flushed (256 MB write) before every step, outside the
+timed span; each step is timed with CUDA events on the search's stream.  ``e2e`` repeats the
+measurement through the same C ABI call with pinned host buffers (query upload and result
+download inside the timed region).  ``roofline`` reports the walk kernel's algorithmic
+bytes (adjacency rows of expanded nodes + level-1 code rows of scored nodes, from the
+kernel's own counters) over its event-timed duration.  ``cpu_baseline`` is the FP64 oracle
+on one host core on a bounded sample of the same queries.
+
+--impl reference times the oracle itself (the slow restatement of the paper the GPU path
+is checked against) on the same workload, a bounded query sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            js = json.load(open(path))
+            flat = {}
+
+            def walk(o, pre=""):
+                if isinstance(o, dict):
+                    for k, v in o.items():
+                        walk(v, f"{pre}{k}.")
+                else:
+                    flat[pre[:-1]] = o
+            walk(js)
+            for k, v in flat.items():
+                if "hbm" in k.lower() and isinstance(v, (int, float)):
+                    return float(v), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    src = os.path.join(ROOT, "paper_1804_09996_gb300", "csrc", "lc_search.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per walk launch from the committed ncu summary, if it was taken on the
+    current kernel source (its 'kernel_source_sha256_16' line must match)."""
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        txt = open(f).read()
+        m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+        w = re.search(r"workload:\s*(\S+)", txt)
+        t = re.search(r"dram_bytes_per_walk_launch:\s*([0-9.eE+]+)", txt)
+        if m and w and t and w.group(1) == workload and m.group(1) == kernel_hash():
+            return float(t.group(1))
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, dev: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:7]))
+                except ValueError:
+                    pass
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+WORKLOADS = {
+    "mix1m": dict(n_base=1_000_000, n_train=100_000, n_query=10_000, d=96, centres=1024, M1=32, M2=31,
+                  opq=1, desc="1M x 96-d Gaussian-mixture (1024 centres), OPQ32 + residual PQ31 + 1 B codeword "
+                              "= 64 B/vector, degree 32, 10k queries/step"),
+    "mix10k": dict(n_base=10_000, n_train=10_000, n_query=1_000, d=96, centres=64, M1=16, M2=16, opq=0,
+                   desc="10k x 96-d Gaussian-mixture (64 centres), PQ16 + residual PQ16 + 1 B codeword, "
+                        "degree 32, 1k queries/step"),
+}
+
+
+def make_data(w):
+    from paper_1804_09996_gb300 import datagen as dg
+    xt = dg.gaussian_mixture(w["n_train"], w["d"], w["centres"], stream=dg.STREAM_TRAIN)
+    xb = dg.gaussian_mixture(w["n_base"], w["d"], w["centres"], stream=dg.STREAM_BASE)
+    xq = dg.gaussian_mixture(w["n_query"], w["d"], w["centres"], stream=dg.STREAM_QUERY)
+    return xt, xb, xq
+
+
+def build_index(w, xt, xb):
+    from paper_1804_09996_gb300 import lc
+    p = lc.lc_default_params(w["d"], w["M1"], w["M2"], use_opq=w["opq"])
+    h = lc.lc_create(p)
+    t0 = time.time()
+    lc.lc_train(h, xt)
+    t1 = time.time()
+    lc.lc_add(h, xb)
+    t2 = time.time()
+    log(f"index: train {t1 - t0:.1f} s, add {t2 - t1:.1f} s")
+    return h, t2 - t0
+
+
+def exact_nn(xb, xq, device):
+    """Exact nearest neighbour of each query: FP32 distances on the GPU to pick 16
+    candidates, then an FP64 recheck on the host (measurement only)."""
+    import torch
+    X = torch.from_numpy(xb).to(device)
+    xx = (X * X).sum(1)
+    out = np.empty(len(xq), np.int64)
+    for a in range(0, len(xq), 1024):
+        Q = torch.from_numpy(xq[a:a + 1024]).to(device)
+        D = xx[None, :] - 2.0 * (Q @ X.T)
+        cand = torch.topk(D, 16, dim=1, largest=False).indices.cpu().numpy()
+        q64 = xq[a:a + 1024].astype(np.float64)
+        for i in range(len(cand)):
+            c = np.sort(cand[i])
+            dd = ((xb[c].astype(np.float64) - q64[i]) ** 2).sum(1)
+            out[a + i] = c[np.lexsort((c, dd))[0]]
+    return out
+
+
+def oracle_view(h, w):
+    from oracle.graph import upper_offsets
+    from oracle.index import OracleIndex
+    from paper_1804_09996_gb300 import lc
+    ex = lc.lc_export(h, w["d"], w["M1"], w["M2"])
+    off, _ = upper_offsets(ex["levels"])
+    return OracleIndex(d=w["d"], M1=w["M1"], M2=w["M2"], R=ex["R"], C1=ex["C1"], C2=ex["C2"],
+                       codes1=ex["codes1"], codes2=ex["codes2"], beta=ex["beta"], B=ex["B"],
+                       adj0=ex["adj0"], upper_off=off, upper_adj=ex["upper_adj"], ep=ex["ep"],
+                       max_level=int(ex["levels"].max()), levels=ex["levels"])
+
+
+def time_oracle(oix, xq, k, ef, budget_s):
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    while done < len(xq) and time.perf_counter() - t0 < budget_s:
+        oracle.search(oix, xq[done:done + 50], k, ef)
+        done += min(50, len(xq) - done)
+    return done, time.perf_counter() - t0
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, w, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1804_09996_gb300 import lc
+    oracle.build()
+    xt, xb, xq = make_data(w)
+    h, _ = build_index(w, xt, xb)
+    oix = oracle_view(h, w)
+    lc.lc_free(h)
+    sample = 200 if w["n_base"] >= 100_000 else len(xq)
+    for s in range(args.warmup):
+        oracle.search(oix, xq[:20], args.k, args.ef)
+    times = []
+    for s in range(args.steps):
+        q = xq[(s * sample) % len(xq):(s * sample) % len(xq) + sample]
+        t0 = time.perf_counter()
+        oracle.search(oix, q, args.k, args.ef)
+        times.append(time.perf_counter() - t0)
+    qps = sample * args.steps / sum(times)
+    line = {
+        "impl": "reference", "metric": "QPS at fixed 1-recall@1", "value": qps, "unit": "queries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "k": args.k, "efSearch": args.ef,
+                   "queries_per_step": sample},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} queries per step of the {len(xq)}-query set, 1 thread, FP64"},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="mix1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--ef", type=int, default=64)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, w, ws, rank)
+        return
+
+    import torch
+
+    from paper_1804_09996_gb300 import build as lcbuild
+    from paper_1804_09996_gb300 import lc
+    lcbuild.build()
+    dev = local
+    torch.cuda.set_device(dev)
+    xt, xb, xq = make_data(w)
+    h, build_s = build_index(w, xt, xb)
+    gt = exact_nn(xb, xq, f"cuda:{dev}")
+    nq, k, d = len(xq), args.k, w["d"]
+    sp = lc.lc_default_search_params(k, args.ef)
+    q = torch.from_numpy(xq).cuda()
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    stats = torch.empty((nq, 3), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    lc.lc_profile(h, True)
+    for _ in range(max(3, args.warmup)):
+        lc.lc_search(h, q, nq, sp, ids, dists, stats, stream)
+    stream.synchronize()
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    walk_ms, refine_ms = [], []
+    clocks = Clocks(dev)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev0[s].record(stream)
+        lc.lc_search(h, q, nq, sp, ids, dists, stats, stream)
+        ev1[s].record(stream)
+        wm, rm = lc.lc_profile_read(h)
+        walk_ms.append(wm)
+        refine_ms.append(rm)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms = max_over_ranks(float(np.mean(step_ms)), ws)
+    value = nq * ws / (ms / 1e3)
+
+    got = ids.cpu().numpy()
+    st = stats.cpu().numpy().astype(np.int64)
+    recall1 = float((got[:, 0] == gt).mean())
+    # walk kernel: algorithmic bytes per launch, from its own counters
+    M1 = w["M1"]
+    R = max(10, k)
+    b_walk = int((st[:, 1] * 128 + (st[:, 0] + st[:, 2]) * M1).sum() + nq * (4 * d + 4 * d + 4 * R))
+    walk_s = float(np.mean(walk_ms)) / 1e3
+    peak, peak_src = peaks()
+    achieved = b_walk / walk_s / 1e9
+    traffic = profiled_traffic(args.workload)
+
+    # e2e through the same C ABI call with pinned host buffers
+    hq = torch.from_numpy(xq).pin_memory()
+    hi = torch.empty((nq, k), dtype=torch.int32).pin_memory()
+    hd = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    lc.lc_profile(h, False)
+    lc.lc_search(h, hq.numpy(), nq, sp, hi.numpy(), hd.numpy())
+    e2e_t = []
+    for s in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lc.lc_search(h, hq.numpy(), nq, sp, hi.numpy(), hd.numpy())
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = nq / float(np.mean(e2e_t))
+
+    cpu = None
+    if rank == 0 and ws == 1:
+        import oracle
+        oracle.build()
+        oix = oracle_view(h, w)
+        n_done, el = time_oracle(oix, xq, k, args.ef, args.cpu_budget)
+        cpu = {"value": n_done / el, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n_done} of the {nq} queries, k={k}, efSearch={args.ef}, 1 thread, FP64"}
+    lc.lc_free(h)
+    if rank != 0:
+        return
+    line = {
+        "metric": "QPS at fixed 1-recall@1", "value": value, "unit": "queries/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "k": k, "efSearch": args.ef,
+                   "mode": "plain", "recall_at_1": recall1, "queries_per_step": nq,
+                   "l2": "flushed before every step (256 MB write, outside the timed span)",
+                   "index_build_s": round(build_s, 1), "parallelism": f"replicas x{ws}",
+                   "walk_ms": float(np.mean(walk_ms)), "refine_ms": float(np.mean(refine_ms)),
+                   "wall_s_timed_loop": wall},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "walk_kernel",
+                     "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": b_walk},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
+                "d2h_bytes_per_step": nq * k * 8},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

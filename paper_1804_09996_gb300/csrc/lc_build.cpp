@@ -148,23 +148,38 @@ static void kmeans(const T *X, int64_t n, int64_t stride, int dim, int K, int it
     }
     std::vector<int32_t> as(n);
     std::vector<double> dm(n);
+    std::vector<T> CT((size_t)dim * K), cn(K);
     for (int it = 0; it < iters; it++) {
-        parallel_for(n, nt, 4096, [&](int64_t a, int64_t b, int) {
+        // assignment by ||c||^2 - 2 x.c over centres laid out [dim][K] (vectorises over c);
+        // the exact distance of the chosen centre is recomputed for the empty-cluster rule
+        for (int c = 0; c < K; c++) {
+            T s = 0;
+            for (int t = 0; t < dim; t++) {
+                CT[(size_t)t * K + c] = C[(int64_t)c * dim + t];
+                s += C[(int64_t)c * dim + t] * C[(int64_t)c * dim + t];
+            }
+            cn[c] = s;
+        }
+        parallel_for(n, nt, 2048, [&](int64_t a, int64_t b, int) {
+            std::vector<T> acc(K);
             for (int64_t i = a; i < b; i++) {
                 const T *x = X + i * stride;
-                int best = 0;
-                double bd = INFINITY;
-                for (int c = 0; c < K; c++) {
-                    const T *cc = C + (int64_t)c * dim;
-                    double s = 0;
-                    for (int t = 0; t < dim; t++) {
-                        double df = (double)x[t] - (double)cc[t];
-                        s += df * df;
-                    }
-                    if (s < bd) { bd = s; best = c; }
+                for (int c = 0; c < K; c++) acc[c] = cn[c];
+                for (int t = 0; t < dim; t++) {
+                    T m2x = (T)-2 * x[t];
+                    const T *ct = CT.data() + (size_t)t * K;
+                    for (int c = 0; c < K; c++) acc[c] += m2x * ct[c];
                 }
+                int best = 0;
+                for (int c = 1; c < K; c++)
+                    if (acc[c] < acc[best]) best = c;
                 as[i] = best;
-                dm[i] = bd;
+                double s = 0;
+                for (int t = 0; t < dim; t++) {
+                    double df = (double)x[t] - (double)C[(int64_t)best * dim + t];
+                    s += df * df;
+                }
+                dm[i] = s;
             }
         });
         std::vector<double> sums((size_t)K * dim, 0.0);
@@ -194,12 +209,23 @@ static void kmeans(const T *X, int64_t n, int64_t stride, int dim, int K, int it
     }
 }
 
-static void pq_train(const float *X, int64_t n, int d, int M, int iters, uint64_t seed,
+static void pq_train(const float *Xall, int64_t nall, int d, int M, int iters, uint64_t seed,
                      float *C, bool have_init, int nt)
 {
     std::vector<int> off, len;
     splits(d, M, off, len);
+    // at most 256 training points per centroid (a seeded subset)
+    const int64_t cap = (int64_t)KSUB * 256;
     std::vector<float> sub;
+    const float *X = Xall;
+    int64_t n = nall;
+    if (nall > cap) {
+        auto pick = sample(nall, cap, seed ^ 0x5bd1e995ULL);
+        sub.resize((size_t)cap * d);
+        for (int64_t i = 0; i < cap; i++) std::memcpy(sub.data() + i * d, Xall + pick[i] * d, sizeof(float) * d);
+        X = sub.data();
+        n = cap;
+    }
     for (int j = 0; j < M; j++) {
         int o = off[j], l = len[j];
         std::vector<float> Cj((size_t)KSUB * l);
@@ -218,21 +244,32 @@ static void pq_encode(const float *X, int64_t n, int d, int M, const float *C, u
 {
     std::vector<int> off, len;
     splits(d, M, off, len);
+    // per sub-space: centroids transposed [len][256] and their squared norms
+    std::vector<std::vector<float>> CT(M), cn(M);
+    for (int j = 0; j < M; j++) {
+        CT[j].resize((size_t)len[j] * KSUB);
+        cn[j].assign(KSUB, 0.f);
+        for (int c = 0; c < KSUB; c++)
+            for (int t = 0; t < len[j]; t++) {
+                float v = C[(int64_t)c * d + off[j] + t];
+                CT[j][(size_t)t * KSUB + c] = v;
+                cn[j][c] += v * v;
+            }
+    }
     parallel_for(n, nt, 2048, [&](int64_t a, int64_t b, int) {
+        float acc[KSUB];
         for (int64_t i = a; i < b; i++) {
             const float *x = X + i * d;
             for (int j = 0; j < M; j++) {
-                int best = 0;
-                float bd = INFINITY;
-                for (int c = 0; c < KSUB; c++) {
-                    const float *cc = C + (int64_t)c * d + off[j];
-                    float s = 0;
-                    for (int t = 0; t < len[j]; t++) {
-                        float df = x[off[j] + t] - cc[t];
-                        s += df * df;
-                    }
-                    if (s < bd) { bd = s; best = c; }
+                for (int c = 0; c < KSUB; c++) acc[c] = cn[j][c];
+                for (int t = 0; t < len[j]; t++) {
+                    float m2x = -2.f * x[off[j] + t];
+                    const float *ct = CT[j].data() + (size_t)t * KSUB;
+                    for (int c = 0; c < KSUB; c++) acc[c] += m2x * ct[c];
                 }
+                int best = 0;
+                for (int c = 1; c < KSUB; c++)
+                    if (acc[c] < acc[best]) best = c;
                 codes[i * M + j] = (uint8_t)best;
             }
         }
@@ -255,16 +292,22 @@ static void pq_decode(const uint8_t *codes, int64_t n, int d, int M, const float
     });
 }
 
-// Y = X R^T, rows of length d.
+// Y = X R^T, rows of length d (axpy form: vectorises over the output coordinate).
 static void rotate(const float *X, int64_t n, int d, const float *R, float *Y, int nt)
 {
+    std::vector<float> RT((size_t)d * d);
+    for (int t = 0; t < d; t++)
+        for (int u = 0; u < d; u++) RT[(size_t)u * d + t] = R[(size_t)t * d + u];
     parallel_for(n, nt, 1024, [&](int64_t a, int64_t b, int) {
-        for (int64_t i = a; i < b; i++)
-            for (int t = 0; t < d; t++) {
-                double s = 0;
-                for (int u = 0; u < d; u++) s += (double)R[(int64_t)t * d + u] * (double)X[i * d + u];
-                Y[i * d + t] = (float)s;
+        for (int64_t i = a; i < b; i++) {
+            float *y = Y + i * d;
+            for (int t = 0; t < d; t++) y[t] = 0.f;
+            for (int u = 0; u < d; u++) {
+                float xu = X[i * d + u];
+                const float *r = RT.data() + (size_t)u * d;
+                for (int t = 0; t < d; t++) y[t] += r[t] * xu;
             }
+        }
     });
 }
 

@@ -78,7 +78,8 @@ def test_parity_pq16(mix3k, k, ef, shortlist):
     ix, xb, xq = mix3k
     h = handle("mix3k", ix)
     ref = oracle.search(ix, xq, k, ef, shortlist=shortlist)
-    compare(ref, *gpu_search(h, xq, k, ef, shortlist), max_exempt=0.25 if ef >= 256 else 0.05)
+    # every adjacent pair of the k returned is a deciding comparison: more near-ties at k = 100
+    compare(ref, *gpu_search(h, xq, k, ef, shortlist), max_exempt=0.25 if ef >= 256 or k >= 100 else 0.05)
 
 
 @pytest.mark.parametrize("name", ["opq3k", "sift2k"])
@@ -121,13 +122,28 @@ def test_visited_spill_to_global_table(mix3k):
 
 
 def test_exhaustive_walk_equals_oracle():
-    # ef' >= N: the walk scores every reachable node and W holds them all
-    import conftest
-    ix, xb, xq = conftest.oracle_index("mix3k")
-    sub = xq[:40]
-    h = handle("mix3k", ix)
-    ref = oracle.search(ix, sub, 10, 1024, shortlist=-1)
-    compare(ref, *gpu_search(h, sub, 10, 1024, shortlist=-1), max_exempt=0.5)
+    # ef' >= N: every node is scored and expanded whatever the expansion order, so the
+    # counts are exactly (N, N) and only the order of the returned list can hold near-ties
+    from paper_1804_09996_gb300 import datagen as dg
+    xt = dg.gaussian_mixture(3000, 96, 64, stream=dg.STREAM_TRAIN)
+    xb = dg.gaussian_mixture(800, 96, 64, stream=dg.STREAM_BASE)
+    xq = dg.gaussian_mixture(60, 96, 64, stream=dg.STREAM_QUERY)
+    ix = oracle.build_index(xt, xb, 16, 16, False, codec_niter=8)
+    h = handle("exh800", ix)
+    k = 50
+    ref = oracle.search(ix, xq, k, 1024, shortlist=-1)
+    ids, ds, st = gpu_search(h, xq, k, 1024, shortlist=-1)
+    assert (st[:, 0] == ix.N).all() and (st[:, 1] == ix.N).all()
+    assert np.array_equal(st, ref["stats"])
+    np.testing.assert_allclose(ds, ref["dists"], rtol=RTOL)
+    d = oracle.search(ix, xq, k + 1, 1024, shortlist=-1)["dists"]      # one more, for the boundary
+    rel = np.diff(d, axis=1) / d[:, 1:]
+    # a position is decided when both of its neighbours in the order are clearly apart
+    clear = np.ones_like(ids, dtype=bool)
+    clear[:, 1:] &= rel[:, :k - 1] >= TIE
+    clear &= rel[:, :k] >= TIE
+    assert np.array_equal(ids[clear], ref["ids"][clear])
+    assert clear.mean() > 0.9
 
 
 def test_ragged_query_counts(mix3k):
