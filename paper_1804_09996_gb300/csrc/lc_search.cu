@@ -1,8 +1,11 @@
 // GPU search path of Link and Code (Douze, Sablayrolles, Jegou, CVPR 2018), sm_103a.
 //
-// walk_kernel  (one warp per query, persistent over the query list)
-//   - rotation y' = R y and the per-query ADC tables LUT[j][c] = ||y'^j - C1_j[c]||^2
-//     (Section 4.1 "asymmetric distance computations"), FP32 in shared memory;
+// walk_kernel  (one warp per query; persistent CTAs take queries from an atomic counter)
+//   - rotation y' = R y; the walk distance is the ADC distance ||y' - c1(x)||^2 of Section
+//     4.1 ("asymmetric distance computations"): the sum over level-1 sub-spaces j of
+//     ||y'^j - C1_j[c_j]||^2, each term computed in FP32 from the codebook C1, which every
+//     CTA keeps once in shared memory (a per-query table of the same terms would cost
+//     32-64 KB of shared memory per query in flight);
 //   - greedy descent of the upper HNSW levels (Section 2);
 //   - best-first search of level 0 with result set W of size ef' (Section 2), kept as a
 //     sorted list of (distance, id) keys with an "expanded" flag: each step expands the best
@@ -18,10 +21,11 @@
 //     y^ = beta_b^T G(x) with b the vector's codeword (Section 4.3), exact squared L2 to
 //     y', and the final top-k by (distance, id).
 //
-// FP32 walk distance: lane l holds the table entry of sub-space l (M1 = 32), of l mod 16
-// (M1 = 16) or the sum of sub-spaces l and l + 32 (M1 = 64); the 32 lane values are added
-// pairwise, lanes differing in bit 4 first, then bits 3, 2, 1, 0.  The sum order is the same
-// for every node, so a node's distance does not depend on where it is scored.
+// FP32 walk distance: lane l holds the term of sub-space l (M1 = 32), of l mod 16 (M1 = 16)
+// or the sum of sub-spaces l and l + 32 (M1 = 64), each term summed over its coordinates in
+// order; the 32 lane values are added pairwise, lanes differing in bit 3 first, then bits 2,
+// 1, 0 and 4.  The order is the same for every node, so a node's distance does not depend on
+// where or with how many others it is scored.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,13 +45,15 @@ struct DeviceIndex {
     int32_t ep = -1;
     float *Rt = nullptr;          // [d][d], Rt[u*d + t] = R[t][u]
     float *C1 = nullptr, *C2 = nullptr, *B = nullptr;
-    uint8_t *codes1 = nullptr, *codes2 = nullptr, *beta = nullptr;
+    uint8_t *codes1 = nullptr, *codes2b = nullptr;   // codes2b: residual codes padded to M2P bytes, codeword id last
+    int M2P = 0;
     int32_t *adj0 = nullptr, *upper_off = nullptr, *upper_adj = nullptr;
     // scratch, grown on demand
     float *yq = nullptr; size_t yq_cap = 0;
     int32_t *shortlist = nullptr; size_t sl_cap = 0;
     int32_t *spill = nullptr; size_t spill_cap = 0;
     int32_t *status = nullptr;
+    unsigned long long *counter = nullptr;
     // staging for host-pointer calls
     float *q_st = nullptr; size_t q_cap = 0;
     int32_t *ids_st = nullptr; float *d_st = nullptr; int32_t *s_st = nullptr; size_t out_cap = 0;
@@ -67,9 +73,9 @@ void device_free(DeviceIndex *dv)
     cudaGetDevice(&cur);
     if (dv->device >= 0) cudaSetDevice(dv->device);
     cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B);
-    cfree(dv->codes1); cfree(dv->codes2); cfree(dv->beta);
+    cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
-    cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status);
+    cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
     cfree(dv->q_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
     for (auto &e : dv->ev) if (e) cudaEventDestroy(e);
     if (cur >= 0) cudaSetDevice(cur);
@@ -105,32 +111,34 @@ struct WalkArgs {
     float *dists_out;
     int32_t *stats_out;
     int32_t *status;
+    unsigned long long *counter;   // next query to take (reset to 0 before each launch)
     SplitTab s1;
 };
 
-constexpr int MAX_WARPS_PER_BLOCK = 2;   // 1 when two warps' shared memory does not fit
+constexpr int MAX_WALK_WARPS = 16;       // warps (queries in flight) per CTA
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Per-warp shared-memory layout of the walk kernel.
+// Shared memory of the walk kernel: the level-1 codebook C1 [256][d] once per CTA, then one
+// region per warp.
 struct WalkSmem {
-    size_t lut, yq, stage, wkey, wflag, cand, slot, hash, total;
+    size_t yq, stage, wkey, wflag, cand, cunsorted, slot, hash, total;
 };
+
+__host__ __device__ inline size_t walk_c1_bytes(int d) { return align_up((size_t)256 * d * 4, 128); }
 
 __host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log)
 {
     WalkSmem s;
     size_t o = 0;
-    int H = M1 > 32 ? 2 : 1;
-    s.lut = o;   o += (size_t)H * 256 * 32 * 4;
-    s.yq = o;    o += align_up((size_t)d * 4, 16);
-    s.stage = o; o += (size_t)32 * (M1 < 32 ? 16 : M1) * (M1 < 32 ? 2 : 1);
-    o = align_up(o, 16);
-    s.wkey = o;  o += (size_t)2 * efcap * 8;
-    s.wflag = o; o += align_up((size_t)2 * efcap, 16);
-    s.cand = o;  o += 32 * 8;
-    s.slot = o;  o += 32 * 4;
-    s.hash = o;  o += ((size_t)1 << hash_log) * 4;
+    s.yq = o;        o += align_up((size_t)d * 4, 16);
+    s.stage = o;     o += (size_t)32 * M1;
+    s.wkey = o;      o += (size_t)2 * efcap * 8;
+    s.wflag = o;     o += align_up((size_t)2 * efcap, 16);
+    s.cand = o;      o += 32 * 8;
+    s.cunsorted = o; o += 32 * 8;
+    s.slot = o;      o += 32 * 4;
+    s.hash = o;      o += ((size_t)1 << hash_log) * 4;
     s.total = align_up(o, 128);
     return s;
 }
@@ -160,115 +168,131 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v)
     return v;
 }
 
-// Bitonic sort of one 64-bit key per lane, ascending across lanes.
-__device__ __forceinline__ uint64_t warp_sort64(uint64_t key, int lane)
+// Lane bits in the order partial distances are combined: 3, 2, 1, 0, then 4.
+__host__ __device__ constexpr int comb_bit(int k) { return k < 4 ? 3 - k : 4; }
+__host__ __device__ constexpr int ilog2c(int s) { return s <= 1 ? 0 : 1 + ilog2c(s >> 1); }
+
+// Sum over the 32 lanes of S per-slot contributions (S a power of two): reduce-scatter along
+// the first log2(S) combination bits, all-reduce along the rest.  The addition tree of
+// every slot is the same (lanes differing in bit 3 first, then 2, 1, 0, 4), whatever S.
+template <int S>
+__device__ __forceinline__ float reduce_slots(float (&v)[S], int lane)
 {
+    constexpr int LS = ilog2c(S);
 #pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
+    for (int k = 0; k < LS; k++) {
+        const int bit = comb_bit(k);
+        const int half = (S >> k) >> 1;
+        const bool hi = (lane >> bit) & 1;
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            uint64_t o = shfl_xor64(key, j);
-            bool up = (lane & k) == 0;
-            bool lower = (lane & j) == 0;
-            uint64_t mn = o < key ? o : key, mx = o < key ? key : o;
-            key = (lower == up) ? mn : mx;
+        for (int i = 0; i < half; i++) {
+            float send = hi ? v[i] : v[i + half];
+            float keep = hi ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, 1 << bit);
         }
     }
-    return key;
+    float r = v[0];
+#pragma unroll
+    for (int k = LS; k < 5; k++) r += __shfl_xor_sync(FULL, r, 1 << comb_bit(k));
+    return r;
 }
 
-// Reduce-scatter of v[32] (lane l holds the contribution of lane l to slots 0..31): on
-// return v[0] of lane i is the sum over lanes of slot i, added lanes-differing-in-bit-4
-// first, then 3, 2, 1, 0.
-__device__ __forceinline__ float transpose_reduce(float (&v)[32], int lane)
+// Slot whose total lane `lane` holds after reduce_slots<S> (S = 2^LS).
+__device__ __forceinline__ int slot_of_lane(int lane, int LS)
 {
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-        bool hi = lane & 16;
-        float send = hi ? v[i] : v[i + 16];
-        float keep = hi ? v[i + 16] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        bool hi = lane & 8;
-        float send = hi ? v[i] : v[i + 8];
-        float keep = hi ? v[i + 8] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        bool hi = lane & 4;
-        float send = hi ? v[i] : v[i + 4];
-        float keep = hi ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, 4);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-        bool hi = lane & 2;
-        float send = hi ? v[i] : v[i + 2];
-        float keep = hi ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(FULL, send, 2);
-    }
-    {
-        bool hi = lane & 1;
-        float send = hi ? v[0] : v[1];
-        float keep = hi ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(FULL, send, 1);
-    }
-    return v[0];
+    int s = 0;
+    for (int k = 0; k < LS; k++) s = (s << 1) | ((lane >> comb_bit(k)) & 1);
+    return s;
 }
 
-// Walk distances of up to 32 nodes: slot i holds node `e` of lane i (e < 0: empty slot, its
-// result is meaningless).  Code rows are staged in shared memory, each lane then reads the
-// table entries of its own sub-space(s) for every slot (conflict-free: lane l always hits
-// bank l), and the slot sums are formed by transpose_reduce.
-template <int M1>
-__device__ __forceinline__ float score_slots(const float *lut, uint8_t *stage, const uint8_t *codes1,
-                                             int32_t e, unsigned valid, int lane)
+// Per-lane geometry: the level-1 sub-space(s) a lane scores and the query's coordinates in
+// them.  M1 = 16: sub-space lane & 15 (the two half-warps score different nodes);
+// M1 = 32: sub-space lane; M1 = 64: sub-spaces lane and lane + 32.  D1 > 0: every sub-space
+// has D1 coordinates (compile-time); D1 = 0: lengths read at run time (uneven splits).
+template <int M1, int D1>
+struct LaneGeo {
+    static constexpr int NSUB = M1 == 64 ? 2 : 1;
+    static constexpr int DMAX = D1 > 0 ? D1 : (M1 == 16 ? 16 : (M1 == 32 ? 8 : 4));   // d <= 256
+    int off[NSUB], len[NSUB];
+    float y[NSUB][DMAX];
+};
+
+// ||y'^j - C1_j[c]||^2 in the fixed order of the sub-space's coordinates.
+template <int M1, int D1>
+__device__ __forceinline__ float part_dist(const float *C1s, int d, int c, const LaneGeo<M1, D1> &g, int k)
 {
-    if (e >= 0) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(codes1 + (int64_t)e * M1);
+    const float *row = C1s + c * d + g.off[k];
+    float s = 0.f;
+    if (D1 > 0) {
+#pragma unroll
+        for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) {
+            float df = g.y[k][u] - row[u];
+            s = fmaf(df, df, s);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++)
+            if (u < g.len[k]) {
+                float df = g.y[k][u] - row[u];
+                s = fmaf(df, df, s);
+            }
+    }
+    return s;
+}
+
+// Sub-space terms of S slots (S = 16 or 32) for this lane, summed by reduce_slots<S>.
+template <int M1, int D1, int S>
+__device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *stage, int nf, int d,
+                                             const LaneGeo<M1, D1> &g, int lane)
+{
+    float v[S];
+    if (M1 == 16) {
+        const int h = lane >> 4, j = lane & 15;
+#pragma unroll
+        for (int i = 0; i < S / 2; i++) {
+            const int sl = 2 * i + h;                // half-warp h scores slots of parity h
+            float t = 0.f;
+            if (2 * i < nf && sl < nf) t = part_dist<M1, D1>(C1s, d, stage[sl * 16 + j], g, 0);
+            v[2 * i] = h ? 0.f : t;
+            v[2 * i + 1] = h ? t : 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < S; i++) {
+            float t = 0.f;
+            if (i < nf) {
+                t = part_dist<M1, D1>(C1s, d, stage[i * M1 + lane], g, 0);
+                if (M1 == 64) t += part_dist<M1, D1>(C1s, d, stage[i * M1 + 32 + lane], g, 1);
+            }
+            v[i] = t;
+        }
+    }
+    return reduce_slots<S>(v, lane);
+}
+
+// Walk distances of the nf nodes in slot[0..nf) (1 <= nf <= 32): their code rows are staged
+// in shared memory, each lane computes its sub-space terms, and the totals are formed with
+// 16 or 32 slots.  Returns lane's total; *my_slot = the slot it holds (>= 32: none).
+template <int M1, int D1>
+__device__ __forceinline__ float score_nodes(const float *C1s, uint8_t *stage, const uint8_t *codes1,
+                                             const int32_t *slot, int nf, int d,
+                                             const LaneGeo<M1, D1> &g, int lane, int *my_slot)
+{
+    if (lane < nf) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(codes1 + (int64_t)slot[lane] * M1);
         uint4 *dst = reinterpret_cast<uint4 *>(stage + lane * M1);
 #pragma unroll
         for (int u = 0; u < M1 / 16; u++) dst[u] = __ldg(src + u);
     }
     __syncwarp();
-    float v[32];
-    if (M1 == 32) {
-#pragma unroll
-        for (int i = 0; i < 32; i++) {
-            v[i] = 0.f;
-            if (valid & (1u << i)) {
-                int c = stage[i * 32 + lane];
-                v[i] = lut[c * 32 + lane];
-            }
-        }
-    } else if (M1 == 64) {
-#pragma unroll
-        for (int i = 0; i < 32; i++) {
-            v[i] = 0.f;
-            if (valid & (1u << i)) {
-                int c0 = stage[i * 64 + lane];
-                int c1 = stage[i * 64 + 32 + lane];
-                v[i] = lut[c0 * 32 + lane] + lut[(256 + c1) * 32 + lane];
-            }
-        }
-    } else {   // M1 == 16: half-warp g takes the odd (g = 1) or even (g = 0) slots
-        int g = lane >> 4, j = lane & 15;
-#pragma unroll
-        for (int s = 0; s < 16; s++) {
-            int i = 2 * s + g;
-            float t = 0.f;
-            if (valid & (1u << i)) {
-                int c = stage[i * 16 + j];
-                t = lut[c * 32 + lane];
-            }
-            v[2 * s] = g == 0 ? t : 0.f;
-            v[2 * s + 1] = g == 1 ? t : 0.f;
-        }
+    float r;
+    if (nf <= 16) {
+        r = score_slots<M1, D1, 16>(C1s, stage, nf, d, g, lane);
+        *my_slot = lane < 16 ? lane : 32;           // lanes l and l + 16 hold slot l
+    } else {
+        r = score_slots<M1, D1, 32>(C1s, stage, nf, d, g, lane);
+        *my_slot = slot_of_lane(lane, 5);
     }
-    float r = transpose_reduce(v, lane);
     __syncwarp();
     return r;
 }
@@ -313,29 +337,41 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
     return false;       // unreachable: the spill table is kept at most half full
 }
 
-template <int M1>
-__global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32) walk_kernel(const WalkArgs a)
+template <int M1, int D1>
+__global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const WalkSmem L = walk_smem(M1, a.d, a.efcap, a.hash_log);
-    unsigned char *base = smem_raw + (size_t)warp * L.total;
-    float *lut = reinterpret_cast<float *>(base + L.lut);
+    const int d = a.d;
+    // the level-1 codebook, shared by every warp of the CTA
+    float *C1s = reinterpret_cast<float *>(smem_raw);
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(a.C1);
+        float4 *dst = reinterpret_cast<float4 *>(C1s);
+        for (int i = threadIdx.x; i < 256 * d / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log);
+    unsigned char *base = smem_raw + walk_c1_bytes(d) + (size_t)warp * L.total;
     float *yq = reinterpret_cast<float *>(base + L.yq);
     uint8_t *stage = base + L.stage;
     uint64_t *wkey = reinterpret_cast<uint64_t *>(base + L.wkey);
     uint8_t *wflag = base + L.wflag;
     uint64_t *cand = reinterpret_cast<uint64_t *>(base + L.cand);
+    uint64_t *cuns = reinterpret_cast<uint64_t *>(base + L.cunsorted);
     int32_t *slot = reinterpret_cast<int32_t *>(base + L.slot);
     int32_t *hash = reinterpret_cast<int32_t *>(base + L.hash);
-    const int d = a.d, H = 1 << a.hash_log;
-    const int wpb = blockDim.x >> 5;
-    const int64_t gwarp = (int64_t)blockIdx.x * wpb + warp;
-    const int64_t nwarps = (int64_t)gridDim.x * wpb;
+    const int H = 1 << a.hash_log;
+    const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     int32_t *spill = a.spill + (gwarp << a.spill_log);
+    const unsigned lt_mask = (1u << lane) - 1;
 
-    for (int64_t q = gwarp; q < a.nq; q += nwarps) {
-        // rotation y' = R y (fixed order u = 0..d-1), kept in shared memory
+    for (;;) {
+        int64_t q = 0;
+        if (lane == 0) q = atomicAdd(a.counter, 1ull);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= a.nq) break;
+        // rotation y' = R y (fixed order u = 0..d-1)
         const float *y = a.Q + q * d;
         for (int t = lane; t < d; t += 32) {
             float s = 0.f;
@@ -344,50 +380,38 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32) walk_kernel(const Wa
         }
         for (int i = lane; i < H; i += 32) hash[i] = -1;
         __syncwarp();
-        // ADC tables in difference form
-        if (M1 == 16) {
-            int g = lane >> 4, j = lane & 15;
-            int o = a.s1.off[j], l = a.s1.len[j];
-            for (int c = g; c < 256; c += 2) {
-                float s = 0.f;
-                for (int t = 0; t < l; t++) {
-                    float df = yq[o + t] - __ldg(a.C1 + (int64_t)c * d + o + t);
-                    s = fmaf(df, df, s);
-                }
-                lut[c * 32 + j] = s;
-                lut[c * 32 + 16 + j] = s;
-            }
-        } else {
+        LaneGeo<M1, D1> g;
 #pragma unroll
-            for (int h = 0; h < M1 / 32; h++) {
-                int j = h * 32 + lane;
-                int o = a.s1.off[j], l = a.s1.len[j];
-                for (int c = 0; c < 256; c++) {
-                    float s = 0.f;
-                    for (int t = 0; t < l; t++) {
-                        float df = yq[o + t] - __ldg(a.C1 + (int64_t)c * d + o + t);
-                        s = fmaf(df, df, s);
-                    }
-                    lut[(h * 256 + c) * 32 + lane] = s;
-                }
-            }
+        for (int k = 0; k < LaneGeo<M1, D1>::NSUB; k++) {
+            const int j = M1 == 16 ? (lane & 15) : lane + 32 * k;
+            g.off[k] = a.s1.off[j];
+            g.len[k] = a.s1.len[j];
+#pragma unroll
+            for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) g.y[k][u] = u < g.len[k] ? yq[g.off[k] + u] : 0.f;
         }
-        __syncwarp();
+        int my_slot;
 
-        // greedy descent of the upper levels
+        // greedy descent of the upper levels (Section 2)
         int32_t n_up = 0, n_dist = 0, n_expand = 0;
         int32_t cur = a.ep;
-        float dcur = score_slots<M1>(lut, stage, a.codes1, lane == 0 ? cur : -1, 1u, lane);
-        dcur = __shfl_sync(FULL, dcur, 0);
+        if (lane == 0) slot[0] = cur;
+        __syncwarp();
+        float dcur = score_nodes<M1, D1>(C1s, stage, a.codes1, slot, 1, d, g, lane, &my_slot);
+        dcur = __shfl_sync(FULL, dcur, 0);                                    // lane 0 holds slot 0
         if (a.max_level >= 1) n_up = 1;
         for (int l = a.max_level; l >= 1; l--) {
             for (;;) {
                 int32_t e = a.upper_adj[((int64_t)a.upper_off[cur] + l - 1) * DEG + lane];
                 unsigned vm = __ballot_sync(FULL, e >= 0);
-                n_up += __popc(vm);
-                float de = score_slots<M1>(lut, stage, a.codes1, e, vm, lane);
-                uint64_t k = e >= 0 ? make_key(de, e) : ~0ull;
+                int nv = __popc(vm);
+                if (nv == 0) break;
+                if (e >= 0) slot[__popc(vm & lt_mask)] = e;
+                __syncwarp();
+                n_up += nv;
+                float de = score_nodes<M1, D1>(C1s, stage, a.codes1, slot, nv, d, g, lane, &my_slot);
+                uint64_t k = my_slot < nv ? make_key(de, slot[my_slot]) : ~0ull;
                 uint64_t best = warp_min64(k);
+                __syncwarp();
                 if (best < make_key(dcur, cur)) {
                     cur = key_id(best);
                     dcur = key_dist(best);
@@ -399,8 +423,7 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32) walk_kernel(const Wa
 
         // level 0: best-first search with result list W (sorted keys + expanded flags)
         int buf = 0, wn = 1;
-        bool spilled = false;
-        bool failed = false;
+        bool spilled = false, failed = false;
         if (lane == 0) {
             wkey[0] = make_key(dcur, cur);
             wflag[0] = 0;
@@ -444,25 +467,28 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32) walk_kernel(const Wa
             n_dist += nf;
             if (spilled) scount += nf; else hcount += nf;
             if (nf == 0) { scan_from = pos; continue; }
-            // compact the fresh nodes into slots 0..nf-1
-            if (fresh) slot[__popc(fm & ((1u << lane) - 1))] = e;
+            if (fresh) slot[__popc(fm & lt_mask)] = e;
             __syncwarp();
-            int32_t se = lane < nf ? slot[lane] : -1;
-            unsigned vm = nf == 32 ? FULL : ((1u << nf) - 1);
-            float de = score_slots<M1>(lut, stage, a.codes1, se, vm, lane);
-            uint64_t k = se >= 0 ? make_key(de, se) : ~0ull;
+            float de = score_nodes<M1, D1>(C1s, stage, a.codes1, slot, nf, d, g, lane, &my_slot);
+            uint64_t k = my_slot < nf ? make_key(de, slot[my_slot]) : ~0ull;
             if (wn == a.efp && k >= W[wn - 1]) k = ~0ull;      // cannot enter W
             unsigned km = __ballot_sync(FULL, k != ~0ull);
             int nc = __popc(km);
             if (nc == 0) { scan_from = pos; continue; }
-            k = warp_sort64(k, lane);
-            cand[lane] = k;
+            // order the candidates by rank (keys are distinct)
+            if (k != ~0ull) cuns[__popc(km & lt_mask)] = k;
+            __syncwarp();
+            if (lane < nc) {
+                uint64_t mk = cuns[lane];
+                int r = 0;
+                for (int m = 0; m < nc; m++) r += cuns[m] < mk;
+                cand[r] = mk;
+            }
             __syncwarp();
             // merge W (wn keys) with the nc candidates into the other buffer, keep efp
             uint64_t *W2 = wkey + (buf ^ 1) * a.efcap;
             uint8_t *F2 = wflag + (buf ^ 1) * a.efcap;
             int wn2 = min(a.efp, wn + nc);
-            int first_new = a.efp;
             for (int p = lane; p < wn; p += 32) {
                 uint64_t key = W[p];
                 int lo = 0, hi = nc;                     // candidates below key
@@ -473,29 +499,23 @@ __global__ void __launch_bounds__(MAX_WARPS_PER_BLOCK * 32) walk_kernel(const Wa
                 int np = p + lo;
                 if (np < wn2) { W2[np] = key; F2[np] = F[p]; }
             }
+            int first_new = a.efp;
             if (lane < nc) {
+                uint64_t ck = cand[lane];
                 int lo = 0, hi = wn;                     // W members below the candidate
                 while (lo < hi) {
                     int mid = (lo + hi) >> 1;
-                    if (W[mid] < k) lo = mid + 1; else hi = mid;
+                    if (W[mid] < ck) lo = mid + 1; else hi = mid;
                 }
                 int np = lane + lo;
-                if (np < wn2) { W2[np] = k; F2[np] = 0; }
-                if (lane == 0) first_new = np;
+                if (np < wn2) { W2[np] = ck; F2[np] = 0; }
+                first_new = np;
             }
             first_new = __shfl_sync(FULL, first_new, 0);
-            // everything before the expanded node's new place, other than new candidates,
-            // was already expanded
-            int shifted = pos;                           // pos + (candidates below ckey)
-            {
-                int lo = 0, hi = nc;
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (cand[mid] < ckey) lo = mid + 1; else hi = mid;
-                }
-                shifted = pos + lo;
-            }
-            scan_from = min(first_new, shifted);
+            // everything before min(first new candidate, expanded node's new place) is expanded
+            int below = 0;
+            for (int m = 0; m < nc; m++) below += cand[m] < ckey;
+            scan_from = min(first_new, pos + below);
             scan_from -= scan_from % 32;
             wn = wn2;
             buf ^= 1;
@@ -532,9 +552,9 @@ struct RefineArgs {
     const float *yq;
     const int32_t *shortlist;
     int64_t nq;
-    int R, k, d, M1, M2;
+    int R, k, d, M1, M2P;           // M2P: padded row of the residual codes (codeword id last)
     const float *C1, *C2, *B;
-    const uint8_t *codes1, *codes2, *beta;
+    const uint8_t *codes1, *codes2b;
     const int32_t *adj0;
     int32_t *ids_out;
     float *dists_out;
@@ -542,75 +562,123 @@ struct RefineArgs {
 };
 
 constexpr int REF_CH = 8;            // candidates staged at a time
-constexpr int REF_WARPS = 4;
 
-__host__ __device__ inline size_t refine_smem(int M1, int M2, int R)
+__host__ __device__ inline int pow2_at_least(int r)
 {
-    int RP = 32;
-    while (RP < R) RP <<= 1;
+    int p = 32;
+    while (p < r) p <<= 1;
+    return p;
+}
+
+// Per-warp shared memory of the refinement kernel.
+__host__ __device__ inline size_t refine_smem(int M1, int M2P, int R)
+{
     size_t o = 0;
     o += (size_t)REF_CH * 9 * 4;            // vertex ids
     o += (size_t)REF_CH * 9 * 4;            // weights
-    o += align_up((size_t)REF_CH * 9 * M1, 16);
-    o += align_up((size_t)REF_CH * 9 * M2, 16);
-    o += (size_t)RP * 8;                     // keys
+    o += (size_t)REF_CH * 9 * M1;           // level-1 code rows
+    o += (size_t)REF_CH * 9 * M2P;          // level-2 code rows (+ codeword id)
+    o += (size_t)pow2_at_least(R) * 8;      // keys
     return align_up(o, 128);
 }
 
-__global__ void __launch_bounds__(REF_WARPS * 32) refine_kernel(const RefineArgs a)
+// One warp per query.  C2_SHARED: both codebooks sit in shared memory (d*4 bytes is a
+// multiple of 128, so lane t reading coordinate t of any centroid hits bank t mod 32);
+// otherwise only C1 does and C2 is read through the cache.
+template <bool C2_SHARED>
+__global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const size_t per = refine_smem(a.M1, a.M2, a.R);
-    unsigned char *base = smem_raw + (size_t)warp * per;
-    int RP = 32;
-    while (RP < a.R) RP <<= 1;
+    const int d = a.d, M1 = a.M1, M2P = a.M2P;
+    float *C1s = reinterpret_cast<float *>(smem_raw);
+    float *C2s = C1s + 256 * d;
+    {
+        const float4 *s1 = reinterpret_cast<const float4 *>(a.C1);
+        const float4 *s2 = reinterpret_cast<const float4 *>(a.C2);
+        for (int i = threadIdx.x; i < 64 * d; i += blockDim.x) {
+            reinterpret_cast<float4 *>(C1s)[i] = __ldg(s1 + i);
+            if (C2_SHARED) reinterpret_cast<float4 *>(C2s)[i] = __ldg(s2 + i);
+        }
+    }
+    __syncthreads();
+    const float *C2 = C2_SHARED ? C2s : a.C2;
+    const size_t cb = (size_t)(C2_SHARED ? 2 : 1) * 256 * d * 4;
+    unsigned char *base = smem_raw + cb + (size_t)warp * refine_smem(M1, M2P, a.R);
+    const int RP = pow2_at_least(a.R);
     int32_t *vid = reinterpret_cast<int32_t *>(base);
     float *wt = reinterpret_cast<float *>(base + REF_CH * 9 * 4);
     uint8_t *st1 = base + REF_CH * 9 * 8;
-    uint8_t *st2 = st1 + align_up((size_t)REF_CH * 9 * a.M1, 16);
-    uint64_t *keys = reinterpret_cast<uint64_t *>(st2 + align_up((size_t)REF_CH * 9 * a.M2, 16));
-    const int d = a.d, M1 = a.M1, M2 = a.M2;
-    const int64_t gwarp = (int64_t)blockIdx.x * REF_WARPS + warp;
-    const int64_t nwarps = (int64_t)gridDim.x * REF_WARPS;
+    uint8_t *st2 = st1 + REF_CH * 9 * M1;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(st2 + REF_CH * 9 * M2P);
+    const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int r1 = M1 / 16, r2 = M2P / 16;          // 16-byte pieces per row
 
     for (int64_t q = gwarp; q < a.nq; q += nwarps) {
         const int32_t *sl = a.shortlist + q * a.R;
-        int rn = 0;                                  // shortlist entries present
+        int rn = 0;                                  // shortlist entries present (packed first)
         for (int i = lane; i < a.R; i += 32) rn += sl[i] >= 0;
 #pragma unroll
         for (int m = 16; m > 0; m >>= 1) rn += __shfl_xor_sync(FULL, rn, m);
         for (int i = lane; i < RP; i += 32) keys[i] = ~0ull;
         for (int c0 = 0; c0 < rn; c0 += REF_CH) {
-            int nc = min(REF_CH, rn - c0);
-            // G(x) vertex ids and codeword weights: task = (candidate r, column j)
-            for (int t = lane; t < nc * 9; t += 32) {
-                int r = t / 9, j = t % 9;
-                int32_t i = sl[c0 + r];
-                int32_t v = j == 0 ? i : a.adj0[(int64_t)i * DEG + j - 1];
-                vid[t] = v;
-                wt[t] = __ldg(a.B + (int)a.beta[i] * 9 + j);
+            const int nc = min(REF_CH, rn - c0);
+            // one candidate per lane: its id, codeword and the 8 neighbours of G(x); the
+            // loads of a phase are all issued before any is used
+            if (lane < nc) {
+                const int32_t i = sl[c0 + lane];
+                const int b = a.codes2b[(int64_t)i * M2P + M2P - 1];
+                const int4 *ar = reinterpret_cast<const int4 *>(a.adj0 + (int64_t)i * DEG);
+                const int4 a0 = __ldg(ar), a1 = __ldg(ar + 1);
+                float w[9];
+#pragma unroll
+                for (int j = 0; j < 9; j++) w[j] = __ldg(a.B + b * 9 + j);
+                int32_t *vr = vid + lane * 9;
+                vr[0] = i;
+                vr[1] = a0.x; vr[2] = a0.y; vr[3] = a0.z; vr[4] = a0.w;
+                vr[5] = a1.x; vr[6] = a1.y; vr[7] = a1.z; vr[8] = a1.w;
+#pragma unroll
+                for (int j = 0; j < 9; j++) wt[lane * 9 + j] = w[j];
             }
             __syncwarp();
-            // stage both code rows of every vertex (row-wise, coalesced)
-            for (int t = 0; t < nc * 9; t++) {
-                int32_t v = vid[t];
-                if (v < 0) continue;
-                for (int b = lane; b < M1; b += 32) st1[t * M1 + b] = a.codes1[(int64_t)v * M1 + b];
-                for (int b = lane; b < M2; b += 32) st2[t * M2 + b] = a.codes2[(int64_t)v * M2 + b];
+            // stage both code rows of every vertex: 16-byte pieces, six loads in flight per lane
+            const int per_row = r1 + r2, pieces = nc * 9 * per_row;
+            for (int t0 = lane; t0 < pieces; t0 += 32 * 6) {
+                uint4 buf[6];
+                bool use[6];
+#pragma unroll
+                for (int u = 0; u < 6; u++) {
+                    const int t = t0 + 32 * u;
+                    const int row = t / per_row, pc = t % per_row;
+                    use[u] = t < pieces && vid[row] >= 0;
+                    if (use[u]) {
+                        const int64_t v = vid[row];
+                        buf[u] = pc < r1 ? __ldg(reinterpret_cast<const uint4 *>(a.codes1 + v * M1) + pc)
+                                         : __ldg(reinterpret_cast<const uint4 *>(a.codes2b + v * M2P) + (pc - r1));
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 6; u++) {
+                    const int t = t0 + 32 * u;
+                    const int row = t / per_row, pc = t % per_row;
+                    if (use[u]) {
+                        if (pc < r1) reinterpret_cast<uint4 *>(st1 + row * M1)[pc] = buf[u];
+                        else reinterpret_cast<uint4 *>(st2 + row * M2P)[pc - r1] = buf[u];
+                    }
+                }
             }
             __syncwarp();
             for (int r = 0; r < nc; r++) {
                 float part = 0.f;
                 for (int t = lane; t < d; t += 32) {
-                    int s1 = a.sub1[t], s2 = a.sub2[t];
+                    const int s1 = a.sub1[t], s2 = a.sub2[t];
                     float yh = 0.f;
 #pragma unroll
                     for (int j = 0; j < 9; j++) {
-                        int tt = r * 9 + j;
+                        const int tt = r * 9 + j;
                         if (vid[tt] < 0) continue;
-                        float x = __ldg(a.C1 + (int)st1[tt * M1 + s1] * d + t) +
-                                  __ldg(a.C2 + (int)st2[tt * M2 + s2] * d + t);
+                        float x = C1s[(int)st1[tt * M1 + s1] * d + t] + C2[(int)st2[tt * M2P + s2] * d + t];
                         yh = fmaf(wt[tt], x, yh);
                     }
                     float df = a.yq[q * d + t] - yh;
@@ -638,7 +706,7 @@ __global__ void __launch_bounds__(REF_WARPS * 32) refine_kernel(const RefineArgs
             }
         }
         for (int i = lane; i < a.k; i += 32) {
-            uint64_t kk = i < RP ? keys[i] : ~0ull;
+            uint64_t kk = keys[i];
             bool ok = kk != ~0ull;
             a.ids_out[q * a.k + i] = ok ? key_id(kk) : -1;
             a.dists_out[q * a.k + i] = ok ? key_dist(kk) : __int_as_float(0x7f800000);
@@ -690,7 +758,8 @@ static lc_status upload(lc_index *ix)
         dv = ix->dev = new DeviceIndex();
         dv->device = dev;
         cudaDeviceGetAttribute(&dv->num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaMalloc(&dv->status, sizeof(int32_t)) != cudaSuccess) {
+        if (cudaMalloc(&dv->status, sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&dv->counter, sizeof(unsigned long long)) != cudaSuccess) {
             set_error("cudaMalloc failed for the status word");
             return LC_ERR_OOM;
         }
@@ -701,9 +770,16 @@ static lc_status upload(lc_index *ix)
         for (int u = 0; u < d; u++) Rt[(size_t)u * d + t] = ix->R[(size_t)t * d + u];
     std::vector<int32_t> off(ix->n);
     for (int64_t i = 0; i < ix->n; i++) off[i] = (int32_t)ix->upper_off[i];
+    // residual codes with the codeword id in the last byte of a 16-byte-aligned row
+    const int M2 = ix->p.M2, M2P = (int)align_up((size_t)M2 + 1, 16);
+    std::vector<uint8_t> c2b((size_t)ix->n * M2P, 0);
+    for (int64_t i = 0; i < ix->n; i++) {
+        std::memcpy(c2b.data() + i * M2P, ix->codes2.data() + i * M2, M2);
+        c2b[i * M2P + M2P - 1] = ix->beta[i];
+    }
     bool ok = dupload(dv->Rt, Rt) && dupload(dv->C1, ix->C1) && dupload(dv->C2, ix->C2) &&
               dupload(dv->B, ix->B) && dupload(dv->codes1, ix->codes1) &&
-              dupload(dv->codes2, ix->codes2) && dupload(dv->beta, ix->beta) &&
+              dupload(dv->codes2b, c2b) &&
               dupload(dv->adj0, ix->adj0) && dupload(dv->upper_off, off) &&
               dupload(dv->upper_adj, ix->upper_adj);
     if (!ok) {
@@ -714,6 +790,7 @@ static lc_status upload(lc_index *ix)
     dv->d = d;
     dv->M1 = ix->p.M1;
     dv->M2 = ix->p.M2;
+    dv->M2P = M2P;
     dv->ep = ix->ep;
     dv->max_level = ix->max_level < 0 ? 0 : ix->max_level;
     ix->dev_dirty = false;
@@ -729,29 +806,32 @@ static int ilog2_ceil(int64_t x)
 
 constexpr size_t MAX_SMEM_PER_BLOCK = 227 * 1024;
 
-template <int M1>
-static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int *wpb_out,
-                               int *grid_out)
+// Warps per CTA: as many as fit next to the codebook (at most MAX_WALK_WARPS).
+template <int M1, int D1>
+static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int *wpc_out,
+                               int *grid_out, size_t *smem_out)
 {
-    int wpb = smem_per_warp * MAX_WARPS_PER_BLOCK <= MAX_SMEM_PER_BLOCK ? MAX_WARPS_PER_BLOCK : 1;
-    size_t smem = smem_per_warp * wpb;
-    if (smem > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t c1 = walk_c1_bytes(wa.d);
+    if (c1 + smem_per_warp > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
+    int wpc = (int)std::min<size_t>(MAX_WALK_WARPS, (MAX_SMEM_PER_BLOCK - c1) / smem_per_warp);
+    size_t smem = c1 + smem_per_warp * wpc;
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1>, wpb * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1>, wpc * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int64_t need = (wa.nq + wpb - 1) / wpb;
+    int64_t need = (wa.nq + wpc - 1) / wpc;
     *grid_out = (int)std::min<int64_t>(need, (int64_t)per_sm * num_sms);
-    *wpb_out = wpb;
+    *wpc_out = wpc;
+    *smem_out = smem;
     return cudaSuccess;
 }
 
-template <int M1>
-static cudaError_t run_walk(const WalkArgs &wa, size_t smem_per_warp, int wpb, int grid, cudaStream_t st)
+template <int M1, int D1>
+static cudaError_t run_walk(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
 {
-    walk_kernel<M1><<<grid, wpb * 32, smem_per_warp * wpb, st>>>(wa);
+    walk_kernel<M1, D1><<<grid, wpc * 32, smem, st>>>(wa);
     return cudaGetLastError();
 }
 
@@ -832,8 +912,8 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
     wa.ep = dv->ep; wa.max_level = dv->max_level;
     wa.efp = efp; wa.efcap = (int)align_up(efp, 32);
     wa.R = R; wa.refine = refine ? 1 : 0;
-    wa.hash_log = sp->visited_log ? sp->visited_log : std::min(14, std::max(10, ilog2_ceil((int64_t)efp * 32)));
-    wa.spill_log = 16;
+    wa.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));
+    wa.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)efp * 64)));
     wa.status = dv->status;
     wa.stats_out = dstats;
     std::vector<int> off, len;
@@ -841,10 +921,25 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
     for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
     size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log).total;
     int grid = 0, wpb = 1;
+    size_t smem = 0;
     cudaError_t ce;
-    if (dv->M1 == 16) ce = launch_walk<16>(wa, per_warp, dv->num_sms, &wpb, &grid);
-    else if (dv->M1 == 32) ce = launch_walk<32>(wa, per_warp, dv->num_sms, &wpb, &grid);
-    else ce = launch_walk<64>(wa, per_warp, dv->num_sms, &wpb, &grid);
+    // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
+    const int variant = (dv->M1 == 16 && dv->d == 96) ? 1 : (dv->M1 == 32 && dv->d == 96) ? 2
+                      : (dv->M1 == 64 && dv->d == 128) ? 3 : 0;
+    switch (variant) {
+    case 1: ce = launch_walk<16, 6>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem); break;
+    case 2: ce = launch_walk<32, 3>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem); break;
+    case 3: ce = launch_walk<64, 2>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem); break;
+    default:
+        if (dv->M1 == 16) ce = launch_walk<16, 0>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem);
+        else if (dv->M1 == 32) ce = launch_walk<32, 0>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem);
+        else ce = launch_walk<64, 0>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem);
+    }
+    if (ce == cudaErrorInvalidConfiguration) {
+        set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
+                  "lower efSearch or visited_log", per_warp, walk_c1_bytes(dv->d));
+        return LC_ERR_CAPACITY;
+    }
     if (ce != cudaSuccess) {
         set_error("walk kernel configuration failed (%zu B shared memory per warp): %s", per_warp,
                   cudaGetErrorString(ce));
@@ -867,7 +962,9 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
         wa.ids_out = dids;
         wa.dists_out = ddists;
     }
-    if (cudaMemsetAsync(dv->status, 0, sizeof(int32_t), st) != cudaSuccess) {
+    wa.counter = dv->counter;
+    if (cudaMemsetAsync(dv->status, 0, sizeof(int32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(dv->counter, 0, sizeof(unsigned long long), st) != cudaSuccess) {
         set_error("status reset failed");
         return LC_ERR_CUDA;
     }
@@ -876,9 +973,15 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(dv->ev[0], st);
     }
-    if (dv->M1 == 16) ce = run_walk<16>(wa, per_warp, wpb, grid, st);
-    else if (dv->M1 == 32) ce = run_walk<32>(wa, per_warp, wpb, grid, st);
-    else ce = run_walk<64>(wa, per_warp, wpb, grid, st);
+    switch (variant) {
+    case 1: ce = run_walk<16, 6>(wa, smem, wpb, grid, st); break;
+    case 2: ce = run_walk<32, 3>(wa, smem, wpb, grid, st); break;
+    case 3: ce = run_walk<64, 2>(wa, smem, wpb, grid, st); break;
+    default:
+        if (dv->M1 == 16) ce = run_walk<16, 0>(wa, smem, wpb, grid, st);
+        else if (dv->M1 == 32) ce = run_walk<32, 0>(wa, smem, wpb, grid, st);
+        else ce = run_walk<64, 0>(wa, smem, wpb, grid, st);
+    }
     if (dv->profile) cudaEventRecord(dv->ev[1], st);
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
@@ -887,22 +990,32 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
     if (refine) {
         RefineArgs ra{};
         ra.yq = dv->yq; ra.shortlist = dv->shortlist; ra.nq = nq; ra.R = R; ra.k = k; ra.d = dv->d;
-        ra.M1 = dv->M1; ra.M2 = dv->M2; ra.C1 = dv->C1; ra.C2 = dv->C2; ra.B = dv->B;
-        ra.codes1 = dv->codes1; ra.codes2 = dv->codes2; ra.beta = dv->beta; ra.adj0 = dv->adj0;
+        ra.M1 = dv->M1; ra.M2P = dv->M2P; ra.C1 = dv->C1; ra.C2 = dv->C2; ra.B = dv->B;
+        ra.codes1 = dv->codes1; ra.codes2b = dv->codes2b; ra.adj0 = dv->adj0;
         ra.ids_out = dids; ra.dists_out = ddists;
         std::vector<int> o2, l2;
         splits(dv->d, dv->M1, off, len);
         splits(dv->d, dv->M2, o2, l2);
         for (int j = 0; j < dv->M1; j++) for (int t = off[j]; t < off[j] + len[j]; t++) ra.sub1[t] = (uint8_t)j;
         for (int j = 0; j < dv->M2; j++) for (int t = o2[j]; t < o2[j] + l2[j]; t++) ra.sub2[t] = (uint8_t)j;
-        size_t rs_per = refine_smem(dv->M1, dv->M2, R);
-        size_t rsm = rs_per * REF_WARPS;
-        cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        const size_t per = refine_smem(dv->M1, dv->M2P, R);
+        const size_t cbytes = (size_t)256 * dv->d * 4;
+        // both codebooks in shared memory when that leaves room for at least 4 warps
+        const bool both = 2 * cbytes + 4 * per <= MAX_SMEM_PER_BLOCK;
+        const size_t cb = (both ? 2 : 1) * cbytes;
+        if (cb + per > MAX_SMEM_PER_BLOCK) {
+            set_error("refinement does not fit in shared memory (d = %d)", dv->d);
+            return LC_ERR_CAPACITY;
+        }
+        const int rw = (int)std::min<size_t>(16, (MAX_SMEM_PER_BLOCK - cb) / per);
+        const size_t rsm = cb + per * rw;
+        auto kern = both ? refine_kernel<true> : refine_kernel<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_kernel, REF_WARPS * 32, rsm);
-        int64_t need = (nq + REF_WARPS - 1) / REF_WARPS;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, rw * 32, rsm);
+        int64_t need = (nq + rw - 1) / rw;
         int rgrid = (int)std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * dv->num_sms);
-        refine_kernel<<<rgrid, REF_WARPS * 32, rsm, st>>>(ra);
+        kern<<<rgrid, rw * 32, rsm, st>>>(ra);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) {
             set_error("refine kernel launch failed: %s", cudaGetErrorString(ce));
