@@ -614,9 +614,21 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
     const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int r1 = M1 / 16, r2 = M2P / 16;          // 16-byte pieces per row
+    // sub-spaces of this lane's coordinates t = lane + 32 u (read once: indexing the
+    // parameter space with a per-lane index would serialise)
+    int s1v[8], s2v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+        const int t = lane + 32 * u;
+        s1v[u] = t < d ? a.sub1[t] : 0;
+        s2v[u] = t < d ? a.sub2[t] : 0;
+    }
 
     for (int64_t q = gwarp; q < a.nq; q += nwarps) {
         const int32_t *sl = a.shortlist + q * a.R;
+        float yv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) yv[u] = lane + 32 * u < d ? a.yq[q * d + lane + 32 * u] : 0.f;
         int rn = 0;                                  // shortlist entries present (packed first)
         for (int i = lane; i < a.R; i += 32) rn += sl[i] >= 0;
 #pragma unroll
@@ -671,18 +683,21 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
             __syncwarp();
             for (int r = 0; r < nc; r++) {
                 float part = 0.f;
-                for (int t = lane; t < d; t += 32) {
-                    const int s1 = a.sub1[t], s2 = a.sub2[t];
-                    float yh = 0.f;
 #pragma unroll
-                    for (int j = 0; j < 9; j++) {
-                        const int tt = r * 9 + j;
-                        if (vid[tt] < 0) continue;
-                        float x = C1s[(int)st1[tt * M1 + s1] * d + t] + C2[(int)st2[tt * M2P + s2] * d + t];
-                        yh = fmaf(wt[tt], x, yh);
+                for (int u = 0; u < 8; u++) {
+                    const int t = lane + 32 * u;
+                    if (t < d) {
+                        float yh = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 9; j++) {
+                            const int tt = r * 9 + j;
+                            if (vid[tt] < 0) continue;
+                            float x = C1s[(int)st1[tt * M1 + s1v[u]] * d + t] + C2[(int)st2[tt * M2P + s2v[u]] * d + t];
+                            yh = fmaf(wt[tt], x, yh);
+                        }
+                        float df = yv[u] - yh;
+                        part = fmaf(df, df, part);
                     }
-                    float df = a.yq[q * d + t] - yh;
-                    part = fmaf(df, df, part);
                 }
 #pragma unroll
                 for (int m = 16; m > 0; m >>= 1) part += __shfl_xor_sync(FULL, part, m);
