@@ -157,6 +157,26 @@ lc_status lc_export(const lc_index *ix, float *R, float *C1, float *C2, uint8_t 
 lc_status lc_save(const lc_index *ix, const char *path);
 lc_status lc_load(const char *path, lc_index **out);
 
+/* The level-0 walk of lc_search without refinement (as lc_search with shortlist < 0:
+ * outputs the walk's own top-k by ADC distance, same layouts), for callers that cannot let
+ * the library allocate device memory while they serve.  cudaMalloc and cudaFree may
+ * synchronise the whole device and take unbounded time, which a latency-bound request loop
+ * cannot afford, and an application that manages device memory through its own pool or a
+ * fixed budget cannot have memory taken behind its back.  This call allocates nothing: its
+ * scratch is a file-scope device array of 32 MiB + 256 B in liblc.so (held on every GPU that
+ * loads the library until the process exits), looked up once per device on the call's first
+ * use there, so make that first call before any stream capture.  The paper has no
+ * counterpart; it is an operational variant of the search above.
+ * Requirements: q, ids, dists (and stats, may be NULL) are device pointers; the index is
+ * already resident on the current device (an earlier lc_search uploads it), else
+ * LC_ERR_STATE; max(ef, k) <= 256, else LC_ERR_ARG.  Work is queued on `stream` and the call
+ * returns without waiting.  Every call shares the one scratch array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be serialised by
+ * the caller.  A query whose visited set overflows the scratch reports n_dist = -1 in stats
+ * and ids -1.  Errors: LC_ERR_ARG, LC_ERR_STATE, LC_ERR_CUDA, LC_ERR_CAPACITY. */
+lc_status lc_search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef,
+                                 int32_t *ids, float *dists, int32_t *stats, void *stream);
+
 /* Kernel timing: after lc_profile(ix, 1) every lc_search records CUDA events on its stream
  * around the walk kernel and the refinement kernel; lc_profile_read waits for the last
  * profiled search and returns the two durations in milliseconds (refine_ms = 0 without

@@ -349,6 +349,18 @@ void lc_free(lc_index *ix)
 
 const char *lc_last_error(void) { return g_err; }
 
+lc_status lc_search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef,
+                                 int32_t *ids, float *dists, int32_t *stats, void *stream)
+{
+    set_error("");
+    if (!ix) { set_error("null index"); return LC_ERR_ARG; }
+    if (nq < 0 || (nq > 0 && (!q || !ids || !dists))) { set_error("null query or output buffer"); return LC_ERR_ARG; }
+    if (k < 1 || k > MAX_K) { set_error("k = %d outside 1..%d", k, MAX_K); return LC_ERR_ARG; }
+    if (ef < 1) { set_error("ef must be >= 1"); return LC_ERR_ARG; }
+    if (!ix->trained) { set_error("search before lc_train/lc_import"); return LC_ERR_STATE; }
+    return lc::search_walk_noalloc(ix, q, nq, k, ef, ids, dists, stats, stream);
+}
+
 lc_status lc_profile(lc_index *ix, int enable)
 {
     set_error("");

@@ -31,6 +31,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "lc_internal.h"
 
@@ -1057,6 +1058,147 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
             set_error("a query's visited set overflowed its table (efSearch too large)");
             return LC_ERR_CAPACITY;
         }
+    }
+    return LC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Walk without allocation (lc_search_walk_noalloc).  Some callers cannot let the library call
+// cudaMalloc while they serve: it may synchronise the whole device and take unbounded time,
+// which a latency-bound request loop cannot afford, and an application that owns the device
+// memory through its own pool or a fixed budget cannot have memory taken behind its back.
+// This entry point runs the same walk kernel as lc_search, but its scratch (the query
+// counter, the status word and the per-warp spill tables of the visited sets) lives in the
+// file-scope array below, which every GPU that loads this library holds until exit.
+constexpr int NOALLOC_SPILL_LOG = 12;                  // 4096 ids per query in flight
+constexpr size_t NOALLOC_SLOTS = 2048;                 // queries in flight at most
+constexpr size_t NOALLOC_HEADER = 256;                 // counter (8 B) and status (4 B)
+constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_SLOTS * ((size_t)1 << NOALLOC_SPILL_LOG) * 4;
+constexpr int NOALLOC_MAX_EF = 256;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device, looked up once per device.
+static lc_status noalloc_scratch(int dev, unsigned char **out)
+{
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_error("device %d is beyond the %d devices the no-allocation path tracks", dev, NOALLOC_MAX_DEVICES);
+        return LC_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+            return LC_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return LC_OK;
+}
+
+lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef, int32_t *ids,
+                              float *dists, int32_t *stats, void *stream_)
+{
+    cudaStream_t st = (cudaStream_t)stream_;
+    const int efp = std::max(ef, k);
+    if (efp > NOALLOC_MAX_EF) {
+        set_error("max(ef, k) = %d exceeds %d, the widest walk the no-allocation scratch supports", efp,
+                  NOALLOC_MAX_EF);
+        return LC_ERR_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        set_error("no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+        return LC_ERR_CUDA;
+    }
+    DeviceIndex *dv = ix->dev;
+    if (!dv || ix->dev_dirty || dv->device != dev) {
+        set_error("index is not resident on device %d: run lc_search (which uploads it) first", dev);
+        return LC_ERR_STATE;
+    }
+    auto on_device = [](const void *p) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    };
+    if (nq > 0 && (!on_device(q) || !on_device(ids) || !on_device(dists) || (stats && !on_device(stats)))) {
+        set_error("the no-allocation walk takes device pointers only");
+        return LC_ERR_ARG;
+    }
+    if (nq == 0) return LC_OK;
+    if (dv->n == 0) {
+        set_error("the no-allocation walk needs a non-empty index");
+        return LC_ERR_STATE;
+    }
+    unsigned char *scratch = nullptr;
+    lc_status s = noalloc_scratch(dev, &scratch);
+    if (s != LC_OK) return s;
+
+    WalkArgs wa{};
+    wa.Q = q; wa.nq = nq; wa.d = dv->d;
+    wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.codes1 = dv->codes1;
+    wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
+    wa.ep = dv->ep; wa.max_level = dv->max_level;
+    wa.efp = efp; wa.efcap = (int)align_up(efp, 32);
+    wa.R = k; wa.refine = 0;
+    wa.hash_log = std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));
+    wa.spill_log = NOALLOC_SPILL_LOG;
+    wa.ids_out = ids; wa.dists_out = dists; wa.stats_out = stats;
+    wa.counter = reinterpret_cast<unsigned long long *>(scratch);
+    wa.status = reinterpret_cast<int32_t *>(scratch + 8);
+    wa.spill = reinterpret_cast<int32_t *>(scratch + NOALLOC_HEADER);
+    std::vector<int> off, len;
+    splits(dv->d, dv->M1, off, len);
+    for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
+    const size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log).total;
+    const int variant = (dv->M1 == 16 && dv->d == 96) ? 1 : (dv->M1 == 32 && dv->d == 96) ? 2
+                      : (dv->M1 == 64 && dv->d == 128) ? 3 : 0;
+    int grid = 0, wpc = 1;
+    size_t smem = 0;
+    cudaError_t ce;
+    switch (variant) {
+    case 1: ce = launch_walk<16, 6>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem); break;
+    case 2: ce = launch_walk<32, 3>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem); break;
+    case 3: ce = launch_walk<64, 2>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem); break;
+    default:
+        if (dv->M1 == 16) ce = launch_walk<16, 0>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
+        else if (dv->M1 == 32) ce = launch_walk<32, 0>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
+        else ce = launch_walk<64, 0>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
+    }
+    if (ce != cudaSuccess) {
+        set_error("walk kernel configuration failed: %s", cudaGetErrorString(ce));
+        return ce == cudaErrorInvalidConfiguration ? LC_ERR_CAPACITY : LC_ERR_CUDA;
+    }
+    // every warp in flight owns one spill table of the array
+    grid = (int)std::min<int64_t>(grid, (int64_t)(NOALLOC_SLOTS / wpc));
+    // the array keeps the previous call's contents: the counter and status start at zero
+    // (spill tables are cleared by the kernel before a query uses one)
+    if (cudaMemsetAsync(scratch, 0, 16, st) != cudaSuccess) {
+        set_error("reset of the no-allocation scratch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return LC_ERR_CUDA;
+    }
+    switch (variant) {
+    case 1: ce = run_walk<16, 6>(wa, smem, wpc, grid, st); break;
+    case 2: ce = run_walk<32, 3>(wa, smem, wpc, grid, st); break;
+    case 3: ce = run_walk<64, 2>(wa, smem, wpc, grid, st); break;
+    default:
+        if (dv->M1 == 16) ce = run_walk<16, 0>(wa, smem, wpc, grid, st);
+        else if (dv->M1 == 32) ce = run_walk<32, 0>(wa, smem, wpc, grid, st);
+        else ce = run_walk<64, 0>(wa, smem, wpc, grid, st);
+    }
+    if (ce != cudaSuccess) {
+        set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
+        return LC_ERR_CUDA;
     }
     return LC_OK;
 }

@@ -21,7 +21,7 @@ LC_LUT_FP32 = 0
 EXPORTED = [
     "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_search",
     "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
-    "lc_profile_read", "lc_free", "lc_last_error",
+    "lc_profile_read", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
 ]
 
 
@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
         "lc_save": (I, [P, ctypes.c_char_p]),
         "lc_load": (I, [ctypes.c_char_p, P]),
         "lc_profile": (I, [P, I]),
+        "lc_search_walk_noalloc": (I, [P, P, I64, I, I, P, P, P, P]),
         "lc_profile_read": (I, [P, P, P]),
         "lc_free": (None, [P]),
         "lc_last_error": (ctypes.c_char_p, []),
@@ -147,6 +148,16 @@ def lc_search(ix, q, nq: int, sp: lc_search_params, ids, dists, stats=None, stre
         s = s.cuda_stream
     _check(lib().lc_search(ix, _ptr(q), nq, ctypes.byref(sp), _ptr(ids), _ptr(dists), _ptr(stats),
                            ctypes.c_void_p(s) if s else None))
+
+
+def lc_search_walk_noalloc(ix, q, nq: int, k: int, ef: int, ids, dists, stats=None, stream=None):
+    """The walk of lc_search without refinement, with no device allocation (device tensors
+    only; see include/lc.h for the requirements)."""
+    s = stream
+    if s is not None and hasattr(s, "cuda_stream"):
+        s = s.cuda_stream
+    _check(lib().lc_search_walk_noalloc(ix, _ptr(q), nq, k, ef, _ptr(ids), _ptr(dists), _ptr(stats),
+                                        ctypes.c_void_p(s) if s else None))
 
 
 def lc_import(ix, n, R, C1, C2, codes1, codes2, beta, B, adj0, levels, upper_adj, ep: int):
