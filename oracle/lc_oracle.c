@@ -11,7 +11,8 @@
  * Everything is single-threaded, in double precision, written for reading rather than
  * speed: sets are plain arrays scanned linearly, and each step follows the paper's order.
  *
- *   orc_search      Section 4.1 (two-stage search) over the HNSW structure of Section 2:
+ *   orc_search      Section 4.1 (two-stage search) over the HNSW structure of Section 2
+ *                   (beam >= 2: the batched form, several expansions per step):
  *                   rotation, ADC tables, greedy descent of the upper levels, best-first
  *                   search of level 0, shortlist, refinement with the regression codebook
  *                   (Section 4.3, reconstruction beta^T G(x)), exact L2 and top-k.
@@ -120,11 +121,82 @@ static void decode2(const orc_index *ix, const int *off1, const int *len1, const
             out[t] += (double)ix->C2[(int64_t)b[j] * ix->d + t];
 }
 
+/* Level-0 search in the batched form: each step takes the `beam` best unexpanded members of
+   W together, scores all their unvisited neighbours (a node shared by two rows is scored and
+   counted once), and keeps the ef' best of W and the new nodes.  With beam = 1 this expands
+   the same nodes in the same order as the best-first search of orc_search. */
+static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, int efp, int beam,
+                        char *visited, int32_t *touched, int *ntouch, double *wd, int32_t *wi,
+                        int32_t *n_dist, int32_t *n_expand, gap_rec *g)
+{
+    int cap = efp + beam * ix->deg + 1;
+    double *ad = malloc(sizeof(double) * cap);
+    int32_t *ai = malloc(sizeof(int32_t) * cap);
+    char *af = malloc((size_t)cap);
+    char *wf = calloc((size_t)efp + 1, 1);
+    int32_t *U = malloc(sizeof(int32_t) * (beam > 0 ? beam : 1));
+    int wn = 1;
+    wd[0] = adc(ix, lut, seed);
+    wi[0] = seed;
+    visited[seed] = 1;
+    touched[(*ntouch)++] = seed;
+    *n_dist = 1;
+    double od = INFINITY;              /* best scored node outside W */
+    int32_t oi = -1;
+    for (;;) {
+        int nu = 0;
+        for (int p = 0; p < wn && nu < beam; p++)
+            if (!wf[p]) U[nu++] = p;
+        if (nu == 0) break;
+        /* which members are taken is decided by the last one taken against the next
+           unexpanded member and against the best node outside W */
+        int last = U[nu - 1], next = -1;
+        for (int p = last + 1; p < wn; p++)
+            if (!wf[p]) { next = p; break; }
+        if (nu == beam && next >= 0) note_gap(g, wd[last], wi[last], wd[next], wi[next], 1);
+        if (oi >= 0) note_gap(g, wd[last], wi[last], od, oi, 1);
+        int an = 0;
+        for (int p = 0; p < wn; p++) { ad[an] = wd[p]; ai[an] = wi[p]; af[an] = wf[p]; an++; }
+        for (int u = 0; u < nu; u++) af[U[u]] = 1;
+        *n_expand += nu;
+        for (int u = 0; u < nu; u++) {
+            const int32_t *row = ix->adj0 + (int64_t)wi[U[u]] * ix->deg;
+            for (int s2 = 0; s2 < ix->deg; s2++) {
+                int32_t e = row[s2];
+                if (e < 0 || visited[e]) continue;
+                visited[e] = 1;
+                touched[(*ntouch)++] = e;
+                (*n_dist)++;
+                ad[an] = adc(ix, lut, e); ai[an] = e; af[an] = 0; an++;
+            }
+        }
+        /* order W and the new nodes by key (insertion sort) and keep the ef' best */
+        for (int x = 1; x < an; x++) {
+            double dx = ad[x]; int32_t ix2 = ai[x]; char fx = af[x];
+            int y = x;
+            while (y > 0 && key_less(dx, ix2, ad[y - 1], ai[y - 1])) {
+                ad[y] = ad[y - 1]; ai[y] = ai[y - 1]; af[y] = af[y - 1];
+                y--;
+            }
+            ad[y] = dx; ai[y] = ix2; af[y] = fx;
+        }
+        wn = an < efp ? an : efp;
+        if (an > efp && key_less(ad[efp], ai[efp], od, oi < 0 ? INT32_MAX : oi)) {
+            od = ad[efp]; oi = ai[efp];
+        }
+        for (int p = 0; p < wn; p++) { wd[p] = ad[p]; wi[p] = ai[p]; wf[p] = af[p]; }
+    }
+    /* termination: the best node outside W against the worst inside */
+    if (oi >= 0) note_gap(g, wd[wn - 1], wi[wn - 1], od, oi, 1);
+    free(ad); free(ai); free(af); free(wf); free(U);
+    return wn;
+}
+
 int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1,
                const float *C2, const uint8_t *codes1, const uint8_t *codes2,
                const uint8_t *beta, const float *B, int deg, const int32_t *adj0, int deg_up,
                const int32_t *upper_off, const int32_t *upper_adj, int32_t ep, int max_level,
-               int64_t nq, const float *Q, int k, int ef, int shortlist,
+               int64_t nq, const float *Q, int k, int ef, int shortlist, int beam,
                int32_t *ids, double *dists, int32_t *stats, double *min_gap,
                int32_t *w_ids, double *w_dists, int32_t *w_size)
 {
@@ -207,86 +279,91 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                 }
             }
 
-            /* Best-first search of level 0 from the seed, result set of size ef'. */
-            int64_t cn = 0;
-            double d0 = adc(&ix, lut, cur);
-            n_dist = 1;
-            visited[cur] = 1;
-            touched[ntouch++] = cur;
-            cd[cn] = d0; ci[cn] = cur; cn++;
-            wd[0] = d0; wi[0] = cur; wn = 1;
-            /* best node scored so far that is not in W (rejected or evicted); W is always
-               the ef' best scored nodes, so this is the (ef'+1)-th best */
-            double od0 = INFINITY;
-            int32_t oid = -1;
-            int ended_by_break = 0;
-            while (cn > 0) {
-                /* c = nearest element of C; its order against the runner-up decides
-                   which element is expanded first */
-                int64_t bc = 0, b2 = -1;
-                for (int64_t s = 1; s < cn; s++) {
-                    if (key_less(cd[s], ci[s], cd[bc], ci[bc])) { b2 = bc; bc = s; }
-                    else if (b2 < 0 || key_less(cd[s], ci[s], cd[b2], ci[b2])) b2 = s;
-                }
-                if (b2 >= 0) note_gap(&g, cd[bc], ci[bc], cd[b2], ci[b2], 1);
-                double dc = cd[bc];
-                int32_t c = ci[bc];
-                cd[bc] = cd[cn - 1]; ci[bc] = ci[cn - 1]; cn--;
-                /* f = furthest element of W */
-                int bf = 0;
-                for (int s = 1; s < wn; s++)
-                    if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
-                if (key_less(wd[bf], wi[bf], dc, c)) {                 /* c further than f */
-                    note_gap(&g, wd[bf], wi[bf], dc, c, 1);
-                    ended_by_break = 1;
-                    break;
-                }
-                /* c is expanded next: decided against the runner-up in C (above) and
-                   against the best node outside W */
-                if (oid >= 0) note_gap(&g, dc, c, od0, oid, 1);
-                n_expand++;
-                const int32_t *row = adj0 + (int64_t)c * deg;
-                for (int s = 0; s < deg; s++) {
-                    int32_t e = row[s];
-                    if (e < 0 || visited[e]) continue;
-                    visited[e] = 1;
-                    touched[ntouch++] = e;
-                    double de = adc(&ix, lut, e);
-                    n_dist++;
-                    bf = 0;
-                    for (int u = 1; u < wn; u++)
-                        if (key_less(wd[bf], wi[bf], wd[u], wi[u])) bf = u;
-                    int take = wn < efp || key_less(de, e, wd[bf], wi[bf]);
-                    if (!take && key_less(de, e, od0, oid < 0 ? INT32_MAX : oid)) {
-                        od0 = de; oid = e;
+            if (beam >= 2) {
+                wn = walk_batched(&ix, lut, cur, efp, beam, visited, touched, &ntouch, wd, wi,
+                                  &n_dist, &n_expand, &g);
+            } else {
+                /* Best-first search of level 0 from the seed, result set of size ef'. */
+                int64_t cn = 0;
+                double d0 = adc(&ix, lut, cur);
+                n_dist = 1;
+                visited[cur] = 1;
+                touched[ntouch++] = cur;
+                cd[cn] = d0; ci[cn] = cur; cn++;
+                wd[0] = d0; wi[0] = cur; wn = 1;
+                /* best node scored so far that is not in W (rejected or evicted); W is always
+                   the ef' best scored nodes, so this is the (ef'+1)-th best */
+                double od0 = INFINITY;
+                int32_t oid = -1;
+                int ended_by_break = 0;
+                while (cn > 0) {
+                    /* c = nearest element of C; its order against the runner-up decides
+                       which element is expanded first */
+                    int64_t bc = 0, b2 = -1;
+                    for (int64_t s = 1; s < cn; s++) {
+                        if (key_less(cd[s], ci[s], cd[bc], ci[bc])) { b2 = bc; bc = s; }
+                        else if (b2 < 0 || key_less(cd[s], ci[s], cd[b2], ci[b2])) b2 = s;
                     }
-                    if (take) {
-                        if (cn == cap) {
-                            cap *= 2;
-                            cd = realloc(cd, sizeof(double) * cap);
-                            ci = realloc(ci, sizeof(int32_t) * cap);
+                    if (b2 >= 0) note_gap(&g, cd[bc], ci[bc], cd[b2], ci[b2], 1);
+                    double dc = cd[bc];
+                    int32_t c = ci[bc];
+                    cd[bc] = cd[cn - 1]; ci[bc] = ci[cn - 1]; cn--;
+                    /* f = furthest element of W */
+                    int bf = 0;
+                    for (int s = 1; s < wn; s++)
+                        if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
+                    if (key_less(wd[bf], wi[bf], dc, c)) {                 /* c further than f */
+                        note_gap(&g, wd[bf], wi[bf], dc, c, 1);
+                        ended_by_break = 1;
+                        break;
+                    }
+                    /* c is expanded next: decided against the runner-up in C (above) and
+                       against the best node outside W */
+                    if (oid >= 0) note_gap(&g, dc, c, od0, oid, 1);
+                    n_expand++;
+                    const int32_t *row = adj0 + (int64_t)c * deg;
+                    for (int s = 0; s < deg; s++) {
+                        int32_t e = row[s];
+                        if (e < 0 || visited[e]) continue;
+                        visited[e] = 1;
+                        touched[ntouch++] = e;
+                        double de = adc(&ix, lut, e);
+                        n_dist++;
+                        bf = 0;
+                        for (int u = 1; u < wn; u++)
+                            if (key_less(wd[bf], wi[bf], wd[u], wi[u])) bf = u;
+                        int take = wn < efp || key_less(de, e, wd[bf], wi[bf]);
+                        if (!take && key_less(de, e, od0, oid < 0 ? INT32_MAX : oid)) {
+                            od0 = de; oid = e;
                         }
-                        cd[cn] = de; ci[cn] = e; cn++;
-                        wd[wn] = de; wi[wn] = e; wn++;
-                        if (wn > efp) {                      /* evict the furthest */
-                            int s1 = 0;
-                            for (int u = 1; u < wn; u++)
-                                if (key_less(wd[s1], wi[s1], wd[u], wi[u])) s1 = u;
-                            if (key_less(wd[s1], wi[s1], od0, oid < 0 ? INT32_MAX : oid)) {
-                                od0 = wd[s1]; oid = wi[s1];
+                        if (take) {
+                            if (cn == cap) {
+                                cap *= 2;
+                                cd = realloc(cd, sizeof(double) * cap);
+                                ci = realloc(ci, sizeof(int32_t) * cap);
                             }
-                            wd[s1] = wd[wn - 1]; wi[s1] = wi[wn - 1]; wn--;
+                            cd[cn] = de; ci[cn] = e; cn++;
+                            wd[wn] = de; wi[wn] = e; wn++;
+                            if (wn > efp) {                      /* evict the furthest */
+                                int s1 = 0;
+                                for (int u = 1; u < wn; u++)
+                                    if (key_less(wd[s1], wi[s1], wd[u], wi[u])) s1 = u;
+                                if (key_less(wd[s1], wi[s1], od0, oid < 0 ? INT32_MAX : oid)) {
+                                    od0 = wd[s1]; oid = wi[s1];
+                                }
+                                wd[s1] = wd[wn - 1]; wi[s1] = wi[wn - 1]; wn--;
+                            }
                         }
                     }
                 }
-            }
-            /* termination: had the best node outside W ranked inside it, the walk would
-               have continued */
-            if (!ended_by_break && oid >= 0) {
-                int bf = 0;
-                for (int s = 1; s < wn; s++)
-                    if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
-                note_gap(&g, wd[bf], wi[bf], od0, oid, 1);
+                /* termination: had the best node outside W ranked inside it, the walk would
+                   have continued */
+                if (!ended_by_break && oid >= 0) {
+                    int bf = 0;
+                    for (int s = 1; s < wn; s++)
+                        if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
+                    note_gap(&g, wd[bf], wi[bf], od0, oid, 1);
+                }
             }
             for (int s = 0; s < ntouch; s++) visited[touched[s]] = 0;
 

@@ -291,3 +291,65 @@ def test_knn_matches_scipy(rng):
     D = cdist(Q, X, "sqeuclidean")
     assert np.array_equal(ids, np.argsort(D, axis=1, kind="stable")[:, :5])
     np.testing.assert_allclose(ds, np.sort(D, axis=1)[:, :5], rtol=1e-12)
+
+
+def test_hand_traced_batched_walk():
+    # beam = 2, ef = 2.  Step 1: only 0 is unexpanded; scores 1 (13), 2 (10), 5 (32); W = {2, 1}.
+    # Step 2: expands 2 and 1 together: 4 (4) from 2's row, 3 (2) from 1's row; W = {3, 4}.
+    # Step 3: expands 3 and 4: every neighbour already visited.  Nothing unexpanded: stop.
+    # => 6 nodes scored, 5 expansions (the one-at-a-time walk stops after 4).
+    ix = tiny_index(CODES, ADJ)
+    r = oracle.search(ix, Q0, k=2, ef=2, shortlist=-1, return_w=True, beam=2)
+    assert r["w_ids"][0].tolist() == [3, 4]
+    assert r["stats"][0].tolist() == [6, 5, 0]
+
+
+def batched_walk(dist, adj, seed, ef, beam):
+    """The batched form restated: take the `beam` best unexpanded members of W, score their
+    unvisited neighbours, keep the ef best of everything scored."""
+    W = [(dist(seed), seed)]
+    expanded, visited = set(), {seed}
+    n_dist, n_exp = 1, 0
+    while True:
+        U = [w[1] for w in sorted(W) if w[1] not in expanded][:beam]
+        if not U:
+            break
+        expanded.update(U)
+        n_exp += len(U)
+        new = []
+        for c in U:
+            for e in adj[c]:
+                if e >= 0 and e not in visited:
+                    visited.add(e)
+                    n_dist += 1
+                    new.append((dist(e), e))
+        W = sorted(W + new)[:ef]
+    return sorted(W), n_dist, n_exp
+
+
+@pytest.mark.parametrize("beam", [2, 4, 8])
+@pytest.mark.parametrize("ef", [3, 16])
+def test_batched_form_matches_restatement(rng, beam, ef):
+    for trial in range(4):
+        ix = integer_index(rng, levels=False)
+        Q = rng.integers(-8, 9, size=(20, 4)).astype(np.float32)
+        r = oracle.search(ix, Q, k=1, ef=ef, shortlist=-1, return_w=True, beam=beam)
+        xh1 = ix.C1.astype(np.float64)[ix.codes1.astype(np.int64), np.arange(4)]
+        for q in range(20):
+            dist = lambda e: float(((Q[q] - xh1[e]) ** 2).sum())
+            W, nd, ne = batched_walk(dist, ix.adj0, ix.ep, ef, beam)
+            n = r["w_size"][q]
+            assert [w[1] for w in W] == r["w_ids"][q, :n].tolist()
+            assert (nd, ne) == tuple(r["stats"][q, :2])
+
+
+def test_batched_recall_close_to_plain(mix10k):
+    ix, xb, xq = mix10k
+    gt, _ = oracle.knn(xb, xq, 1)
+    p = oracle.search(ix, xq, k=10, ef=64)
+    b = oracle.search(ix, xq, k=10, ef=64, beam=4)
+    rp = (p["ids"][:, 0] == gt[:, 0]).mean()
+    rb = (b["ids"][:, 0] == gt[:, 0]).mean()
+    # the batched form expands a superset of useful nodes: recall does not drop
+    assert rb >= rp - 0.01
+    assert (b["stats"][:, 1] >= p["stats"][:, 1]).mean() > 0.9
