@@ -68,8 +68,12 @@ typedef struct {
 /* Fills *p with the defaults above for dimension d and code sizes M1, M2. */
 void lc_default_params(lc_params *p, int d, int M1, int M2);
 
-/* Search modes. */
-enum { LC_MODE_PLAIN = 0 };           /* exact best-first walk, one expansion at a time */
+/* Search modes.  PLAIN: the best-first walk of Section 2, one expansion at a time.
+ * BATCHED: each step expands the `beam` best unexpanded members of the result set together
+ * and merges all their new neighbours at once (a node shared by two of their rows is scored
+ * once); a deterministic variant with more work in flight per query, compared with PLAIN at
+ * equal recall (beam = 1 would be PLAIN). */
+enum { LC_MODE_PLAIN = 0, LC_MODE_BATCHED = 1 };
 /* Precision of the per-query ADC tables kept in shared memory. */
 enum { LC_LUT_FP32 = 0 };
 
@@ -81,11 +85,12 @@ typedef struct {
                         > 0: refine max(shortlist, k) (at most 256); < 0: no refinement,
                         return the walk's own top-k by ADC distance */
     int lut_prec;    /* LC_LUT_FP32 */
-    int mode;        /* LC_MODE_PLAIN */
+    int mode;        /* LC_MODE_PLAIN or LC_MODE_BATCHED */
     int visited_log; /* 0: automatic; 10..14: the per-query visited table in shared memory has
                         2^visited_log entries (ids beyond half of it go to a table in global
                         memory, 2^16 entries per query in flight; beyond half of that the
                         query fails with LC_ERR_CAPACITY) */
+    int beam;        /* LC_MODE_BATCHED: expansions per step, 2..8 (ignored in PLAIN mode) */
 } lc_search_params;
 
 void lc_default_search_params(lc_search_params *p, int k, int ef);

@@ -74,6 +74,7 @@ void lc_default_search_params(lc_search_params *p, int k, int ef)
     p->shortlist = 0;
     p->lut_prec = LC_LUT_FP32;
     p->mode = LC_MODE_PLAIN;
+    p->beam = 1;
 }
 
 lc_status lc_create(const lc_params *params, lc_index **out)
@@ -130,7 +131,11 @@ lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_pa
     if ((sp->ef > sp->k ? sp->ef : sp->k) > MAX_EF) { set_error("max(ef, k) exceeds %d", MAX_EF); return LC_ERR_ARG; }
     if (sp->shortlist > MAX_SHORTLIST) { set_error("shortlist exceeds %d", MAX_SHORTLIST); return LC_ERR_ARG; }
     if (sp->lut_prec != LC_LUT_FP32) { set_error("unsupported lut_prec %d", sp->lut_prec); return LC_ERR_ARG; }
-    if (sp->mode != LC_MODE_PLAIN) { set_error("unsupported mode %d", sp->mode); return LC_ERR_ARG; }
+    if (sp->mode != LC_MODE_PLAIN && sp->mode != LC_MODE_BATCHED) { set_error("unsupported mode %d", sp->mode); return LC_ERR_ARG; }
+    if (sp->mode == LC_MODE_BATCHED && (sp->beam < 2 || sp->beam > 8)) {
+        set_error("beam = %d outside 2..8 for the batched mode", sp->beam);
+        return LC_ERR_ARG;
+    }
     if (sp->visited_log != 0 && (sp->visited_log < 10 || sp->visited_log > 14)) {
         set_error("visited_log = %d outside 10..14", sp->visited_log);
         return LC_ERR_ARG;

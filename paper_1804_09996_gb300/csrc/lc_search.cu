@@ -103,6 +103,7 @@ struct WalkArgs {
     int efcap;        // efp rounded up to a multiple of 32
     int R;            // shortlist length (refine) or k (no refinement)
     int refine;
+    int beam;         // expansions per step (1: the plain walk)
     int hash_log;     // shared-memory visited table: 2^hash_log entries
     int spill_log;    // global spill table per warp: 2^spill_log entries
     int32_t *spill;
@@ -123,12 +124,12 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 // Shared memory of the walk kernel: the level-1 codebook C1 [256][d] once per CTA, then one
 // region per warp.
 struct WalkSmem {
-    size_t yq, stage, wkey, wflag, cand, cunsorted, slot, hash, total;
+    size_t yq, stage, wkey, wflag, cand, cunsorted, slot, rowbuf, hash, total;
 };
 
 __host__ __device__ inline size_t walk_c1_bytes(int d) { return align_up((size_t)256 * d * 4, 128); }
 
-__host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log)
+__host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log, int beam)
 {
     WalkSmem s;
     size_t o = 0;
@@ -136,9 +137,10 @@ __host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash
     s.stage = o;     o += (size_t)32 * M1;
     s.wkey = o;      o += (size_t)2 * efcap * 8;
     s.wflag = o;     o += align_up((size_t)2 * efcap, 16);
-    s.cand = o;      o += 32 * 8;
-    s.cunsorted = o; o += 32 * 8;
-    s.slot = o;      o += 32 * 4;
+    s.cand = o;      o += (size_t)32 * beam * 8;
+    s.cunsorted = o; o += (size_t)32 * beam * 8;
+    s.slot = o;      o += (size_t)32 * beam * 4;
+    s.rowbuf = o;    o += (size_t)32 * beam * 4;
     s.hash = o;      o += ((size_t)1 << hash_log) * 4;
     s.total = align_up(o, 128);
     return s;
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         for (int i = threadIdx.x; i < 256 * d / 4; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
-    const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log);
+    const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam);
     unsigned char *base = smem_raw + walk_c1_bytes(d) + (size_t)warp * L.total;
     float *yq = reinterpret_cast<float *>(base + L.yq);
     uint8_t *stage = base + L.stage;
@@ -361,6 +363,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
     uint64_t *cand = reinterpret_cast<uint64_t *>(base + L.cand);
     uint64_t *cuns = reinterpret_cast<uint64_t *>(base + L.cunsorted);
     int32_t *slot = reinterpret_cast<int32_t *>(base + L.slot);
+    int32_t *rowbuf = reinterpret_cast<int32_t *>(base + L.rowbuf);
     int32_t *hash = reinterpret_cast<int32_t *>(base + L.hash);
     const int H = 1 << a.hash_log;
     const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -434,53 +437,76 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         int32_t hcount = 1, scount = 0;
         __syncwarp();
         int scan_from = 0;
+        const int B = a.beam;                // expansions per step; 1 = the plain walk
         for (;;) {
             uint64_t *W = wkey + buf * a.efcap;
             uint8_t *F = wflag + buf * a.efcap;
-            int pos = -1;
-            for (int b0 = scan_from; b0 < wn; b0 += 32) {
-                int p = b0 + lane;
-                bool un = p < wn && !F[p];
-                unsigned m = __ballot_sync(FULL, un);
-                if (m) { pos = b0 + __ffs(m) - 1; break; }
+            // the B best unexpanded members of W: lane i < nb holds the i-th one's position
+            int nb = 0, my_pos = -1;
+            for (int b0 = scan_from; b0 < wn && nb < B; b0 += 32) {
+                const int p = b0 + lane;
+                unsigned m = __ballot_sync(FULL, p < wn && !F[p]);
+                while (m && nb < B) {
+                    if (lane == nb) my_pos = b0 + __ffs(m) - 1;
+                    nb++;
+                    m &= m - 1;
+                }
             }
-            if (pos < 0) break;
-            uint64_t ckey = W[pos];
+            if (nb == 0) break;
+            const int pos0 = __shfl_sync(FULL, my_pos, 0);
+            const uint64_t ckey0 = W[pos0];
+            const int32_t my_c = lane < nb ? key_id(W[my_pos]) : -1;
             __syncwarp();
-            if (lane == 0) F[pos] = 1;
-            __syncwarp();
-            n_expand++;
-            int32_t c = key_id(ckey);
-            int32_t e = a.adj0[(int64_t)c * DEG + lane];
-            // switch to the global table before the shared one passes half full
-            if (!spilled && hcount + 32 > H / 2) {
-                spilled = true;
-                for (int i = lane; i < (1 << a.spill_log); i += 32) spill[i] = -1;
-                __syncwarp();
+            if (lane < nb) F[my_pos] = 1;
+            n_expand += nb;
+            // their adjacency rows, all loads in flight together
+            for (int r = 0; r < nb; r++) {
+                const int32_t cr = __shfl_sync(FULL, my_c, r);
+                rowbuf[r * DEG + lane] = a.adj0[(int64_t)cr * DEG + lane];
             }
-            if (spilled && scount + 32 > (1 << a.spill_log) / 2) {
-                failed = true;
-                break;
-            }
-            bool fresh = e >= 0 && visit(e, hash, a.hash_log, spilled, spill, a.spill_log);
-            unsigned fm = __ballot_sync(FULL, fresh);
-            int nf = __popc(fm);
-            n_dist += nf;
-            if (spilled) scount += nf; else hcount += nf;
-            if (nf == 0) { scan_from = pos; continue; }
-            if (fresh) slot[__popc(fm & lt_mask)] = e;
             __syncwarp();
-            float de = score_nodes<M1, D1>(C1s, stage, a.codes1, slot, nf, d, g, lane, &my_slot);
-            uint64_t k = my_slot < nf ? make_key(de, slot[my_slot]) : ~0ull;
-            if (wn == a.efp && k >= W[wn - 1]) k = ~0ull;      // cannot enter W
-            unsigned km = __ballot_sync(FULL, k != ~0ull);
-            int nc = __popc(km);
-            if (nc == 0) { scan_from = pos; continue; }
+            // visited test row by row (row order, then slot order); fresh nodes are appended
+            int ns = 0;
+            for (int r = 0; r < nb; r++) {
+                // switch to the global table before the shared one passes half full
+                if (!spilled && hcount + 32 > H / 2) {
+                    spilled = true;
+                    for (int i = lane; i < (1 << a.spill_log); i += 32) spill[i] = -1;
+                    __syncwarp();
+                }
+                if (spilled && scount + 32 > (1 << a.spill_log) / 2) {
+                    failed = true;
+                    break;
+                }
+                const int32_t e = rowbuf[r * DEG + lane];
+                const bool fresh = e >= 0 && visit(e, hash, a.hash_log, spilled, spill, a.spill_log);
+                const unsigned fm = __ballot_sync(FULL, fresh);
+                if (fresh) slot[ns + __popc(fm & lt_mask)] = e;
+                const int nf = __popc(fm);
+                ns += nf;
+                n_dist += nf;
+                if (spilled) scount += nf; else hcount += nf;
+            }
+            if (failed) break;
+            __syncwarp();
+            if (ns == 0) { scan_from = pos0; continue; }
+            // score the fresh nodes 32 at a time; keep those that can enter W
+            const uint64_t wmax = wn == a.efp ? W[wn - 1] : ~0ull;
+            int nc = 0;
+            for (int ch = 0; ch < ns; ch += 32) {
+                const int nf = min(32, ns - ch);
+                const float de = score_nodes<M1, D1>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot);
+                uint64_t k = my_slot < nf ? make_key(de, slot[ch + my_slot]) : ~0ull;
+                if (k >= wmax) k = ~0ull;
+                const unsigned km = __ballot_sync(FULL, k != ~0ull);
+                if (k != ~0ull) cuns[nc + __popc(km & lt_mask)] = k;
+                nc += __popc(km);
+            }
+            __syncwarp();
+            if (nc == 0) { scan_from = pos0; continue; }
             // order the candidates by rank (keys are distinct)
-            if (k != ~0ull) cuns[__popc(km & lt_mask)] = k;
-            __syncwarp();
-            if (lane < nc) {
-                uint64_t mk = cuns[lane];
+            for (int m0 = lane; m0 < nc; m0 += 32) {
+                const uint64_t mk = cuns[m0];
                 int r = 0;
                 for (int m = 0; m < nc; m++) r += cuns[m] < mk;
                 cand[r] = mk;
@@ -489,34 +515,35 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             // merge W (wn keys) with the nc candidates into the other buffer, keep efp
             uint64_t *W2 = wkey + (buf ^ 1) * a.efcap;
             uint8_t *F2 = wflag + (buf ^ 1) * a.efcap;
-            int wn2 = min(a.efp, wn + nc);
+            const int wn2 = min(a.efp, wn + nc);
             for (int p = lane; p < wn; p += 32) {
-                uint64_t key = W[p];
+                const uint64_t key = W[p];
                 int lo = 0, hi = nc;                     // candidates below key
                 while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
+                    const int mid = (lo + hi) >> 1;
                     if (cand[mid] < key) lo = mid + 1; else hi = mid;
                 }
-                int np = p + lo;
+                const int np = p + lo;
                 if (np < wn2) { W2[np] = key; F2[np] = F[p]; }
             }
             int first_new = a.efp;
-            if (lane < nc) {
-                uint64_t ck = cand[lane];
+            for (int m0 = lane; m0 < nc; m0 += 32) {
+                const uint64_t ck = cand[m0];
                 int lo = 0, hi = wn;                     // W members below the candidate
                 while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
+                    const int mid = (lo + hi) >> 1;
                     if (W[mid] < ck) lo = mid + 1; else hi = mid;
                 }
-                int np = lane + lo;
+                const int np = m0 + lo;
                 if (np < wn2) { W2[np] = ck; F2[np] = 0; }
-                first_new = np;
+                if (m0 == 0) first_new = np;
             }
             first_new = __shfl_sync(FULL, first_new, 0);
-            // everything before min(first new candidate, expanded node's new place) is expanded
+            // everything before min(first new candidate, first expanded node's new place) is
+            // expanded
             int below = 0;
-            for (int m = 0; m < nc; m++) below += cand[m] < ckey;
-            scan_from = min(first_new, pos + below);
+            for (int m = 0; m < nc; m++) below += cand[m] < ckey0;
+            scan_from = min(first_new, pos0 + below);
             scan_from -= scan_from % 32;
             wn = wn2;
             buf ^= 1;
@@ -928,6 +955,7 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
     wa.ep = dv->ep; wa.max_level = dv->max_level;
     wa.efp = efp; wa.efcap = (int)align_up(efp, 32);
     wa.R = R; wa.refine = refine ? 1 : 0;
+    wa.beam = sp->mode == LC_MODE_BATCHED ? sp->beam : 1;
     wa.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));
     wa.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)efp * 64)));
     wa.status = dv->status;
@@ -935,7 +963,7 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
     std::vector<int> off, len;
     splits(dv->d, dv->M1, off, len);
     for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
-    size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log).total;
+    size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log, wa.beam).total;
     int grid = 0, wpb = 1;
     size_t smem = 0;
     cudaError_t ce;
@@ -1151,6 +1179,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     wa.ep = dv->ep; wa.max_level = dv->max_level;
     wa.efp = efp; wa.efcap = (int)align_up(efp, 32);
     wa.R = k; wa.refine = 0;
+    wa.beam = 1;
     wa.hash_log = std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));
     wa.spill_log = NOALLOC_SPILL_LOG;
     wa.ids_out = ids; wa.dists_out = dists; wa.stats_out = stats;
@@ -1160,7 +1189,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     std::vector<int> off, len;
     splits(dv->d, dv->M1, off, len);
     for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
-    const size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log).total;
+    const size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log, wa.beam).total;
     const int variant = (dv->M1 == 16 && dv->d == 96) ? 1 : (dv->M1 == 32 && dv->d == 96) ? 2
                       : (dv->M1 == 64 && dv->d == 128) ? 3 : 0;
     int grid = 0, wpc = 1;

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblc.so")
 
 LC_OK, LC_ERR_ARG, LC_ERR_OOM, LC_ERR_STATE, LC_ERR_CUDA = 0, 1, 2, 3, 4
 LC_ERR_TIMEOUT, LC_ERR_BUDGET, LC_ERR_IO, LC_ERR_CAPACITY = 5, 6, 7, 8
-LC_MODE_PLAIN = 0
+LC_MODE_PLAIN, LC_MODE_BATCHED = 0, 1
 LC_LUT_FP32 = 0
 
 EXPORTED = [
@@ -40,7 +40,7 @@ class lc_params(ctypes.Structure):
 
 
 class lc_search_params(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log")]
+    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam")]
 
 
 _lib = None

@@ -38,10 +38,12 @@ def handle(name, ix):
     return _handles[name]
 
 
-def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0):
+def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1):
     import torch
     nq = len(xq)
     sp = lc.lc_default_search_params(k, ef, shortlist=shortlist, visited_log=visited_log)
+    if beam > 1:
+        sp.mode, sp.beam = lc.LC_MODE_BATCHED, beam
     if device:
         q = torch.from_numpy(np.ascontiguousarray(xq, np.float32)).cuda()
         ids = torch.full((nq, k), -7, dtype=torch.int32, device="cuda")
@@ -91,6 +93,24 @@ def test_parity_64_and_128_byte_codes(request, name, ef):
     compare(ref, *gpu_search(h, xq, 10, ef), max_exempt=0.1)
     ref = oracle.search(ix, xq, 10, ef, shortlist=-1)
     compare(ref, *gpu_search(h, xq, 10, ef, shortlist=-1), max_exempt=0.1)
+
+
+@pytest.mark.parametrize("beam", [2, 4, 8])
+@pytest.mark.parametrize("name", ["mix3k", "opq3k", "sift2k"])
+def test_parity_batched(request, name, beam):
+    # the batched form (beam best unexpanded members per step) against the oracle's
+    ix, xb, xq = request.getfixturevalue(name)
+    h = handle(name, ix)
+    for shortlist in (0, -1):
+        ref = oracle.search(ix, xq, 10, 64, shortlist=shortlist, beam=beam)
+        compare(ref, *gpu_search(h, xq, 10, 64, shortlist, beam=beam), max_exempt=0.1)
+
+
+def test_batched_spill_and_wide(mix3k):
+    ix, xb, xq = mix3k
+    h = handle("mix3k", ix)
+    ref = oracle.search(ix, xq, 10, 256, beam=4)
+    compare(ref, *gpu_search(h, xq, 10, 256, visited_log=10, beam=4), max_exempt=0.3)
 
 
 def test_parity_10k_workload(mix10k):
