@@ -73,14 +73,15 @@ def kernel_hash():
     return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per walk launch from the committed ncu summary, if it was taken on the
-    current kernel source (its 'kernel_source_sha256_16' line must match)."""
+def profiled_traffic(workload: str, form: str):
+    """DRAM bytes per walk launch of the given form ('plain' or 'batched') from the committed
+    ncu summary, if it was taken on the current kernel source (its 'kernel_source_sha256_16'
+    line must match)."""
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         txt = open(f).read()
         m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
         w = re.search(r"workload:\s*(\S+)", txt)
-        t = re.search(r"dram_bytes_per_walk_launch:\s*([0-9.eE+]+)", txt)
+        t = re.search(r"dram_bytes_per_walk_launch_" + form + r":\s*([0-9.eE+]+)", txt)
         if m and w and t and w.group(1) == workload and m.group(1) == kernel_hash():
             return float(t.group(1))
     return None
@@ -364,7 +365,7 @@ def main():
     walk_s = best["walk_ms"] / 1e3
     peak, peak_src = peaks()
     achieved = b_walk / walk_s / 1e9
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled_traffic(args.workload, "plain" if best_name == "plain" else "batched")
 
     # e2e through the same C ABI call with pinned host buffers
     hq = torch.from_numpy(xq).pin_memory()
