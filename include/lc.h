@@ -182,6 +182,47 @@ lc_status lc_load(const char *path, lc_index **out);
 lc_status lc_search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef,
                                  int32_t *ids, float *dists, int32_t *stats, void *stream);
 
+/* ---- Serving: continuous batching of requests on one GPU (the paper has no serving
+ * component; this is the library's own).  The index stays resident; each request (a batch of
+ * 1..max_request host queries with its own k, efSearch, shortlist and mode) needs device state
+ * for its queries, results and search scratch, sub-allocated from one arena of
+ * device_budget_bytes created at open.  Requests start in arrival order as soon as a stream
+ * slot (max_inflight of them) and room in the budget are free, so requests that arrive while
+ * others are on the GPU start alongside them and their kernels overlap.  Results are exactly
+ * those of lc_search with the same parameters.  A server is driven by one host thread:
+ * submit, poll and close from the same thread. */
+typedef struct lc_server lc_server;
+
+/* Completion callback, invoked from lc_serve_poll or lc_serve_close on the calling thread.
+ * status LC_OK: ids/dists hold [nq][k] results (as lc_search), valid only during the call.
+ * Otherwise ids/dists must not be read: LC_ERR_CAPACITY (a query's visited set overflowed),
+ * LC_ERR_CUDA, or LC_ERR_STATE (cancelled by lc_serve_close before it started). */
+typedef void (*lc_request_cb)(void *user, uint64_t req_id, lc_status status, const int32_t *ids,
+                              const float *dists, int32_t nq, int32_t k);
+
+/* Opens a server on the index's device (uploads the index if needed).  Errors: LC_ERR_ARG,
+ * LC_ERR_STATE (untrained or empty index), LC_ERR_OOM (budget or staging allocation),
+ * LC_ERR_CUDA. */
+lc_status lc_serve_open(lc_index *ix, size_t device_budget_bytes, int max_inflight, int max_request,
+                        lc_server **out);
+
+/* Queues a request (host queries q [nq][d], copied before returning) and starts it if it can
+ * start now; never waits for the device.  *req_id (may be NULL) receives its id (increasing).
+ * Errors: LC_ERR_ARG (as lc_search), LC_ERR_BUDGET (more than max_request queries, or more
+ * device state than the whole budget: it could never be admitted), LC_ERR_CAPACITY, LC_ERR_OOM. */
+lc_status lc_serve_submit(lc_server *s, const float *q, int32_t nq, const lc_search_params *sp,
+                          lc_request_cb cb, void *user, uint64_t *req_id);
+
+/* Delivers completed requests (callbacks), then starts queued ones that now fit.  Waits up to
+ * timeout_ms for at least one completion while requests are in flight (0: do not wait).
+ * *n_completed (may be NULL) receives the number delivered.  Errors: LC_ERR_ARG, LC_ERR_CUDA
+ * (a request failed on the device; its callback received LC_ERR_CUDA). */
+lc_status lc_serve_poll(lc_server *s, int timeout_ms, int *n_completed);
+
+/* Cancels queued requests (callback status LC_ERR_STATE), waits for and delivers those on the
+ * device, and frees the server (NULL is a no-op). */
+lc_status lc_serve_close(lc_server *s);
+
 /* Kernel timing: after lc_profile(ix, 1) every lc_search records CUDA events on its stream
  * around the walk kernel and the refinement kernel; lc_profile_read waits for the last
  * profiled search and returns the two durations in milliseconds (refine_ms = 0 without

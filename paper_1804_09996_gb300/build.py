@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU = ["lc_search.cu"]
-CPP = ["lc_capi.cpp", "lc_build.cpp"]
+CPP = ["lc_capi.cpp", "lc_build.cpp", "lc_serve.cpp"]
 
 
 def _nvcc() -> str:
@@ -51,7 +51,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
             cmd = [nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xptxas", "-v",
                    "-c", src, "-o", obj]
         else:
-            cmd = ["g++", "-std=c++17", "-O3", "-fPIC", "-pthread", "-Wall", "-c", src, "-o", obj]
+            cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+            cmd = ["g++", "-std=c++17", "-O3", "-fPIC", "-pthread", "-Wall", "-I", cuda_inc, "-c", src, "-o", obj]
         jobs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
     failed = []
     for cmd, pr in jobs:

@@ -38,6 +38,25 @@ static lc_status check_params(const lc_params *p)
     return LC_OK;
 }
 
+lc_status check_search_params(const lc_search_params *sp)
+{
+    if (sp->k < 1 || sp->k > MAX_K) { set_error("k = %d outside 1..%d", sp->k, MAX_K); return LC_ERR_ARG; }
+    if (sp->ef < 1) { set_error("ef must be >= 1"); return LC_ERR_ARG; }
+    if ((sp->ef > sp->k ? sp->ef : sp->k) > MAX_EF) { set_error("max(ef, k) exceeds %d", MAX_EF); return LC_ERR_ARG; }
+    if (sp->shortlist > MAX_SHORTLIST) { set_error("shortlist exceeds %d", MAX_SHORTLIST); return LC_ERR_ARG; }
+    if (sp->lut_prec != LC_LUT_FP32) { set_error("unsupported lut_prec %d", sp->lut_prec); return LC_ERR_ARG; }
+    if (sp->mode != LC_MODE_PLAIN && sp->mode != LC_MODE_BATCHED) { set_error("unsupported mode %d", sp->mode); return LC_ERR_ARG; }
+    if (sp->mode == LC_MODE_BATCHED && (sp->beam < 2 || sp->beam > 8)) {
+        set_error("beam = %d outside 2..8 for the batched mode", sp->beam);
+        return LC_ERR_ARG;
+    }
+    if (sp->visited_log != 0 && (sp->visited_log < 10 || sp->visited_log > 14)) {
+        set_error("visited_log = %d outside 10..14", sp->visited_log);
+        return LC_ERR_ARG;
+    }
+    return LC_OK;
+}
+
 }  // namespace lc
 
 using namespace lc;
@@ -126,20 +145,8 @@ lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_pa
     set_error("");
     if (!ix || !sp) { set_error("null index or search parameters"); return LC_ERR_ARG; }
     if (nq < 0 || (nq > 0 && (!q || !ids || !dists))) { set_error("null query or output buffer"); return LC_ERR_ARG; }
-    if (sp->k < 1 || sp->k > MAX_K) { set_error("k = %d outside 1..%d", sp->k, MAX_K); return LC_ERR_ARG; }
-    if (sp->ef < 1) { set_error("ef must be >= 1"); return LC_ERR_ARG; }
-    if ((sp->ef > sp->k ? sp->ef : sp->k) > MAX_EF) { set_error("max(ef, k) exceeds %d", MAX_EF); return LC_ERR_ARG; }
-    if (sp->shortlist > MAX_SHORTLIST) { set_error("shortlist exceeds %d", MAX_SHORTLIST); return LC_ERR_ARG; }
-    if (sp->lut_prec != LC_LUT_FP32) { set_error("unsupported lut_prec %d", sp->lut_prec); return LC_ERR_ARG; }
-    if (sp->mode != LC_MODE_PLAIN && sp->mode != LC_MODE_BATCHED) { set_error("unsupported mode %d", sp->mode); return LC_ERR_ARG; }
-    if (sp->mode == LC_MODE_BATCHED && (sp->beam < 2 || sp->beam > 8)) {
-        set_error("beam = %d outside 2..8 for the batched mode", sp->beam);
-        return LC_ERR_ARG;
-    }
-    if (sp->visited_log != 0 && (sp->visited_log < 10 || sp->visited_log > 14)) {
-        set_error("visited_log = %d outside 10..14", sp->visited_log);
-        return LC_ERR_ARG;
-    }
+    lc_status cs = check_search_params(sp);
+    if (cs != LC_OK) return cs;
     if (!ix->trained) { set_error("search before lc_train/lc_import"); return LC_ERR_STATE; }
     if (ix->n > 0 && !ix->has_codebook) { set_error("index has no regression codebook"); return LC_ERR_STATE; }
     try {

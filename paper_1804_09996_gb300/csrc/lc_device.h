@@ -1,0 +1,64 @@
+// Host-side view of the device index and of one search's launch plan and scratch, shared by
+// the search (lc_search.cu) and the request server (lc_serve.cpp).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lc_internal.h"
+
+namespace lc {
+
+struct DeviceIndex {
+    int device = -1;
+    int64_t n = 0;
+    int d = 0, M1 = 0, M2 = 0, max_level = 0;
+    int32_t ep = -1;
+    float *Rt = nullptr;          // [d][d], Rt[u*d + t] = R[t][u]
+    float *C1 = nullptr, *C2 = nullptr, *B = nullptr;
+    uint8_t *codes1 = nullptr, *codes2b = nullptr;   // codes2b: residual codes padded to M2P bytes, codeword id last
+    int M2P = 0;
+    int32_t *adj0 = nullptr, *upper_off = nullptr, *upper_adj = nullptr;
+    // scratch of lc_search, grown on demand
+    float *yq = nullptr; size_t yq_cap = 0;
+    int32_t *shortlist = nullptr; size_t sl_cap = 0;
+    int32_t *spill = nullptr; size_t spill_cap = 0;
+    int32_t *status = nullptr;
+    unsigned long long *counter = nullptr;
+    // staging for host-pointer calls
+    float *q_st = nullptr; size_t q_cap = 0;
+    int32_t *ids_st = nullptr; float *d_st = nullptr; int32_t *s_st = nullptr; size_t out_cap = 0;
+    // profiling
+    bool profile = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ev_valid = false, has_refine = false;
+    int num_sms = 0;
+};
+
+// Launch configuration of one search and the scratch it needs.
+struct SearchPlan {
+    int k = 0, efp = 0, R = 0, beam = 1, hash_log = 0, spill_log = 0, variant = 0;
+    bool refine = false;
+    int wpc = 0, grid = 0;               // walk: warps per CTA, CTAs
+    size_t per_warp = 0, smem = 0;
+    int rw = 0, rgrid = 0;               // refine: warps per CTA, CTAs
+    size_t rsm = 0;
+    bool rboth = false;                  // both codebooks in shared memory
+    size_t yq_elems = 0, sl_elems = 0, spill_elems = 0;
+};
+
+// Device scratch of one search in flight.
+struct SearchScratch {
+    float *yq = nullptr;                 // [nq][d] (refinement only)
+    int32_t *shortlist = nullptr;        // [nq][R] (refinement only)
+    int32_t *spill = nullptr;            // [grid * wpc][2^spill_log]
+    int32_t *status = nullptr;           // 1 word
+    unsigned long long *counter = nullptr;
+};
+
+lc_status upload(lc_index *ix);
+lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl);
+// Queues the walk (and refinement) on `st`; q, ids, dists, stats are device pointers.
+lc_status run_search(DeviceIndex *dv, const SearchPlan &pl, const float *q, int64_t nq, int32_t *ids,
+                     float *dists, int32_t *stats, const SearchScratch &sc, cudaStream_t st, bool profile);
+
+}  // namespace lc

@@ -19,6 +19,7 @@ constexpr int MAX_K = 256;
 constexpr int MAX_SHORTLIST = 256;
 
 void set_error(const char *fmt, ...);
+lc_status check_search_params(const lc_search_params *sp);   // argument checks of lc_search
 
 // Sub-space split: M contiguous blocks, the first (d mod M) of ceil(d/M) dimensions.
 void splits(int d, int M, std::vector<int> &off, std::vector<int> &len);

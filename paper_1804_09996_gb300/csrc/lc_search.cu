@@ -33,37 +33,11 @@
 #include <cstring>
 #include <mutex>
 
-#include "lc_internal.h"
+#include "lc_device.h"
 
 namespace lc {
 
 #define FULL 0xffffffffu
-
-struct DeviceIndex {
-    int device = -1;
-    int64_t n = 0;
-    int d = 0, M1 = 0, M2 = 0, max_level = 0;
-    int32_t ep = -1;
-    float *Rt = nullptr;          // [d][d], Rt[u*d + t] = R[t][u]
-    float *C1 = nullptr, *C2 = nullptr, *B = nullptr;
-    uint8_t *codes1 = nullptr, *codes2b = nullptr;   // codes2b: residual codes padded to M2P bytes, codeword id last
-    int M2P = 0;
-    int32_t *adj0 = nullptr, *upper_off = nullptr, *upper_adj = nullptr;
-    // scratch, grown on demand
-    float *yq = nullptr; size_t yq_cap = 0;
-    int32_t *shortlist = nullptr; size_t sl_cap = 0;
-    int32_t *spill = nullptr; size_t spill_cap = 0;
-    int32_t *status = nullptr;
-    unsigned long long *counter = nullptr;
-    // staging for host-pointer calls
-    float *q_st = nullptr; size_t q_cap = 0;
-    int32_t *ids_st = nullptr; float *d_st = nullptr; int32_t *s_st = nullptr; size_t out_cap = 0;
-    // profiling
-    bool profile = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    bool ev_valid = false, has_refine = false;
-    int num_sms = 0;
-};
 
 static void cfree(void *p) { if (p) cudaFree(p); }
 
@@ -784,7 +758,7 @@ static bool grow(T *&p, size_t &cap, size_t need)
     return true;
 }
 
-static lc_status upload(lc_index *ix)
+lc_status upload(lc_index *ix)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -858,7 +832,10 @@ static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num
     if (c1 + smem_per_warp > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
     int wpc = (int)std::min<size_t>(MAX_WALK_WARPS, (MAX_SMEM_PER_BLOCK - c1) / smem_per_warp);
     size_t smem = c1 + smem_per_warp * wpc;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the attribute is an upper bound: set to the maximum, so plans made in any order (the
+    // server plans at submission and launches later) all remain launchable
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)MAX_SMEM_PER_BLOCK);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1>, wpc * 32, smem);
@@ -878,17 +855,160 @@ static cudaError_t run_walk(const WalkArgs &wa, size_t smem, int wpc, int grid, 
     return cudaGetLastError();
 }
 
+lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl)
+{
+    SearchPlan P;
+    P.k = sp->k;
+    P.efp = std::max(sp->ef, sp->k);
+    P.refine = sp->shortlist >= 0;
+    P.R = P.refine ? std::max(sp->shortlist > 0 ? sp->shortlist : 10, P.k) : P.k;
+    if (P.refine && P.R > MAX_SHORTLIST) {
+        set_error("shortlist %d exceeds %d", P.R, MAX_SHORTLIST);
+        return LC_ERR_ARG;
+    }
+    P.beam = sp->mode == LC_MODE_BATCHED ? sp->beam : 1;
+    P.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)P.efp * 32)));
+    P.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)P.efp * 64)));
+    const int efcap = (int)align_up(P.efp, 32);
+    P.per_warp = walk_smem(dv->M1, dv->d, efcap, P.hash_log, P.beam).total;
+    // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
+    P.variant = (dv->M1 == 16 && dv->d == 96) ? 1 : (dv->M1 == 32 && dv->d == 96) ? 2
+              : (dv->M1 == 64 && dv->d == 128) ? 3 : 0;
+    WalkArgs wa{};
+    wa.nq = nq;
+    wa.d = dv->d;
+    cudaError_t ce;
+    switch (P.variant) {
+    case 1: ce = launch_walk<16, 6>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem); break;
+    case 2: ce = launch_walk<32, 3>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem); break;
+    case 3: ce = launch_walk<64, 2>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem); break;
+    default:
+        if (dv->M1 == 16) ce = launch_walk<16, 0>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
+        else if (dv->M1 == 32) ce = launch_walk<32, 0>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
+        else ce = launch_walk<64, 0>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
+    }
+    if (ce == cudaErrorInvalidConfiguration) {
+        set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
+                  "lower efSearch or visited_log", P.per_warp, walk_c1_bytes(dv->d));
+        return LC_ERR_CAPACITY;
+    }
+    if (ce != cudaSuccess) {
+        set_error("walk kernel configuration failed (%zu B shared memory per warp): %s", P.per_warp,
+                  cudaGetErrorString(ce));
+        return LC_ERR_CUDA;
+    }
+    P.spill_elems = ((size_t)P.grid * P.wpc) << P.spill_log;
+    if (P.refine) {
+        P.yq_elems = (size_t)nq * dv->d;
+        P.sl_elems = (size_t)nq * P.R;
+        const size_t per = refine_smem(dv->M1, dv->M2P, P.R);
+        const size_t cbytes = (size_t)256 * dv->d * 4;
+        // both codebooks in shared memory when that leaves room for at least 4 warps
+        P.rboth = 2 * cbytes + 4 * per <= MAX_SMEM_PER_BLOCK;
+        const size_t cb = (P.rboth ? 2 : 1) * cbytes;
+        if (cb + per > MAX_SMEM_PER_BLOCK) {
+            set_error("refinement does not fit in shared memory (d = %d)", dv->d);
+            return LC_ERR_CAPACITY;
+        }
+        P.rw = (int)std::min<size_t>(16, (MAX_SMEM_PER_BLOCK - cb) / per);
+        P.rsm = cb + per * P.rw;
+        auto kern = P.rboth ? refine_kernel<true> : refine_kernel<false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM_PER_BLOCK) != cudaSuccess) {
+            set_error("refine kernel configuration failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return LC_ERR_CUDA;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P.rw * 32, P.rsm);
+        const int64_t need = (nq + P.rw - 1) / P.rw;
+        P.rgrid = (int)std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * dv->num_sms);
+    }
+    *pl = P;
+    return LC_OK;
+}
+
+lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int64_t nq, int32_t *dids,
+                     float *ddists, int32_t *dstats, const SearchScratch &sc, cudaStream_t st, bool profile)
+{
+    WalkArgs wa{};
+    wa.Q = dq; wa.nq = nq; wa.d = dv->d;
+    wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.codes1 = dv->codes1;
+    wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
+    wa.ep = dv->ep; wa.max_level = dv->max_level;
+    wa.efp = P.efp; wa.efcap = (int)align_up(P.efp, 32);
+    wa.R = P.R; wa.refine = P.refine ? 1 : 0;
+    wa.beam = P.beam;
+    wa.hash_log = P.hash_log;
+    wa.spill_log = P.spill_log;
+    wa.spill = sc.spill;
+    wa.status = sc.status;
+    wa.counter = sc.counter;
+    wa.stats_out = dstats;
+    if (P.refine) {
+        wa.yq_out = sc.yq;
+        wa.short_out = sc.shortlist;
+    } else {
+        wa.ids_out = dids;
+        wa.dists_out = ddists;
+    }
+    std::vector<int> off, len;
+    splits(dv->d, dv->M1, off, len);
+    for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
+    if (cudaMemsetAsync(sc.status, 0, sizeof(int32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(sc.counter, 0, sizeof(unsigned long long), st) != cudaSuccess) {
+        set_error("status reset failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return LC_ERR_CUDA;
+    }
+    if (profile) {
+        for (auto &e : dv->ev)
+            if (!e) cudaEventCreate(&e);
+        cudaEventRecord(dv->ev[0], st);
+    }
+    cudaError_t ce;
+    switch (P.variant) {
+    case 1: ce = run_walk<16, 6>(wa, P.smem, P.wpc, P.grid, st); break;
+    case 2: ce = run_walk<32, 3>(wa, P.smem, P.wpc, P.grid, st); break;
+    case 3: ce = run_walk<64, 2>(wa, P.smem, P.wpc, P.grid, st); break;
+    default:
+        if (dv->M1 == 16) ce = run_walk<16, 0>(wa, P.smem, P.wpc, P.grid, st);
+        else if (dv->M1 == 32) ce = run_walk<32, 0>(wa, P.smem, P.wpc, P.grid, st);
+        else ce = run_walk<64, 0>(wa, P.smem, P.wpc, P.grid, st);
+    }
+    if (profile) cudaEventRecord(dv->ev[1], st);
+    if (ce != cudaSuccess) {
+        set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
+        return LC_ERR_CUDA;
+    }
+    if (P.refine) {
+        RefineArgs ra{};
+        ra.yq = sc.yq; ra.shortlist = sc.shortlist; ra.nq = nq; ra.R = P.R; ra.k = P.k; ra.d = dv->d;
+        ra.M1 = dv->M1; ra.M2P = dv->M2P; ra.C1 = dv->C1; ra.C2 = dv->C2; ra.B = dv->B;
+        ra.codes1 = dv->codes1; ra.codes2b = dv->codes2b; ra.adj0 = dv->adj0;
+        ra.ids_out = dids; ra.dists_out = ddists;
+        std::vector<int> o2, l2;
+        splits(dv->d, dv->M2, o2, l2);
+        for (int j = 0; j < dv->M1; j++) for (int t = off[j]; t < off[j] + len[j]; t++) ra.sub1[t] = (uint8_t)j;
+        for (int j = 0; j < dv->M2; j++) for (int t = o2[j]; t < o2[j] + l2[j]; t++) ra.sub2[t] = (uint8_t)j;
+        auto kern = P.rboth ? refine_kernel<true> : refine_kernel<false>;
+        kern<<<P.rgrid, P.rw * 32, P.rsm, st>>>(ra);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) {
+            set_error("refine kernel launch failed: %s", cudaGetErrorString(ce));
+            return LC_ERR_CUDA;
+        }
+    }
+    if (profile) {
+        cudaEventRecord(dv->ev[2], st);
+        dv->ev_valid = true;
+        dv->has_refine = P.refine;
+    }
+    return LC_OK;
+}
+
 lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
                  int32_t *ids, float *dists, int32_t *stats, void *stream_)
 {
     cudaStream_t st = (cudaStream_t)stream_;
-    int k = sp->k, efp = std::max(sp->ef, sp->k);
-    bool refine = sp->shortlist >= 0;
-    int R = refine ? std::max(sp->shortlist > 0 ? sp->shortlist : 10, k) : k;
-    if (refine && R > MAX_SHORTLIST) {
-        set_error("shortlist %d exceeds %d", R, MAX_SHORTLIST);
-        return LC_ERR_ARG;
-    }
+    const int k = sp->k;
     // pointer kinds: all device or all host
     auto kind = [](const void *p) {
         cudaPointerAttributes at;
@@ -903,10 +1023,13 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
         set_error("query and output pointers must all be host or all be device memory");
         return LC_ERR_ARG;
     }
-    bool dev_ptrs = kq == 1;
+    const bool dev_ptrs = kq == 1;
     lc_status rs = upload(ix);
     if (rs != LC_OK) return rs;
     DeviceIndex *dv = ix->dev;
+    SearchPlan P;
+    rs = plan_search(dv, std::max<int64_t>(nq, 1), sp, &P);
+    if (rs != LC_OK) return rs;
     if (nq == 0) return LC_OK;
     const float *dq = q;
     int32_t *dids = ids, *dstats = stats;
@@ -947,137 +1070,26 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
         if (stats) cudaMemcpy(stats, hs.data(), hs.size() * 4, kk);
         return LC_OK;
     }
-
-    WalkArgs wa{};
-    wa.Q = dq; wa.nq = nq; wa.d = dv->d;
-    wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.codes1 = dv->codes1;
-    wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
-    wa.ep = dv->ep; wa.max_level = dv->max_level;
-    wa.efp = efp; wa.efcap = (int)align_up(efp, 32);
-    wa.R = R; wa.refine = refine ? 1 : 0;
-    wa.beam = sp->mode == LC_MODE_BATCHED ? sp->beam : 1;
-    wa.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));
-    wa.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)efp * 64)));
-    wa.status = dv->status;
-    wa.stats_out = dstats;
-    std::vector<int> off, len;
-    splits(dv->d, dv->M1, off, len);
-    for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
-    size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log, wa.beam).total;
-    int grid = 0, wpb = 1;
-    size_t smem = 0;
-    cudaError_t ce;
-    // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
-    const int variant = (dv->M1 == 16 && dv->d == 96) ? 1 : (dv->M1 == 32 && dv->d == 96) ? 2
-                      : (dv->M1 == 64 && dv->d == 128) ? 3 : 0;
-    switch (variant) {
-    case 1: ce = launch_walk<16, 6>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem); break;
-    case 2: ce = launch_walk<32, 3>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem); break;
-    case 3: ce = launch_walk<64, 2>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem); break;
-    default:
-        if (dv->M1 == 16) ce = launch_walk<16, 0>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem);
-        else if (dv->M1 == 32) ce = launch_walk<32, 0>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem);
-        else ce = launch_walk<64, 0>(wa, per_warp, dv->num_sms, &wpb, &grid, &smem);
-    }
-    if (ce == cudaErrorInvalidConfiguration) {
-        set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
-                  "lower efSearch or visited_log", per_warp, walk_c1_bytes(dv->d));
-        return LC_ERR_CAPACITY;
-    }
-    if (ce != cudaSuccess) {
-        set_error("walk kernel configuration failed (%zu B shared memory per warp): %s", per_warp,
-                  cudaGetErrorString(ce));
-        return LC_ERR_CUDA;
-    }
-    size_t slots = (size_t)grid * wpb;
-    if (!grow(dv->spill, dv->spill_cap, slots << wa.spill_log)) {
-        set_error("cudaMalloc failed for the visited spill tables");
+    if (!grow(dv->spill, dv->spill_cap, P.spill_elems) ||
+        (P.refine && (!grow(dv->yq, dv->yq_cap, P.yq_elems) || !grow(dv->shortlist, dv->sl_cap, P.sl_elems)))) {
+        set_error("cudaMalloc failed for search scratch");
         return LC_ERR_OOM;
     }
-    wa.spill = dv->spill;
-    if (refine) {
-        if (!grow(dv->yq, dv->yq_cap, (size_t)nq * dv->d) || !grow(dv->shortlist, dv->sl_cap, (size_t)nq * R)) {
-            set_error("cudaMalloc failed for search scratch");
-            return LC_ERR_OOM;
-        }
-        wa.yq_out = dv->yq;
-        wa.short_out = dv->shortlist;
-    } else {
-        wa.ids_out = dids;
-        wa.dists_out = ddists;
-    }
-    wa.counter = dv->counter;
-    if (cudaMemsetAsync(dv->status, 0, sizeof(int32_t), st) != cudaSuccess ||
-        cudaMemsetAsync(dv->counter, 0, sizeof(unsigned long long), st) != cudaSuccess) {
-        set_error("status reset failed");
-        return LC_ERR_CUDA;
-    }
-    if (dv->profile) {
-        for (auto &e : dv->ev)
-            if (!e) cudaEventCreate(&e);
-        cudaEventRecord(dv->ev[0], st);
-    }
-    switch (variant) {
-    case 1: ce = run_walk<16, 6>(wa, smem, wpb, grid, st); break;
-    case 2: ce = run_walk<32, 3>(wa, smem, wpb, grid, st); break;
-    case 3: ce = run_walk<64, 2>(wa, smem, wpb, grid, st); break;
-    default:
-        if (dv->M1 == 16) ce = run_walk<16, 0>(wa, smem, wpb, grid, st);
-        else if (dv->M1 == 32) ce = run_walk<32, 0>(wa, smem, wpb, grid, st);
-        else ce = run_walk<64, 0>(wa, smem, wpb, grid, st);
-    }
-    if (dv->profile) cudaEventRecord(dv->ev[1], st);
-    if (ce != cudaSuccess) {
-        set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
-        return LC_ERR_CUDA;
-    }
-    if (refine) {
-        RefineArgs ra{};
-        ra.yq = dv->yq; ra.shortlist = dv->shortlist; ra.nq = nq; ra.R = R; ra.k = k; ra.d = dv->d;
-        ra.M1 = dv->M1; ra.M2P = dv->M2P; ra.C1 = dv->C1; ra.C2 = dv->C2; ra.B = dv->B;
-        ra.codes1 = dv->codes1; ra.codes2b = dv->codes2b; ra.adj0 = dv->adj0;
-        ra.ids_out = dids; ra.dists_out = ddists;
-        std::vector<int> o2, l2;
-        splits(dv->d, dv->M1, off, len);
-        splits(dv->d, dv->M2, o2, l2);
-        for (int j = 0; j < dv->M1; j++) for (int t = off[j]; t < off[j] + len[j]; t++) ra.sub1[t] = (uint8_t)j;
-        for (int j = 0; j < dv->M2; j++) for (int t = o2[j]; t < o2[j] + l2[j]; t++) ra.sub2[t] = (uint8_t)j;
-        const size_t per = refine_smem(dv->M1, dv->M2P, R);
-        const size_t cbytes = (size_t)256 * dv->d * 4;
-        // both codebooks in shared memory when that leaves room for at least 4 warps
-        const bool both = 2 * cbytes + 4 * per <= MAX_SMEM_PER_BLOCK;
-        const size_t cb = (both ? 2 : 1) * cbytes;
-        if (cb + per > MAX_SMEM_PER_BLOCK) {
-            set_error("refinement does not fit in shared memory (d = %d)", dv->d);
-            return LC_ERR_CAPACITY;
-        }
-        const int rw = (int)std::min<size_t>(16, (MAX_SMEM_PER_BLOCK - cb) / per);
-        const size_t rsm = cb + per * rw;
-        auto kern = both ? refine_kernel<true> : refine_kernel<false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, rw * 32, rsm);
-        int64_t need = (nq + rw - 1) / rw;
-        int rgrid = (int)std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * dv->num_sms);
-        kern<<<rgrid, rw * 32, rsm, st>>>(ra);
-        ce = cudaGetLastError();
-        if (ce != cudaSuccess) {
-            set_error("refine kernel launch failed: %s", cudaGetErrorString(ce));
-            return LC_ERR_CUDA;
-        }
-    }
-    if (dv->profile) {
-        cudaEventRecord(dv->ev[2], st);
-        dv->ev_valid = true;
-        dv->has_refine = refine;
-    }
+    SearchScratch sc;
+    sc.yq = dv->yq;
+    sc.shortlist = dv->shortlist;
+    sc.spill = dv->spill;
+    sc.status = dv->status;
+    sc.counter = dv->counter;
+    rs = run_search(dv, P, dq, nq, dids, ddists, dstats, sc, st, dv->profile);
+    if (rs != LC_OK) return rs;
     if (!dev_ptrs) {
         cudaMemcpyAsync(ids, dids, sizeof(int32_t) * nq * k, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(dists, ddists, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, st);
         if (stats) cudaMemcpyAsync(stats, dstats, sizeof(int32_t) * nq * 3, cudaMemcpyDeviceToHost, st);
         int32_t status = 0;
         cudaMemcpyAsync(&status, dv->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-        ce = cudaStreamSynchronize(st);
+        cudaError_t ce = cudaStreamSynchronize(st);
         if (ce != cudaSuccess) {
             set_error("search failed: %s", cudaGetErrorString(ce));
             return LC_ERR_CUDA;

@@ -22,7 +22,14 @@ EXPORTED = [
     "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_search",
     "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
     "lc_profile_read", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
+    "lc_serve_open", "lc_serve_submit", "lc_serve_poll", "lc_serve_close",
 ]
+
+# void (*lc_request_cb)(void *user, uint64_t req_id, lc_status status, const int32_t *ids,
+#                       const float *dists, int32_t nq, int32_t k)
+LC_REQUEST_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                                 ctypes.c_int32, ctypes.c_int32)
 
 
 class LcError(RuntimeError):
@@ -71,6 +78,10 @@ def lib() -> ctypes.CDLL:
         "lc_load": (I, [ctypes.c_char_p, P]),
         "lc_profile": (I, [P, I]),
         "lc_search_walk_noalloc": (I, [P, P, I64, I, I, P, P, P, P]),
+        "lc_serve_open": (I, [P, ctypes.c_size_t, I, I, P]),
+        "lc_serve_submit": (I, [P, P, ctypes.c_int32, P, LC_REQUEST_CB, P, P]),
+        "lc_serve_poll": (I, [P, I, P]),
+        "lc_serve_close": (I, [P]),
         "lc_profile_read": (I, [P, P, P]),
         "lc_free": (None, [P]),
         "lc_last_error": (ctypes.c_char_p, []),
@@ -158,6 +169,43 @@ def lc_search_walk_noalloc(ix, q, nq: int, k: int, ef: int, ids, dists, stats=No
         s = s.cuda_stream
     _check(lib().lc_search_walk_noalloc(ix, _ptr(q), nq, k, ef, _ptr(ids), _ptr(dists), _ptr(stats),
                                         ctypes.c_void_p(s) if s else None))
+
+
+def make_request_cb(fn):
+    """Wraps fn(req_id, status, ids, dists) into an lc_request_cb; ids/dists are copied into
+    numpy arrays ([nq][k]) when status is LC_OK, else None.  Keep the returned object alive
+    until the request has completed."""
+    def _cb(user, req_id, status, ids, dists, nq, k):
+        if status == LC_OK:
+            i = np.ctypeslib.as_array(ids, shape=(nq, k)).copy()
+            d = np.ctypeslib.as_array(dists, shape=(nq, k)).copy()
+        else:
+            i = d = None
+        fn(int(req_id), int(status), i, d)
+    return LC_REQUEST_CB(_cb)
+
+
+def lc_serve_open(ix, device_budget_bytes: int, max_inflight: int, max_request: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().lc_serve_open(ix, device_budget_bytes, max_inflight, max_request, ctypes.byref(h)))
+    return h
+
+
+def lc_serve_submit(srv, q: np.ndarray, sp: lc_search_params, cb) -> int:
+    q = np.ascontiguousarray(q, np.float32)
+    rid = ctypes.c_uint64()
+    _check(lib().lc_serve_submit(srv, _ptr(q), q.shape[0], ctypes.byref(sp), cb, None, ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def lc_serve_poll(srv, timeout_ms: int = 0) -> int:
+    n = ctypes.c_int()
+    _check(lib().lc_serve_poll(srv, timeout_ms, ctypes.byref(n)))
+    return int(n.value)
+
+
+def lc_serve_close(srv):
+    _check(lib().lc_serve_close(srv))
 
 
 def lc_import(ix, n, R, C1, C2, codes1, codes2, beta, B, adj0, levels, upper_adj, ep: int):
