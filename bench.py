@@ -16,7 +16,9 @@ measurement through the same C ABI call with pinned host buffers (query upload a
 download inside the timed region).  ``roofline`` reports the walk kernel's algorithmic
 bytes (adjacency rows of expanded nodes + level-1 code rows of scored nodes, from the
 kernel's own counters) over its event-timed duration.  ``cpu_baseline`` is the FP64 oracle
-on one host core on a bounded sample of the same queries.
+on one host core on a bounded sample of the same queries.  ``config.served`` measures the
+request server (lc_serve_*): saturation QPS with the headline parameters, and p50/p99 latency
+under open-loop Poisson arrivals of mixed requests.
 
 --impl reference times the oracle itself (the slow restatement of the paper the GPU path
 is checked against) on the same workload, a bounded query sample per step.
@@ -196,6 +198,83 @@ def time_oracle(oix, xq, k, ef, budget_s):
     return done, time.perf_counter() - t0
 
 
+def measure_serving(lc, h, xq, gt, k, args, sp_best):
+    """Serving through lc_serve_*.  (1) Saturation: 512-query requests with the headline
+    parameters (same results as the batch search) submitted back to back with up to 16 in
+    flight; QPS over the whole run.  (2) Open loop: Poisson arrivals at fixed query rates,
+    request sizes log-uniform in [1, 512], k in {1, 10, 100}, efSearch log-uniform in
+    [16, 512], plain; latency = completion - arrival on the host clock."""
+    rng = np.random.default_rng(7)
+    budget = 8 << 30
+    srv = lc.lc_serve_open(h, budget, 16, 512)
+    out = {"budget_bytes": budget, "max_inflight": 16, "max_request": 512}
+    try:
+        done = {}
+        cbs = []
+
+        def cb_store(rid, st, i, d):
+            done[rid] = (time.perf_counter(), st, None if i is None else i[:, 0].copy())
+
+        n_req = 120
+        starts = [(j * 512) % (len(xq) - 512) for j in range(n_req)]
+        t0 = time.perf_counter()
+        ids = []
+        for j in range(n_req):
+            cb = lc.make_request_cb(cb_store)
+            cbs.append(cb)
+            ids.append(lc.lc_serve_submit(srv, xq[starts[j]:starts[j] + 512], sp_best, cb))
+            while len(ids) - len(done) > 24:
+                lc.lc_serve_poll(srv, 1)
+        while len(done) < n_req:
+            lc.lc_serve_poll(srv, 5)
+        t1 = max(v[0] for v in done.values())
+        ok = all(v[1] == 0 for v in done.values())
+        rec = float(np.mean([(done[r][2] == gt[s:s + 512]).mean() for r, s in zip(ids, starts)]))
+        out["saturation"] = {"qps": n_req * 512 / (t1 - t0), "requests": n_req, "request_size": 512,
+                             "recall_at_1": rec, "all_ok": ok}
+        # open loop
+        sizes_all = np.exp(rng.uniform(0, np.log(512), size=100000)).astype(int)
+        mean_size = float(sizes_all.mean())
+        points = []
+        for lam in args.serve_rates:
+            n = int(min(2000, max(200, lam * args.serve_seconds / mean_size)))
+            gaps = rng.exponential(mean_size / lam, size=n)
+            arrive = np.cumsum(gaps)
+            sizes = np.exp(rng.uniform(0, np.log(512), size=n)).astype(int)
+            ks = rng.choice([1, 10, 100], size=n)
+            efs = np.exp(rng.uniform(np.log(16), np.log(512), size=n)).astype(int)
+            lat, cbs2, arr_of = [], [], {}
+            fin = {}
+
+            def cb_lat(rid, st, i, d):
+                fin[rid] = (time.perf_counter(), st)
+
+            tb = time.perf_counter()
+            j = 0
+            while j < n or len(fin) < n:
+                now = time.perf_counter() - tb
+                while j < n and arrive[j] <= now:
+                    s0 = int(rng.integers(0, len(xq) - sizes[j]))
+                    sp = lc.lc_default_search_params(int(ks[j]), int(efs[j]))
+                    cb = lc.make_request_cb(cb_lat)
+                    cbs2.append(cb)
+                    rid = lc.lc_serve_submit(srv, xq[s0:s0 + sizes[j]], sp, cb)
+                    arr_of[rid] = tb + arrive[j]
+                    j += 1
+                lc.lc_serve_poll(srv, 0)
+            lat = np.array([(fin[r][0] - arr_of[r]) * 1e3 for r in arr_of])
+            span = max(v[0] for v in fin.values()) - tb
+            points.append({"offered_qps": lam, "requests": n, "achieved_qps": float(sizes.sum() / span),
+                           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                           "all_ok": all(v[1] == 0 for v in fin.values())})
+        out["open_loop"] = points
+        out["open_loop_mix"] = ("request sizes log-uniform in [1, 512] queries, k uniform in {1, 10, 100}, "
+                                "efSearch log-uniform in [16, 512], plain mode, Poisson arrivals")
+    finally:
+        lc.lc_serve_close(srv)
+    return out
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,6 +346,10 @@ def main():
     ap.add_argument("--ef", type=int, default=64)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--beam", type=int, default=4, help="batched form: expansions per step (1: plain only)")
+    ap.add_argument("--serve", type=int, default=1, help="1: also measure the request server")
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[20000, 50000, 100000, 200000],
+                    help="open-loop offered loads, queries per second")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="target duration of each open-loop point")
     ap.add_argument("--mode", default="both", choices=["both", "plain", "batched"],
                     help="both: plain sets the recall target, batched is swept to reach it; "
                          "plain / batched: that form only, at --ef")
@@ -382,6 +465,10 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     e2e = nq / float(np.mean(e2e_t))
 
+    served = None
+    if args.serve and ws == 1:
+        served = measure_serving(lc, h, xq, gt, k, args, best_sp)
+
     cpu = None
     if rank == 0 and ws == 1:
         import oracle
@@ -412,6 +499,7 @@ def main():
                    "plain": None if plain is None else summary(plain, args.ef),
                    "batched": None if batched is None else summary(
                        batched, batched["ef"], {"beam": args.beam, "sweep": batched["sweep"]}),
+                   "served": served,
                    "l2": "flushed before every step (256 MB read, outside the timed span)",
                    "index_build_s": round(build_s, 1), "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
