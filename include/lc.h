@@ -91,6 +91,8 @@ typedef struct {
                         memory, 2^16 entries per query in flight; beyond half of that the
                         query fails with LC_ERR_CAPACITY) */
     int beam;        /* LC_MODE_BATCHED: expansions per step, 2..8 (ignored in PLAIN mode) */
+    int max_dist;    /* search-time cap T (Section 3.1): 0 = none; > 0: the level-0 search stops
+                        before an expansion once T distances have been computed there */
 } lc_search_params;
 
 void lc_default_search_params(lc_search_params *p, int k, int ef);
@@ -181,6 +183,17 @@ lc_status lc_load(const char *path, lc_index **out);
  * and ids -1.  Errors: LC_ERR_ARG, LC_ERR_STATE, LC_ERR_CUDA, LC_ERR_CAPACITY. */
 lc_status lc_search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef,
                                  int32_t *ids, float *dists, int32_t *stats, void *stream);
+
+/* Merges per-shard search results into global top-k lists.  A database split into S shards of
+ * contiguous id ranges, each with its own index, is searched by running every query against
+ * every shard; this call merges the S result lists of each query by (distance, global id),
+ * global id = shard-local id + id_offsets[s] (-1 entries are padding).  The paper searches one
+ * index; sharding is this library's way to hold larger databases or use several GPUs.
+ * ids, dists: device arrays [S][nq][k] (the shards' outputs stacked); id_offsets: host [S];
+ * ids_out, dists_out: device [nq][k].  Queued on `stream`.  Requires S <= 64, S * k <= 2048.
+ * Errors: LC_ERR_ARG, LC_ERR_CUDA. */
+lc_status lc_merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, int k,
+                        const int64_t *id_offsets, int32_t *ids_out, float *dists_out, void *stream);
 
 /* ---- Serving: continuous batching of requests on one GPU (the paper has no serving
  * component; this is the library's own).  The index stays resident; each request (a batch of

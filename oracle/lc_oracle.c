@@ -12,7 +12,8 @@
  * speed: sets are plain arrays scanned linearly, and each step follows the paper's order.
  *
  *   orc_search      Section 4.1 (two-stage search) over the HNSW structure of Section 2
- *                   (beam >= 2: the batched form, several expansions per step):
+ *                   (beam >= 2: the batched form, several expansions per step; tcap > 0:
+ *                   stop after T level-0 distance computations, Section 3.1):
  *                   rotation, ADC tables, greedy descent of the upper levels, best-first
  *                   search of level 0, shortlist, refinement with the regression codebook
  *                   (Section 4.3, reconstruction beta^T G(x)), exact L2 and top-k.
@@ -126,8 +127,8 @@ static void decode2(const orc_index *ix, const int *off1, const int *len1, const
    counted once), and keeps the ef' best of W and the new nodes.  With beam = 1 this expands
    the same nodes in the same order as the best-first search of orc_search. */
 static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, int efp, int beam,
-                        char *visited, int32_t *touched, int *ntouch, double *wd, int32_t *wi,
-                        int32_t *n_dist, int32_t *n_expand, gap_rec *g)
+                        int tcap, char *visited, int32_t *touched, int *ntouch, double *wd,
+                        int32_t *wi, int32_t *n_dist, int32_t *n_expand, gap_rec *g)
 {
     int cap = efp + beam * ix->deg + 1;
     double *ad = malloc(sizeof(double) * cap);
@@ -144,6 +145,7 @@ static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, in
     double od = INFINITY;              /* best scored node outside W */
     int32_t oi = -1;
     for (;;) {
+        if (tcap > 0 && *n_dist >= tcap) break;          /* T distance computations done */
         int nu = 0;
         for (int p = 0; p < wn && nu < beam; p++)
             if (!wf[p]) U[nu++] = p;
@@ -187,7 +189,7 @@ static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, in
         for (int p = 0; p < wn; p++) { wd[p] = ad[p]; wi[p] = ai[p]; wf[p] = af[p]; }
     }
     /* termination: the best node outside W against the worst inside */
-    if (oi >= 0) note_gap(g, wd[wn - 1], wi[wn - 1], od, oi, 1);
+    if (oi >= 0 && !(tcap > 0 && *n_dist >= tcap)) note_gap(g, wd[wn - 1], wi[wn - 1], od, oi, 1);
     free(ad); free(ai); free(af); free(wf); free(U);
     return wn;
 }
@@ -196,7 +198,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                const float *C2, const uint8_t *codes1, const uint8_t *codes2,
                const uint8_t *beta, const float *B, int deg, const int32_t *adj0, int deg_up,
                const int32_t *upper_off, const int32_t *upper_adj, int32_t ep, int max_level,
-               int64_t nq, const float *Q, int k, int ef, int shortlist, int beam,
+               int64_t nq, const float *Q, int k, int ef, int shortlist, int beam, int tcap,
                int32_t *ids, double *dists, int32_t *stats, double *min_gap,
                int32_t *w_ids, double *w_dists, int32_t *w_size)
 {
@@ -280,7 +282,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
             }
 
             if (beam >= 2) {
-                wn = walk_batched(&ix, lut, cur, efp, beam, visited, touched, &ntouch, wd, wi,
+                wn = walk_batched(&ix, lut, cur, efp, beam, tcap, visited, touched, &ntouch, wd, wi,
                                   &n_dist, &n_expand, &g);
             } else {
                 /* Best-first search of level 0 from the seed, result set of size ef'. */
@@ -297,6 +299,9 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                 int32_t oid = -1;
                 int ended_by_break = 0;
                 while (cn > 0) {
+                    /* the search-time cap T of Section 3.1: stop once T distance
+                       computations have been made (checked before each expansion) */
+                    if (tcap > 0 && n_dist >= tcap) { ended_by_break = 1; break; }
                     /* c = nearest element of C; its order against the runner-up decides
                        which element is expanded first */
                     int64_t bc = 0, b2 = -1;

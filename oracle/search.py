@@ -17,11 +17,13 @@ from ._clib import lib, ptr
 
 
 def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: bool = False,
-           beam: int = 1):
+           beam: int = 1, tcap: int = 0):
     """Returns dict(ids [nq][k] int32, dists [nq][k] float64, stats [nq][3] int32 =
     (n_dist, n_expand, n_dist_upper), gap [nq] = smallest relative gap of a deciding
     comparison, and with ``return_w`` the final result set W sorted by (dist, id)).  ``beam``
-    >= 2 selects the batched form of the level-0 search (that many expansions per step)."""
+    >= 2 selects the batched form of the level-0 search (that many expansions per step);
+    ``tcap`` > 0 stops the level-0 search once that many distances were computed (Section 3.1's
+    search-time parameter T, checked before each expansion)."""
     Q = np.ascontiguousarray(Q, np.float32)
     nq = Q.shape[0]
     efp = max(ef, k)
@@ -38,7 +40,7 @@ def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: boo
         ptr(ix.codes2), ptr(ix.beta), ptr(ix.B), ix.adj0.shape[1], ptr(ix.adj0),
         ix.upper_adj.shape[1], ptr(ix.upper_off),
         ptr(ix.upper_adj) if ix.upper_adj.shape[0] > 0 else None, ix.ep, ix.max_level,
-        nq, ptr(Q), k, ef, shortlist, beam, ptr(ids), ptr(dists), ptr(stats), ptr(gap),
+        nq, ptr(Q), k, ef, shortlist, beam, tcap, ptr(ids), ptr(dists), ptr(stats), ptr(gap),
         ptr(w_ids), ptr(w_d), ptr(w_n))
     if rc != 0:
         raise RuntimeError(f"orc_search failed ({rc})")
@@ -46,6 +48,22 @@ def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: boo
     if return_w:
         out.update(w_ids=w_ids, w_dists=w_d, w_size=w_n)
     return out
+
+
+def merge_topk(ids: np.ndarray, dists: np.ndarray, offsets, k: int):
+    """Merged top-k of per-shard results [S][nq][k] by (distance, global id), global id =
+    local id + the shard's offset; -1 entries are padding.  Returns (ids [nq][k] int64,
+    dists [nq][k] float64)."""
+    S, nq, _ = ids.shape
+    out_i = np.full((nq, k), -1, np.int64)
+    out_d = np.full((nq, k), np.inf)
+    for q in range(nq):
+        cand = [(float(dists[s, q, j]), int(ids[s, q, j]) + int(offsets[s]))
+                for s in range(S) for j in range(ids.shape[2]) if ids[s, q, j] >= 0]
+        cand.sort()
+        for j, (d, i) in enumerate(cand[:k]):
+            out_i[q, j], out_d[q, j] = i, d
+    return out_i, out_d
 
 
 def knn(X: np.ndarray, Q: np.ndarray, k: int, chunk: int = 256):

@@ -50,6 +50,7 @@ lc_status check_search_params(const lc_search_params *sp)
         set_error("beam = %d outside 2..8 for the batched mode", sp->beam);
         return LC_ERR_ARG;
     }
+    if (sp->max_dist < 0) { set_error("max_dist must be >= 0"); return LC_ERR_ARG; }
     if (sp->visited_log != 0 && (sp->visited_log < 10 || sp->visited_log > 14)) {
         set_error("visited_log = %d outside 10..14", sp->visited_log);
         return LC_ERR_ARG;
@@ -371,6 +372,17 @@ lc_status lc_search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k
     if (ef < 1) { set_error("ef must be >= 1"); return LC_ERR_ARG; }
     if (!ix->trained) { set_error("search before lc_train/lc_import"); return LC_ERR_STATE; }
     return lc::search_walk_noalloc(ix, q, nq, k, ef, ids, dists, stats, stream);
+}
+
+lc_status lc_merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, int k,
+                        const int64_t *id_offsets, int32_t *ids_out, float *dists_out, void *stream)
+{
+    set_error("");
+    if (S < 1 || S > 64 || k < 1 || nq < 0 || (int64_t)S * k > 2048) { set_error("need 1 <= S <= 64, 1 <= k, S * k <= 2048"); return LC_ERR_ARG; }
+    if (nq > 0 && (!ids || !dists || !id_offsets || !ids_out || !dists_out)) { set_error("null argument"); return LC_ERR_ARG; }
+    for (int s = 0; s < S; s++)
+        if (id_offsets[s] < 0 || id_offsets[s] > 0x7fffffff) { set_error("id offset out of range"); return LC_ERR_ARG; }
+    return lc::merge_topk(ids, dists, S, nq, k, id_offsets, ids_out, dists_out, stream);
 }
 
 lc_status lc_profile(lc_index *ix, int enable)

@@ -36,7 +36,7 @@ struct DeviceIndex {
 
 // Launch configuration of one search and the scratch it needs.
 struct SearchPlan {
-    int k = 0, efp = 0, R = 0, beam = 1, hash_log = 0, spill_log = 0, variant = 0;
+    int k = 0, efp = 0, R = 0, beam = 1, tcap = 0, hash_log = 0, spill_log = 0, variant = 0;
     bool refine = false;
     int wpc = 0, grid = 0;               // walk: warps per CTA, CTAs
     size_t per_warp = 0, smem = 0;

@@ -64,6 +64,8 @@ int n_threads(const lc_params &p);
 lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
                  int32_t *ids, float *dists, int32_t *stats, void *stream);
 lc_status profile_enable(lc_index *ix, int on);
+lc_status merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, int k, const int64_t *offsets,
+                     int32_t *ids_out, float *dists_out, void *stream);
 lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef, int32_t *ids,
                               float *dists, int32_t *stats, void *stream);
 lc_status profile_read(lc_index *ix, float *walk_ms, float *refine_ms);

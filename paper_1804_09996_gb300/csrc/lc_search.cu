@@ -78,6 +78,7 @@ struct WalkArgs {
     int R;            // shortlist length (refine) or k (no refinement)
     int refine;
     int beam;         // expansions per step (1: the plain walk)
+    int tcap;         // > 0: stop once that many level-0 distances were computed
     int hash_log;     // shared-memory visited table: 2^hash_log entries
     int spill_log;    // global spill table per warp: 2^spill_log entries
     int32_t *spill;
@@ -413,6 +414,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         int scan_from = 0;
         const int B = a.beam;                // expansions per step; 1 = the plain walk
         for (;;) {
+            if (a.tcap > 0 && n_dist >= a.tcap) break;     // search-time cap T (Section 3.1)
             uint64_t *W = wkey + buf * a.efcap;
             uint8_t *F = wflag + buf * a.efcap;
             // the B best unexpanded members of W: lane i < nb holds the i-th one's position
@@ -867,6 +869,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
         return LC_ERR_ARG;
     }
     P.beam = sp->mode == LC_MODE_BATCHED ? sp->beam : 1;
+    P.tcap = sp->max_dist;
     P.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)P.efp * 32)));
     P.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)P.efp * 64)));
     const int efcap = (int)align_up(P.efp, 32);
@@ -937,6 +940,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
     wa.efp = P.efp; wa.efcap = (int)align_up(P.efp, 32);
     wa.R = P.R; wa.refine = P.refine ? 1 : 0;
     wa.beam = P.beam;
+    wa.tcap = P.tcap;
     wa.hash_log = P.hash_log;
     wa.spill_log = P.spill_log;
     wa.spill = sc.spill;
@@ -1239,6 +1243,89 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     }
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
+        return LC_ERR_CUDA;
+    }
+    return LC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Top-k merge of per-shard results (sharded search: every query searches every shard, then
+// the shards' k best are merged by (distance, global id)).  One warp per query: the S*k keys
+// (shard-local ids shifted by the shard's id offset) are sorted in shared memory by a bitonic
+// network and the k smallest are written.
+constexpr int MERGE_MAX = 2048;   // S * k per query
+constexpr int MERGE_WARPS = 4;
+constexpr int MERGE_MAX_SHARDS = 64;
+
+struct ShardOffsets {
+    int64_t v[MERGE_MAX_SHARDS];
+};
+
+__global__ void __launch_bounds__(MERGE_WARPS * 32) merge_kernel(const int32_t *ids, const float *dists,
+                                                                 int S, int64_t nq, int k,
+                                                                 const ShardOffsets offsets, int32_t *ids_out,
+                                                                 float *dists_out, int P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw) + (size_t)warp * P;
+    const int64_t gwarp = (int64_t)blockIdx.x * MERGE_WARPS + warp;
+    const int64_t nwarps = (int64_t)gridDim.x * MERGE_WARPS;
+    for (int64_t q = gwarp; q < nq; q += nwarps) {
+        for (int i = lane; i < P; i += 32) {
+            uint64_t key = ~0ull;
+            if (i < S * k) {
+                const int s = i / k, j = i % k;
+                const int64_t src = ((int64_t)s * nq + q) * k + j;
+                const int32_t id = ids[src];
+                if (id >= 0) key = make_key(dists[src], (int32_t)(id + offsets.v[s]));
+            }
+            keys[i] = key;
+        }
+        __syncwarp();
+        for (int kk = 2; kk <= P; kk <<= 1) {
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < P; i += 32) {
+                    const int p = i ^ j;
+                    if (p > i) {
+                        const uint64_t x = keys[i], y = keys[p];
+                        const bool up = (i & kk) == 0;
+                        if ((x > y) == up) { keys[i] = y; keys[p] = x; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int i = lane; i < k; i += 32) {
+            const uint64_t key = keys[i];
+            const bool ok = key != ~0ull;
+            ids_out[q * k + i] = ok ? key_id(key) : -1;
+            dists_out[q * k + i] = ok ? key_dist(key) : __int_as_float(0x7f800000);
+        }
+        __syncwarp();
+    }
+}
+
+lc_status merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, int k, const int64_t *offsets,
+                     int32_t *ids_out, float *dists_out, void *stream_)
+{
+    cudaStream_t st = (cudaStream_t)stream_;
+    if (nq == 0) return LC_OK;
+    int P = 32;
+    while (P < S * k) P <<= 1;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ShardOffsets off{};
+    for (int i = 0; i < S; i++) off.v[i] = offsets[i];
+    const size_t smem = (size_t)P * 8 * MERGE_WARPS;
+    cudaFuncSetAttribute(merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM_PER_BLOCK);
+    const int64_t need = (nq + MERGE_WARPS - 1) / MERGE_WARPS;
+    const int grid = (int)std::min<int64_t>(need, (int64_t)sms * 8);
+    merge_kernel<<<grid, MERGE_WARPS * 32, smem, st>>>(ids, dists, S, nq, k, off, ids_out, dists_out, P);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        set_error("merge kernel launch failed: %s", cudaGetErrorString(ce));
         return LC_ERR_CUDA;
     }
     return LC_OK;

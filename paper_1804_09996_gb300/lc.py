@@ -22,7 +22,7 @@ EXPORTED = [
     "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_search",
     "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
     "lc_profile_read", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
-    "lc_serve_open", "lc_serve_submit", "lc_serve_poll", "lc_serve_close",
+    "lc_serve_open", "lc_serve_submit", "lc_serve_poll", "lc_serve_close", "lc_merge_topk",
 ]
 
 # void (*lc_request_cb)(void *user, uint64_t req_id, lc_status status, const int32_t *ids,
@@ -47,7 +47,7 @@ class lc_params(ctypes.Structure):
 
 
 class lc_search_params(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam")]
+    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam", "max_dist")]
 
 
 _lib = None
@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
         "lc_profile": (I, [P, I]),
         "lc_search_walk_noalloc": (I, [P, P, I64, I, I, P, P, P, P]),
         "lc_serve_open": (I, [P, ctypes.c_size_t, I, I, P]),
+        "lc_merge_topk": (I, [P, P, I, I64, I, P, P, P, P]),
         "lc_serve_submit": (I, [P, P, ctypes.c_int32, P, LC_REQUEST_CB, P, P]),
         "lc_serve_poll": (I, [P, I, P]),
         "lc_serve_close": (I, [P]),
@@ -169,6 +170,16 @@ def lc_search_walk_noalloc(ix, q, nq: int, k: int, ef: int, ids, dists, stats=No
         s = s.cuda_stream
     _check(lib().lc_search_walk_noalloc(ix, _ptr(q), nq, k, ef, _ptr(ids), _ptr(dists), _ptr(stats),
                                         ctypes.c_void_p(s) if s else None))
+
+
+def lc_merge_topk(ids, dists, S: int, nq: int, k: int, id_offsets, ids_out, dists_out, stream=None):
+    """ids/dists: device tensors [S][nq][k]; id_offsets: sequence of S ints; outputs [nq][k]."""
+    off = np.ascontiguousarray(np.asarray(id_offsets, np.int64))
+    s = stream
+    if s is not None and hasattr(s, "cuda_stream"):
+        s = s.cuda_stream
+    _check(lib().lc_merge_topk(_ptr(ids), _ptr(dists), S, nq, k, _ptr(off), _ptr(ids_out), _ptr(dists_out),
+                               ctypes.c_void_p(s) if s else None))
 
 
 def make_request_cb(fn):

@@ -38,10 +38,10 @@ def handle(name, ix):
     return _handles[name]
 
 
-def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1):
+def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1, tcap=0):
     import torch
     nq = len(xq)
-    sp = lc.lc_default_search_params(k, ef, shortlist=shortlist, visited_log=visited_log)
+    sp = lc.lc_default_search_params(k, ef, shortlist=shortlist, visited_log=visited_log, max_dist=tcap)
     if beam > 1:
         sp.mode, sp.beam = lc.LC_MODE_BATCHED, beam
     if device:
@@ -111,6 +111,16 @@ def test_batched_spill_and_wide(mix3k):
     h = handle("mix3k", ix)
     ref = oracle.search(ix, xq, 10, 256, beam=4)
     compare(ref, *gpu_search(h, xq, 10, 256, visited_log=10, beam=4), max_exempt=0.3)
+
+
+@pytest.mark.parametrize("tcap", [60, 250])
+@pytest.mark.parametrize("beam", [1, 4])
+def test_parity_tcap(opq3k, tcap, beam):
+    # search-time cap T (Section 3.1): stop once T level-0 distances were computed
+    ix, xb, xq = opq3k
+    h = handle("opq3k", ix)
+    ref = oracle.search(ix, xq, 10, 128, beam=beam, tcap=tcap)
+    compare(ref, *gpu_search(h, xq, 10, 128, beam=beam, tcap=tcap), max_exempt=0.1)
 
 
 def test_parity_10k_workload(mix10k):

@@ -353,3 +353,25 @@ def test_batched_recall_close_to_plain(mix10k):
     # the batched form expands a superset of useful nodes: recall does not drop
     assert rb >= rp - 0.01
     assert (b["stats"][:, 1] >= p["stats"][:, 1]).mean() > 0.9
+
+
+def test_hand_traced_tcap():
+    # T = 4: the first expansion (of 0) scores 1, 2, 5 -> n_dist = 4 >= T, the walk stops with
+    # W = {2 (10), 1 (13)}; T = 5: one more expansion (of 2) scores 4 -> W = {4, 2}.
+    ix = tiny_index(CODES, ADJ)
+    r = oracle.search(ix, Q0, k=2, ef=2, shortlist=-1, return_w=True, tcap=4)
+    assert r["w_ids"][0].tolist() == [2, 1] and r["stats"][0].tolist() == [4, 1, 0]
+    r = oracle.search(ix, Q0, k=2, ef=2, shortlist=-1, return_w=True, tcap=5)
+    assert r["w_ids"][0].tolist() == [4, 2] and r["stats"][0].tolist() == [5, 2, 0]
+    # batched form: the cap is checked before each step
+    r = oracle.search(ix, Q0, k=2, ef=2, shortlist=-1, return_w=True, beam=2, tcap=5)
+    assert r["stats"][0].tolist() == [6, 3, 0]
+
+
+def test_tcap_large_is_no_cap(mix3k):
+    ix, xb, xq = mix3k
+    a = oracle.search(ix, xq[:50], k=10, ef=64)
+    b = oracle.search(ix, xq[:50], k=10, ef=64, tcap=10**9)
+    assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["stats"], b["stats"])
+    c = oracle.search(ix, xq[:50], k=10, ef=64, tcap=120)
+    assert (c["stats"][:, 0] < 120 + 32).all() and (c["stats"][:, 0] <= a["stats"][:, 0]).all()
