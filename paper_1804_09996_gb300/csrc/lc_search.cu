@@ -218,6 +218,39 @@ __device__ __forceinline__ float part_dist(const float *C1s, int d, int c, const
     return s;
 }
 
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// The sub-space terms of two codes c0, c1 at once with packed FP32x2 arithmetic: each half
+// performs exactly the scalar operations of part_dist (same rounding), two slots per
+// instruction.
+template <int M1, int D1>
+__device__ __forceinline__ void pair_dist(const float *C1s, int d, int c0, int c1, const LaneGeo<M1, D1> &g,
+                                          int k, float &s0, float &s1)
+{
+    const float *r0 = C1s + c0 * d + g.off[k];
+    const float *r1 = C1s + c1 * d + g.off[k];
+    unsigned long long acc = 0ull;                   // (+0.f, +0.f)
+#pragma unroll
+    for (int u = 0; u < D1; u++) {
+        const unsigned long long yy = pack2(g.y[k][u], g.y[k][u]);
+        const unsigned long long cc = pack2(r0[u], r1[u]);
+        unsigned long long df;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(yy), "l"(cc));
+        asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(acc) : "l"(df), "l"(acc));
+    }
+    unpack2(acc, s0, s1);
+}
+
 // Sub-space terms of S slots (S = 16 or 32) for this lane, summed by reduce_slots<S>.
 template <int M1, int D1, int S>
 __device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *stage, int nf, int d,
@@ -233,6 +266,25 @@ __device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *st
             if (2 * i < nf && sl < nf) t = part_dist<M1, D1>(C1s, d, stage[sl * 16 + j], g, 0);
             v[2 * i] = h ? 0.f : t;
             v[2 * i + 1] = h ? t : 0.f;
+        }
+    } else if (D1 > 0) {
+        // two slots per step (the staged row of slot i + 1 >= nf is stale but a valid code;
+        // its term is discarded)
+#pragma unroll
+        for (int i = 0; i < S; i += 2) {
+            float t0 = 0.f, t1 = 0.f;
+            if (i < nf) {
+                pair_dist<M1, D1>(C1s, d, stage[i * M1 + lane], stage[(i + 1) * M1 + lane], g, 0, t0, t1);
+                if (M1 == 64) {
+                    float u0, u1;
+                    pair_dist<M1, D1>(C1s, d, stage[i * M1 + 32 + lane], stage[(i + 1) * M1 + 32 + lane], g, 1, u0, u1);
+                    t0 += u0;
+                    t1 += u1;
+                }
+                if (i + 1 >= nf) t1 = 0.f;
+            }
+            v[i] = t0;
+            v[i + 1] = t1;
         }
     } else {
 #pragma unroll
