@@ -4,9 +4,9 @@ Workload (default): 1,000,000 database vectors, d = 96, drawn from a mixture of 
 Gaussians and L2-normalised (a stand-in for Deep1B descriptors, which are not available
 here); OPQ32 level-1 codes + residual PQ31 + 1-byte regression codeword = 64 B/vector;
 degree-32 graph; 10,000 queries per step, k = 10.  The plain walk at efSearch = 64 sets the
-1-recall@1 target; the batched form (--beam expansions per step) is swept over efSearch for the
-cheapest setting that reaches it; the faster of the two at the target is the headline, and both
-are reported in ``config``.  The index is built by the library's host build (lc_train +
+1-recall@1 target; the batched form (--beam expansions per step), with the FP32 and with the
+FP16 level-1 codebook, is swept over efSearch for the cheapest setting that reaches it; the
+fastest form at the target is the headline, and all are reported in ``config``.  The index is built by the library's host build (lc_train +
 lc_add) before timing.
 
 A step = one lc_search of the 10k queries with inputs already resident on the GPU (walk
@@ -420,21 +420,26 @@ def main():
         plain = measure(sp_plain, args.steps)
         target = plain["recall"]
         best, best_sp, best_name = plain, sp_plain, "plain"
+    forms = {}
     if args.mode == "both" and args.beam > 1:
-        # the cheapest efSearch at which the batched form reaches the plain form's recall
-        sweep = []
-        for ef_b in sorted({e for e in (16, 24, 32, 40, 48, 56, 64, 80, 96) if e <= max(args.ef, 16)}):
-            sp_b = lc.lc_default_search_params(k, ef_b, mode=lc.LC_MODE_BATCHED, beam=args.beam)
-            r = measure(sp_b, max(10, args.steps // 5))
-            sweep.append((ef_b, r["recall"], r["qps"]))
-            if r["recall"] >= target:
-                break
-        ef_b = sweep[-1][0]
-        sp_b = lc.lc_default_search_params(k, ef_b, mode=lc.LC_MODE_BATCHED, beam=args.beam)
-        batched = measure(sp_b, args.steps)
-        batched.update(ef=ef_b, sweep=sweep)
-        if batched["recall"] >= target and batched["qps"] > plain["qps"]:
-            best, best_sp, best_name = batched, sp_b, f"batched(beam={args.beam})"
+        # the cheapest efSearch at which each faster form reaches the plain form's recall
+        for name, prec in (("batched", lc.LC_LUT_FP32), ("batched_fp16", lc.LC_LUT_FP16)):
+            sweep = []
+            for ef_b in sorted({e for e in (16, 24, 32, 40, 48, 56, 64, 80, 96, 128) if e <= max(2 * args.ef, 16)}):
+                sp_b = lc.lc_default_search_params(k, ef_b, mode=lc.LC_MODE_BATCHED, beam=args.beam, lut_prec=prec)
+                r = measure(sp_b, max(10, args.steps // 5))
+                sweep.append((ef_b, r["recall"], r["qps"]))
+                if r["recall"] >= target:
+                    break
+            ef_b = sweep[-1][0]
+            sp_b = lc.lc_default_search_params(k, ef_b, mode=lc.LC_MODE_BATCHED, beam=args.beam, lut_prec=prec)
+            r = measure(sp_b, args.steps)
+            r.update(ef=ef_b, sweep=sweep, sp=sp_b)
+            forms[name] = r
+            if r["recall"] >= target and r["qps"] > best["qps"]:
+                best, best_sp = r, sp_b
+                best_name = f"batched(beam={args.beam}){', fp16 codebook' if prec else ''}"
+        batched = forms.get("batched")
     clk = clocks.stop()
     if args.mode == "both" and best is not plain:   # leave the headline's counters in `stats`
         measure(best_sp, 3)
@@ -448,7 +453,7 @@ def main():
     walk_s = best["walk_ms"] / 1e3
     peak, peak_src = peaks()
     achieved = b_walk / walk_s / 1e9
-    traffic = profiled_traffic(args.workload, "plain" if best_name == "plain" else "batched")
+    traffic = None if "fp16" in best_name else profiled_traffic(args.workload, "plain" if best_name == "plain" else "batched")
 
     # e2e through the same C ABI call with pinned host buffers
     hq = torch.from_numpy(xq).pin_memory()
@@ -499,6 +504,10 @@ def main():
                    "plain": None if plain is None else summary(plain, args.ef),
                    "batched": None if batched is None else summary(
                        batched, batched["ef"], {"beam": args.beam, "sweep": batched["sweep"]}),
+                   "batched_fp16": None if "batched_fp16" not in forms else summary(
+                       forms["batched_fp16"], forms["batched_fp16"]["ef"],
+                       {"beam": args.beam, "sweep": forms["batched_fp16"]["sweep"],
+                        "codebook": "level-1 codebook rounded to FP16 in the walk, FP32 arithmetic"}),
                    "served": served,
                    "l2": "flushed before every step (256 MB read, outside the timed span)",
                    "index_build_s": round(build_s, 1), "parallelism": f"replicas x{ws}"},

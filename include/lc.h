@@ -74,8 +74,11 @@ void lc_default_params(lc_params *p, int d, int M1, int M2);
  * once); a deterministic variant with more work in flight per query, compared with PLAIN at
  * equal recall (beam = 1 would be PLAIN). */
 enum { LC_MODE_PLAIN = 0, LC_MODE_BATCHED = 1 };
-/* Precision of the per-query ADC tables kept in shared memory. */
-enum { LC_LUT_FP32 = 0 };
+/* Precision of the level-1 codebook the walk scores with (the ADC terms).  FP32: exact FP32
+ * terms.  FP16: the codebook rounded to FP16 (nearest even) and held at half the shared
+ * memory, so more queries are in flight per SM; arithmetic stays FP32, and the re-rank always
+ * uses the FP32 codebooks. */
+enum { LC_LUT_FP32 = 0, LC_LUT_FP16 = 1 };
 
 /* Search parameters (Section 2 search, Section 4.1 two-stage strategy). */
 typedef struct {
@@ -84,7 +87,7 @@ typedef struct {
     int shortlist;   /* 0: refine max(k, 10) candidates (Section 5.1 refines at most 10);
                         > 0: refine max(shortlist, k) (at most 256); < 0: no refinement,
                         return the walk's own top-k by ADC distance */
-    int lut_prec;    /* LC_LUT_FP32 */
+    int lut_prec;    /* LC_LUT_FP32 or LC_LUT_FP16 */
     int mode;        /* LC_MODE_PLAIN or LC_MODE_BATCHED */
     int visited_log; /* 0: automatic; 10..14: the per-query visited table in shared memory has
                         2^visited_log entries (ids beyond half of it go to a table in global

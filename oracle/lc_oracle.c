@@ -13,7 +13,8 @@
  *
  *   orc_search      Section 4.1 (two-stage search) over the HNSW structure of Section 2
  *                   (beam >= 2: the batched form, several expansions per step; tcap > 0:
- *                   stop after T level-0 distance computations, Section 3.1):
+ *                   stop after T level-0 distance computations, Section 3.1; C1w: the
+ *                   codebook the walk's ADC terms use, NULL = C1):
  *                   rotation, ADC tables, greedy descent of the upper levels, best-first
  *                   search of level 0, shortlist, refinement with the regression codebook
  *                   (Section 4.3, reconstruction beta^T G(x)), exact L2 and top-k.
@@ -199,12 +200,15 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                const uint8_t *beta, const float *B, int deg, const int32_t *adj0, int deg_up,
                const int32_t *upper_off, const int32_t *upper_adj, int32_t ep, int max_level,
                int64_t nq, const float *Q, int k, int ef, int shortlist, int beam, int tcap,
-               int32_t *ids, double *dists, int32_t *stats, double *min_gap,
+               const float *C1w, int32_t *ids, double *dists, int32_t *stats, double *min_gap,
                int32_t *w_ids, double *w_dists, int32_t *w_size)
 {
     orc_index ix = {N, d, M1, M2, deg, deg_up, max_level, ep, R, C1, C2, B,
                     codes1, codes2, beta, adj0, upper_off, upper_adj};
     int efp = ef > k ? ef : k;                               /* ef' = max(efSearch, k) */
+    /* the walk's codebook: C1 itself, or a variant of it (e.g. rounded to FP16); the
+       refinement always decodes with C1 */
+    if (!C1w) C1w = C1;
     int off1[256], len1[256], off2[256], len2[256];
     if (M1 > 256 || M2 > 256 || k < 1) return -1;
     split_offsets(d, M1, off1, len1);
@@ -241,7 +245,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
             for (int c = 0; c < 256; c++) {
                 double s = 0.0;
                 for (int t = off1[j]; t < off1[j] + len1[j]; t++) {
-                    double diff = yr[t] - (double)C1[(int64_t)c * d + t];
+                    double diff = yr[t] - (double)C1w[(int64_t)c * d + t];
                     s += diff * diff;
                 }
                 lut[j * 256 + c] = s;

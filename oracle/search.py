@@ -17,13 +17,14 @@ from ._clib import lib, ptr
 
 
 def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: bool = False,
-           beam: int = 1, tcap: int = 0):
+           beam: int = 1, tcap: int = 0, c1_walk: np.ndarray | None = None):
     """Returns dict(ids [nq][k] int32, dists [nq][k] float64, stats [nq][3] int32 =
     (n_dist, n_expand, n_dist_upper), gap [nq] = smallest relative gap of a deciding
     comparison, and with ``return_w`` the final result set W sorted by (dist, id)).  ``beam``
     >= 2 selects the batched form of the level-0 search (that many expansions per step);
     ``tcap`` > 0 stops the level-0 search once that many distances were computed (Section 3.1's
-    search-time parameter T, checked before each expansion)."""
+    search-time parameter T, checked before each expansion).  ``c1_walk`` replaces the level-1
+    codebook in the walk's ADC terms only (e.g. C1 rounded to FP16); the re-rank uses ix.C1."""
     Q = np.ascontiguousarray(Q, np.float32)
     nq = Q.shape[0]
     efp = max(ef, k)
@@ -40,7 +41,8 @@ def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: boo
         ptr(ix.codes2), ptr(ix.beta), ptr(ix.B), ix.adj0.shape[1], ptr(ix.adj0),
         ix.upper_adj.shape[1], ptr(ix.upper_off),
         ptr(ix.upper_adj) if ix.upper_adj.shape[0] > 0 else None, ix.ep, ix.max_level,
-        nq, ptr(Q), k, ef, shortlist, beam, tcap, ptr(ids), ptr(dists), ptr(stats), ptr(gap),
+        nq, ptr(Q), k, ef, shortlist, beam, tcap,
+        ptr(np.ascontiguousarray(c1_walk, np.float32)) if c1_walk is not None else None, ptr(ids), ptr(dists), ptr(stats), ptr(gap),
         ptr(w_ids), ptr(w_d), ptr(w_n))
     if rc != 0:
         raise RuntimeError(f"orc_search failed ({rc})")

@@ -15,6 +15,7 @@ struct DeviceIndex {
     int32_t ep = -1;
     float *Rt = nullptr;          // [d][d], Rt[u*d + t] = R[t][u]
     float *C1 = nullptr, *C2 = nullptr, *B = nullptr;
+    void *C1h = nullptr;          // C1 rounded to FP16 (device __half), for the FP16 mode
     uint8_t *codes1 = nullptr, *codes2b = nullptr;   // codes2b: residual codes padded to M2P bytes, codeword id last
     int M2P = 0;
     int32_t *adj0 = nullptr, *upper_off = nullptr, *upper_adj = nullptr;
@@ -38,6 +39,7 @@ struct DeviceIndex {
 struct SearchPlan {
     int k = 0, efp = 0, R = 0, beam = 1, tcap = 0, hash_log = 0, spill_log = 0, variant = 0;
     bool refine = false;
+    bool half = false;                   // FP16 level-1 codebook in the walk
     int wpc = 0, grid = 0;               // walk: warps per CTA, CTAs
     size_t per_warp = 0, smem = 0;
     int rw = 0, rgrid = 0;               // refine: warps per CTA, CTAs

@@ -26,6 +26,7 @@
 // order; the 32 lane values are added pairwise, lanes differing in bit 3 first, then bits 2,
 // 1, 0 and 4.  The order is the same for every node, so a node's distance does not depend on
 // where or with how many others it is scored.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,7 +48,7 @@ void device_free(DeviceIndex *dv)
     int cur = -1;
     cudaGetDevice(&cur);
     if (dv->device >= 0) cudaSetDevice(dv->device);
-    cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B);
+    cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B); cfree(dv->C1h);
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
@@ -69,6 +70,7 @@ struct WalkArgs {
     int64_t nq;
     int d;
     const float *Rt, *C1;
+    const __half *C1h;     // the same codebook in FP16 (FP16 mode)
     const uint8_t *codes1;
     const int32_t *adj0, *upper_off, *upper_adj;
     int32_t ep;
@@ -102,7 +104,11 @@ struct WalkSmem {
     size_t yq, stage, wkey, wflag, cand, cunsorted, slot, rowbuf, hash, total;
 };
 
-__host__ __device__ inline size_t walk_c1_bytes(int d) { return align_up((size_t)256 * d * 4, 128); }
+// bytes of the level-1 codebook in shared memory (es = 4: FP32, es = 2: FP16)
+__host__ __device__ inline size_t walk_c1_bytes(int d, size_t es = 4) { return align_up((size_t)256 * d * es, 128); }
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
 
 __host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log, int beam)
 {
@@ -196,22 +202,22 @@ struct LaneGeo {
 };
 
 // ||y'^j - C1_j[c]||^2 in the fixed order of the sub-space's coordinates.
-template <int M1, int D1>
-__device__ __forceinline__ float part_dist(const float *C1s, int d, int c, const LaneGeo<M1, D1> &g, int k)
+template <int M1, int D1, typename CT>
+__device__ __forceinline__ float part_dist(const CT *C1s, int d, int c, const LaneGeo<M1, D1> &g, int k)
 {
-    const float *row = C1s + c * d + g.off[k];
+    const CT *row = C1s + c * d + g.off[k];
     float s = 0.f;
     if (D1 > 0) {
 #pragma unroll
         for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) {
-            float df = g.y[k][u] - row[u];
+            float df = g.y[k][u] - to_f(row[u]);
             s = fmaf(df, df, s);
         }
     } else {
 #pragma unroll
         for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++)
             if (u < g.len[k]) {
-                float df = g.y[k][u] - row[u];
+                float df = g.y[k][u] - to_f(row[u]);
                 s = fmaf(df, df, s);
             }
     }
@@ -233,17 +239,17 @@ __device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &
 // The sub-space terms of two codes c0, c1 at once with packed FP32x2 arithmetic: each half
 // performs exactly the scalar operations of part_dist (same rounding), two slots per
 // instruction.
-template <int M1, int D1>
-__device__ __forceinline__ void pair_dist(const float *C1s, int d, int c0, int c1, const LaneGeo<M1, D1> &g,
+template <int M1, int D1, typename CT>
+__device__ __forceinline__ void pair_dist(const CT *C1s, int d, int c0, int c1, const LaneGeo<M1, D1> &g,
                                           int k, float &s0, float &s1)
 {
-    const float *r0 = C1s + c0 * d + g.off[k];
-    const float *r1 = C1s + c1 * d + g.off[k];
+    const CT *r0 = C1s + c0 * d + g.off[k];
+    const CT *r1 = C1s + c1 * d + g.off[k];
     unsigned long long acc = 0ull;                   // (+0.f, +0.f)
 #pragma unroll
     for (int u = 0; u < D1; u++) {
         const unsigned long long yy = pack2(g.y[k][u], g.y[k][u]);
-        const unsigned long long cc = pack2(r0[u], r1[u]);
+        const unsigned long long cc = pack2(to_f(r0[u]), to_f(r1[u]));
         unsigned long long df;
         asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(yy), "l"(cc));
         asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(acc) : "l"(df), "l"(acc));
@@ -252,8 +258,8 @@ __device__ __forceinline__ void pair_dist(const float *C1s, int d, int c0, int c
 }
 
 // Sub-space terms of S slots (S = 16 or 32) for this lane, summed by reduce_slots<S>.
-template <int M1, int D1, int S>
-__device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *stage, int nf, int d,
+template <int M1, int D1, int S, typename CT>
+__device__ __forceinline__ float score_slots(const CT *C1s, const uint8_t *stage, int nf, int d,
                                              const LaneGeo<M1, D1> &g, int lane)
 {
     float v[S];
@@ -263,7 +269,7 @@ __device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *st
         for (int i = 0; i < S / 2; i++) {
             const int sl = 2 * i + h;                // half-warp h scores slots of parity h
             float t = 0.f;
-            if (2 * i < nf && sl < nf) t = part_dist<M1, D1>(C1s, d, stage[sl * 16 + j], g, 0);
+            if (2 * i < nf && sl < nf) t = part_dist<M1, D1, CT>(C1s, d, stage[sl * 16 + j], g, 0);
             v[2 * i] = h ? 0.f : t;
             v[2 * i + 1] = h ? t : 0.f;
         }
@@ -274,10 +280,10 @@ __device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *st
         for (int i = 0; i < S; i += 2) {
             float t0 = 0.f, t1 = 0.f;
             if (i < nf) {
-                pair_dist<M1, D1>(C1s, d, stage[i * M1 + lane], stage[(i + 1) * M1 + lane], g, 0, t0, t1);
+                pair_dist<M1, D1, CT>(C1s, d, stage[i * M1 + lane], stage[(i + 1) * M1 + lane], g, 0, t0, t1);
                 if (M1 == 64) {
                     float u0, u1;
-                    pair_dist<M1, D1>(C1s, d, stage[i * M1 + 32 + lane], stage[(i + 1) * M1 + 32 + lane], g, 1, u0, u1);
+                    pair_dist<M1, D1, CT>(C1s, d, stage[i * M1 + 32 + lane], stage[(i + 1) * M1 + 32 + lane], g, 1, u0, u1);
                     t0 += u0;
                     t1 += u1;
                 }
@@ -291,8 +297,8 @@ __device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *st
         for (int i = 0; i < S; i++) {
             float t = 0.f;
             if (i < nf) {
-                t = part_dist<M1, D1>(C1s, d, stage[i * M1 + lane], g, 0);
-                if (M1 == 64) t += part_dist<M1, D1>(C1s, d, stage[i * M1 + 32 + lane], g, 1);
+                t = part_dist<M1, D1, CT>(C1s, d, stage[i * M1 + lane], g, 0);
+                if (M1 == 64) t += part_dist<M1, D1, CT>(C1s, d, stage[i * M1 + 32 + lane], g, 1);
             }
             v[i] = t;
         }
@@ -303,8 +309,8 @@ __device__ __forceinline__ float score_slots(const float *C1s, const uint8_t *st
 // Walk distances of the nf nodes in slot[0..nf) (1 <= nf <= 32): their code rows are staged
 // in shared memory, each lane computes its sub-space terms, and the totals are formed with
 // 16 or 32 slots.  Returns lane's total; *my_slot = the slot it holds (>= 32: none).
-template <int M1, int D1>
-__device__ __forceinline__ float score_nodes(const float *C1s, uint8_t *stage, const uint8_t *codes1,
+template <int M1, int D1, typename CT>
+__device__ __forceinline__ float score_nodes(const CT *C1s, uint8_t *stage, const uint8_t *codes1,
                                              const int32_t *slot, int nf, int d,
                                              const LaneGeo<M1, D1> &g, int lane, int *my_slot)
 {
@@ -317,10 +323,10 @@ __device__ __forceinline__ float score_nodes(const float *C1s, uint8_t *stage, c
     __syncwarp();
     float r;
     if (nf <= 16) {
-        r = score_slots<M1, D1, 16>(C1s, stage, nf, d, g, lane);
+        r = score_slots<M1, D1, 16, CT>(C1s, stage, nf, d, g, lane);
         *my_slot = lane < 16 ? lane : 32;           // lanes l and l + 16 hold slot l
     } else {
-        r = score_slots<M1, D1, 32>(C1s, stage, nf, d, g, lane);
+        r = score_slots<M1, D1, 32, CT>(C1s, stage, nf, d, g, lane);
         *my_slot = slot_of_lane(lane, 5);
     }
     __syncwarp();
@@ -367,22 +373,22 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
     return false;       // unreachable: the spill table is kept at most half full
 }
 
-template <int M1, int D1>
+template <int M1, int D1, typename CT>
 __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int d = a.d;
     // the level-1 codebook, shared by every warp of the CTA
-    float *C1s = reinterpret_cast<float *>(smem_raw);
+    CT *C1s = reinterpret_cast<CT *>(smem_raw);
     {
-        const float4 *src = reinterpret_cast<const float4 *>(a.C1);
-        float4 *dst = reinterpret_cast<float4 *>(C1s);
-        for (int i = threadIdx.x; i < 256 * d / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+        const uint4 *src = reinterpret_cast<const uint4 *>(sizeof(CT) == 4 ? a.C1 : (const void *)a.C1h);
+        uint4 *dst = reinterpret_cast<uint4 *>(C1s);
+        for (int i = threadIdx.x; i < (int)(256 * d * sizeof(CT) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
     const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam);
-    unsigned char *base = smem_raw + walk_c1_bytes(d) + (size_t)warp * L.total;
+    unsigned char *base = smem_raw + walk_c1_bytes(d, sizeof(CT)) + (size_t)warp * L.total;
     float *yq = reinterpret_cast<float *>(base + L.yq);
     uint8_t *stage = base + L.stage;
     uint64_t *wkey = reinterpret_cast<uint64_t *>(base + L.wkey);
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         int32_t cur = a.ep;
         if (lane == 0) slot[0] = cur;
         __syncwarp();
-        float dcur = score_nodes<M1, D1>(C1s, stage, a.codes1, slot, 1, d, g, lane, &my_slot);
+        float dcur = score_nodes<M1, D1, CT>(C1s, stage, a.codes1, slot, 1, d, g, lane, &my_slot);
         dcur = __shfl_sync(FULL, dcur, 0);                                    // lane 0 holds slot 0
         if (a.max_level >= 1) n_up = 1;
         for (int l = a.max_level; l >= 1; l--) {
@@ -439,7 +445,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                 if (e >= 0) slot[__popc(vm & lt_mask)] = e;
                 __syncwarp();
                 n_up += nv;
-                float de = score_nodes<M1, D1>(C1s, stage, a.codes1, slot, nv, d, g, lane, &my_slot);
+                float de = score_nodes<M1, D1, CT>(C1s, stage, a.codes1, slot, nv, d, g, lane, &my_slot);
                 uint64_t k = my_slot < nv ? make_key(de, slot[my_slot]) : ~0ull;
                 uint64_t best = warp_min64(k);
                 __syncwarp();
@@ -523,7 +529,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             int nc = 0;
             for (int ch = 0; ch < ns; ch += 32) {
                 const int nf = min(32, ns - ch);
-                const float de = score_nodes<M1, D1>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot);
+                const float de = score_nodes<M1, D1, CT>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot);
                 uint64_t k = my_slot < nf ? make_key(de, slot[ch + my_slot]) : ~0ull;
                 if (k >= wmax) k = ~0ull;
                 const unsigned km = __ballot_sync(FULL, k != ~0ull);
@@ -848,11 +854,16 @@ lc_status upload(lc_index *ix)
         std::memcpy(c2b.data() + i * M2P, ix->codes2.data() + i * M2, M2);
         c2b[i * M2P + M2P - 1] = ix->beta[i];
     }
+    std::vector<__half> c1h(ix->C1.size());
+    for (size_t i = 0; i < c1h.size(); i++) c1h[i] = __float2half_rn(ix->C1[i]);   // round to nearest even
+    __half *c1h_dev = static_cast<__half *>(dv->C1h);
     bool ok = dupload(dv->Rt, Rt) && dupload(dv->C1, ix->C1) && dupload(dv->C2, ix->C2) &&
+              dupload(c1h_dev, c1h) &&
               dupload(dv->B, ix->B) && dupload(dv->codes1, ix->codes1) &&
               dupload(dv->codes2b, c2b) &&
               dupload(dv->adj0, ix->adj0) && dupload(dv->upper_off, off) &&
               dupload(dv->upper_adj, ix->upper_adj);
+    dv->C1h = c1h_dev;
     if (!ok) {
         set_error("device upload of the index failed: %s", cudaGetErrorString(cudaGetLastError()));
         return LC_ERR_OOM;
@@ -878,21 +889,21 @@ static int ilog2_ceil(int64_t x)
 constexpr size_t MAX_SMEM_PER_BLOCK = 227 * 1024;
 
 // Warps per CTA: as many as fit next to the codebook (at most MAX_WALK_WARPS).
-template <int M1, int D1>
+template <int M1, int D1, typename CT>
 static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int *wpc_out,
                                int *grid_out, size_t *smem_out)
 {
-    size_t c1 = walk_c1_bytes(wa.d);
+    size_t c1 = walk_c1_bytes(wa.d, sizeof(CT));
     if (c1 + smem_per_warp > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
     int wpc = (int)std::min<size_t>(MAX_WALK_WARPS, (MAX_SMEM_PER_BLOCK - c1) / smem_per_warp);
     size_t smem = c1 + smem_per_warp * wpc;
     // the attribute is an upper bound: set to the maximum, so plans made in any order (the
     // server plans at submission and launches later) all remain launchable
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)MAX_SMEM_PER_BLOCK);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1>, wpc * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1, CT>, wpc * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t need = (wa.nq + wpc - 1) / wpc;
@@ -902,11 +913,41 @@ static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num
     return cudaSuccess;
 }
 
-template <int M1, int D1>
+template <int M1, int D1, typename CT>
 static cudaError_t run_walk(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
 {
-    walk_kernel<M1, D1><<<grid, wpc * 32, smem, st>>>(wa);
+    walk_kernel<M1, D1, CT><<<grid, wpc * 32, smem, st>>>(wa);
     return cudaGetLastError();
+}
+
+// Dispatch on (sub-space width variant, codebook element type).
+template <typename CT>
+static cudaError_t launch_any(int variant, int M1, const WalkArgs &wa, size_t per_warp, int sms, int *wpc,
+                              int *grid, size_t *smem)
+{
+    switch (variant) {
+    case 1: return launch_walk<16, 6, CT>(wa, per_warp, sms, wpc, grid, smem);
+    case 2: return launch_walk<32, 3, CT>(wa, per_warp, sms, wpc, grid, smem);
+    case 3: return launch_walk<64, 2, CT>(wa, per_warp, sms, wpc, grid, smem);
+    default:
+        if (M1 == 16) return launch_walk<16, 0, CT>(wa, per_warp, sms, wpc, grid, smem);
+        if (M1 == 32) return launch_walk<32, 0, CT>(wa, per_warp, sms, wpc, grid, smem);
+        return launch_walk<64, 0, CT>(wa, per_warp, sms, wpc, grid, smem);
+    }
+}
+
+template <typename CT>
+static cudaError_t run_any(int variant, int M1, const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
+{
+    switch (variant) {
+    case 1: return run_walk<16, 6, CT>(wa, smem, wpc, grid, st);
+    case 2: return run_walk<32, 3, CT>(wa, smem, wpc, grid, st);
+    case 3: return run_walk<64, 2, CT>(wa, smem, wpc, grid, st);
+    default:
+        if (M1 == 16) return run_walk<16, 0, CT>(wa, smem, wpc, grid, st);
+        if (M1 == 32) return run_walk<32, 0, CT>(wa, smem, wpc, grid, st);
+        return run_walk<64, 0, CT>(wa, smem, wpc, grid, st);
+    }
 }
 
 lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl)
@@ -932,19 +973,12 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     WalkArgs wa{};
     wa.nq = nq;
     wa.d = dv->d;
-    cudaError_t ce;
-    switch (P.variant) {
-    case 1: ce = launch_walk<16, 6>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem); break;
-    case 2: ce = launch_walk<32, 3>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem); break;
-    case 3: ce = launch_walk<64, 2>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem); break;
-    default:
-        if (dv->M1 == 16) ce = launch_walk<16, 0>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
-        else if (dv->M1 == 32) ce = launch_walk<32, 0>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
-        else ce = launch_walk<64, 0>(wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
-    }
+    P.half = sp->lut_prec == LC_LUT_FP16;
+    cudaError_t ce = P.half ? launch_any<__half>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem)
+                            : launch_any<float>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
     if (ce == cudaErrorInvalidConfiguration) {
         set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
-                  "lower efSearch or visited_log", P.per_warp, walk_c1_bytes(dv->d));
+                  "lower efSearch or visited_log", P.per_warp, walk_c1_bytes(dv->d, P.half ? 2 : 4));
         return LC_ERR_CAPACITY;
     }
     if (ce != cudaSuccess) {
@@ -986,7 +1020,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
 {
     WalkArgs wa{};
     wa.Q = dq; wa.nq = nq; wa.d = dv->d;
-    wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.codes1 = dv->codes1;
+    wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.C1h = static_cast<const __half *>(dv->C1h); wa.codes1 = dv->codes1;
     wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
     wa.ep = dv->ep; wa.max_level = dv->max_level;
     wa.efp = P.efp; wa.efcap = (int)align_up(P.efp, 32);
@@ -1019,16 +1053,8 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(dv->ev[0], st);
     }
-    cudaError_t ce;
-    switch (P.variant) {
-    case 1: ce = run_walk<16, 6>(wa, P.smem, P.wpc, P.grid, st); break;
-    case 2: ce = run_walk<32, 3>(wa, P.smem, P.wpc, P.grid, st); break;
-    case 3: ce = run_walk<64, 2>(wa, P.smem, P.wpc, P.grid, st); break;
-    default:
-        if (dv->M1 == 16) ce = run_walk<16, 0>(wa, P.smem, P.wpc, P.grid, st);
-        else if (dv->M1 == 32) ce = run_walk<32, 0>(wa, P.smem, P.wpc, P.grid, st);
-        else ce = run_walk<64, 0>(wa, P.smem, P.wpc, P.grid, st);
-    }
+    cudaError_t ce = P.half ? run_any<__half>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st)
+                            : run_any<float>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st);
     if (profile) cudaEventRecord(dv->ev[1], st);
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
@@ -1263,15 +1289,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     int grid = 0, wpc = 1;
     size_t smem = 0;
     cudaError_t ce;
-    switch (variant) {
-    case 1: ce = launch_walk<16, 6>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem); break;
-    case 2: ce = launch_walk<32, 3>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem); break;
-    case 3: ce = launch_walk<64, 2>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem); break;
-    default:
-        if (dv->M1 == 16) ce = launch_walk<16, 0>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
-        else if (dv->M1 == 32) ce = launch_walk<32, 0>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
-        else ce = launch_walk<64, 0>(wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
-    }
+    ce = launch_any<float>(variant, dv->M1, wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
     if (ce != cudaSuccess) {
         set_error("walk kernel configuration failed: %s", cudaGetErrorString(ce));
         return ce == cudaErrorInvalidConfiguration ? LC_ERR_CAPACITY : LC_ERR_CUDA;
@@ -1284,15 +1302,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
         set_error("reset of the no-allocation scratch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return LC_ERR_CUDA;
     }
-    switch (variant) {
-    case 1: ce = run_walk<16, 6>(wa, smem, wpc, grid, st); break;
-    case 2: ce = run_walk<32, 3>(wa, smem, wpc, grid, st); break;
-    case 3: ce = run_walk<64, 2>(wa, smem, wpc, grid, st); break;
-    default:
-        if (dv->M1 == 16) ce = run_walk<16, 0>(wa, smem, wpc, grid, st);
-        else if (dv->M1 == 32) ce = run_walk<32, 0>(wa, smem, wpc, grid, st);
-        else ce = run_walk<64, 0>(wa, smem, wpc, grid, st);
-    }
+    ce = run_any<float>(variant, dv->M1, wa, smem, wpc, grid, st);
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
         return LC_ERR_CUDA;

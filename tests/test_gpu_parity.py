@@ -38,10 +38,11 @@ def handle(name, ix):
     return _handles[name]
 
 
-def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1, tcap=0):
+def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1, tcap=0, lut_prec=0):
     import torch
     nq = len(xq)
-    sp = lc.lc_default_search_params(k, ef, shortlist=shortlist, visited_log=visited_log, max_dist=tcap)
+    sp = lc.lc_default_search_params(k, ef, shortlist=shortlist, visited_log=visited_log, max_dist=tcap,
+                                     lut_prec=lut_prec)
     if beam > 1:
         sp.mode, sp.beam = lc.LC_MODE_BATCHED, beam
     if device:
@@ -121,6 +122,19 @@ def test_parity_tcap(opq3k, tcap, beam):
     h = handle("opq3k", ix)
     ref = oracle.search(ix, xq, 10, 128, beam=beam, tcap=tcap)
     compare(ref, *gpu_search(h, xq, 10, 128, beam=beam, tcap=tcap), max_exempt=0.1)
+
+
+@pytest.mark.parametrize("name", ["mix3k", "opq3k", "sift2k"])
+@pytest.mark.parametrize("beam", [1, 4])
+def test_parity_fp16_codebook(request, name, beam):
+    # FP16 form: the walk scores with C1 rounded to FP16 (nearest even); the oracle runs the
+    # same definition (walk codebook rounded, FP64 arithmetic, re-rank with the FP32 C1)
+    ix, xb, xq = request.getfixturevalue(name)
+    h = handle(name, ix)
+    c1h = ix.C1.astype(np.float16).astype(np.float32)
+    for shortlist in (0, -1):
+        ref = oracle.search(ix, xq, 10, 64, shortlist=shortlist, beam=beam, c1_walk=c1h)
+        compare(ref, *gpu_search(h, xq, 10, 64, shortlist, beam=beam, lut_prec=lc.LC_LUT_FP16), max_exempt=0.1)
 
 
 def test_parity_10k_workload(mix10k):
