@@ -646,8 +646,9 @@ __host__ __device__ inline size_t refine_smem(int M1, int M2P, int R)
 
 // One warp per query.  C2_SHARED: both codebooks sit in shared memory (d*4 bytes is a
 // multiple of 128, so lane t reading coordinate t of any centroid hits bank t mod 32);
-// otherwise only C1 does and C2 is read through the cache.
-template <bool C2_SHARED>
+// otherwise only C1 does and C2 is read through the cache.  DU: coordinates per lane
+// (d = 32 DU), or 8 with bounds checks for other d <= 256.
+template <bool C2_SHARED, int DU>
 __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -678,9 +679,9 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
     const int r1 = M1 / 16, r2 = M2P / 16;          // 16-byte pieces per row
     // sub-spaces of this lane's coordinates t = lane + 32 u (read once: indexing the
     // parameter space with a per-lane index would serialise)
-    int s1v[8], s2v[8];
+    int s1v[DU], s2v[DU];
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
+    for (int u = 0; u < DU; u++) {
         const int t = lane + 32 * u;
         s1v[u] = t < d ? a.sub1[t] : 0;
         s2v[u] = t < d ? a.sub2[t] : 0;
@@ -688,9 +689,9 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
 
     for (int64_t q = gwarp; q < a.nq; q += nwarps) {
         const int32_t *sl = a.shortlist + q * a.R;
-        float yv[8];
+        float yv[DU];
 #pragma unroll
-        for (int u = 0; u < 8; u++) yv[u] = lane + 32 * u < d ? a.yq[q * d + lane + 32 * u] : 0.f;
+        for (int u = 0; u < DU; u++) yv[u] = lane + 32 * u < d ? a.yq[q * d + lane + 32 * u] : 0.f;
         int rn = 0;                                  // shortlist entries present (packed first)
         for (int i = lane; i < a.R; i += 32) rn += sl[i] >= 0;
 #pragma unroll
@@ -744,22 +745,31 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
             }
             __syncwarp();
             for (int r = 0; r < nc; r++) {
+                // y^_t = sum_j beta_j (C1[c1_j][t] + C2[c2_j][t]) for this lane's coordinates,
+                // accumulated over j in order; then sum_t (y'_t - y^_t)^2 over t ascending
+                float yh[DU];
+#pragma unroll
+                for (int u = 0; u < DU; u++) yh[u] = 0.f;
+#pragma unroll
+                for (int j = 0; j < 9; j++) {
+                    const int tt = r * 9 + j;
+                    if (vid[tt] < 0) continue;
+                    const float w = wt[tt];
+                    const uint8_t *c1r = st1 + tt * M1, *c2r = st2 + tt * M2P;
+#pragma unroll
+                    for (int u = 0; u < DU; u++) {
+                        const int t = lane + 32 * u;
+                        if (DU == 8 && t >= d) continue;
+                        const float x = C1s[(int)c1r[s1v[u]] * d + t] + C2[(int)c2r[s2v[u]] * d + t];
+                        yh[u] = fmaf(w, x, yh[u]);
+                    }
+                }
                 float part = 0.f;
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const int t = lane + 32 * u;
-                    if (t < d) {
-                        float yh = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 9; j++) {
-                            const int tt = r * 9 + j;
-                            if (vid[tt] < 0) continue;
-                            float x = C1s[(int)st1[tt * M1 + s1v[u]] * d + t] + C2[(int)st2[tt * M2P + s2v[u]] * d + t];
-                            yh = fmaf(wt[tt], x, yh);
-                        }
-                        float df = yv[u] - yh;
-                        part = fmaf(df, df, part);
-                    }
+                for (int u = 0; u < DU; u++) {
+                    if (DU == 8 && lane + 32 * u >= d) continue;
+                    const float df = yv[u] - yh[u];
+                    part = fmaf(df, df, part);
                 }
 #pragma unroll
                 for (int m = 16; m > 0; m >>= 1) part += __shfl_xor_sync(FULL, part, m);
@@ -920,6 +930,17 @@ static cudaError_t run_walk(const WalkArgs &wa, size_t smem, int wpc, int grid, 
     return cudaGetLastError();
 }
 
+using RefineFn = void (*)(const RefineArgs);
+
+// Refinement instantiation: codebooks placement and coordinates per lane (3 for d = 96,
+// 4 for d = 128, else the checked 8).
+static RefineFn refine_kernel_for(bool both, int d)
+{
+    if (d == 96) return both ? refine_kernel<true, 3> : refine_kernel<false, 3>;
+    if (d == 128) return both ? refine_kernel<true, 4> : refine_kernel<false, 4>;
+    return both ? refine_kernel<true, 8> : refine_kernel<false, 8>;
+}
+
 // Dispatch on (sub-space width variant, codebook element type).
 template <typename CT>
 static cudaError_t launch_any(int variant, int M1, const WalkArgs &wa, size_t per_warp, int sms, int *wpc,
@@ -1001,7 +1022,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
         }
         P.rw = (int)std::min<size_t>(16, (MAX_SMEM_PER_BLOCK - cb) / per);
         P.rsm = cb + per * P.rw;
-        auto kern = P.rboth ? refine_kernel<true> : refine_kernel<false>;
+        auto kern = refine_kernel_for(P.rboth, dv->d);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM_PER_BLOCK) != cudaSuccess) {
             set_error("refine kernel configuration failed: %s", cudaGetErrorString(cudaGetLastError()));
             return LC_ERR_CUDA;
@@ -1070,7 +1091,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         splits(dv->d, dv->M2, o2, l2);
         for (int j = 0; j < dv->M1; j++) for (int t = off[j]; t < off[j] + len[j]; t++) ra.sub1[t] = (uint8_t)j;
         for (int j = 0; j < dv->M2; j++) for (int t = o2[j]; t < o2[j] + l2[j]; t++) ra.sub2[t] = (uint8_t)j;
-        auto kern = P.rboth ? refine_kernel<true> : refine_kernel<false>;
+        auto kern = refine_kernel_for(P.rboth, dv->d);
         kern<<<P.rgrid, P.rw * 32, P.rsm, st>>>(ra);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) {
