@@ -20,6 +20,11 @@ on one host core on a bounded sample of the same queries.  ``config.served`` mea
 request server (lc_serve_*): saturation QPS with the headline parameters, and p50/p99 latency
 under open-loop Poisson arrivals of mixed requests.
 
+--workload sift10m: 10M SIFT-like uint8 vectors (128-d, OPQ64 + residual PQ63 + 1 B = 128
+B/vector), 100k uint8 queries per step, each with its own efSearch drawn from {16, 32, 64,
+128, 256}; the sweep levels scale every query's efSearch by one factor, and recall is judged
+on the first 10k queries against exact search.  sift1m is the same at 1M vectors.
+
 --impl reference times the oracle itself (the slow restatement of the paper the GPU path
 is checked against) on the same workload, a bounded query sample per step.
 """
@@ -128,21 +133,35 @@ class Clocks:
 
 
 WORKLOADS = {
-    "mix1m": dict(n_base=1_000_000, n_train=100_000, n_query=10_000, d=96, centres=1024, M1=32, M2=31,
-                  opq=1, desc="1M x 96-d Gaussian-mixture (1024 centres), OPQ32 + residual PQ31 + 1 B codeword "
-                              "= 64 B/vector, degree 32, 10k queries/step"),
-    "mix10k": dict(n_base=10_000, n_train=10_000, n_query=1_000, d=96, centres=64, M1=16, M2=16, opq=0,
+    "mix1m": dict(kind="mixture", n_base=1_000_000, n_train=100_000, n_query=10_000, d=96, centres=1024,
+                  M1=32, M2=31, opq=1,
+                  desc="1M x 96-d Gaussian-mixture (1024 centres), OPQ32 + residual PQ31 + 1 B codeword "
+                       "= 64 B/vector, degree 32, 10k queries/step"),
+    "mix10k": dict(kind="mixture", n_base=10_000, n_train=10_000, n_query=1_000, d=96, centres=64, M1=16,
+                   M2=16, opq=0,
                    desc="10k x 96-d Gaussian-mixture (64 centres), PQ16 + residual PQ16 + 1 B codeword, "
                         "degree 32, 1k queries/step"),
+    "sift10m": dict(kind="sift", n_base=10_000_000, n_train=200_000, n_query=100_000, d=128, centres=1024,
+                    M1=64, M2=63, opq=1, uneven=(16, 32, 64, 128, 256), gt_sample=10_000,
+                    desc="10M x 128-d SIFT-like uint8 (1024 Gamma profiles), OPQ64 + residual PQ63 + 1 B "
+                         "codeword = 128 B/vector, degree 32, 100k uint8 queries/step with efSearch drawn "
+                         "per query from {16, 32, 64, 128, 256}; recall on the first 10k queries"),
+    "sift1m": dict(kind="sift", n_base=1_000_000, n_train=100_000, n_query=20_000, d=128, centres=1024,
+                   M1=64, M2=63, opq=1, uneven=(16, 32, 64, 128, 256), gt_sample=10_000,
+                   desc="1M x 128-d SIFT-like uint8 (1024 Gamma profiles), OPQ64 + residual PQ63 + 1 B "
+                        "codeword = 128 B/vector, degree 32, 20k uint8 queries/step with efSearch drawn "
+                        "per query from {16, 32, 64, 128, 256}; recall on the first 10k queries"),
 }
 
 
 def make_data(w):
+    """Training, database and query vectors (float32, or uint8 for the SIFT-like kind)."""
     from paper_1804_09996_gb300 import datagen as dg
-    xt = dg.gaussian_mixture(w["n_train"], w["d"], w["centres"], stream=dg.STREAM_TRAIN)
-    xb = dg.gaussian_mixture(w["n_base"], w["d"], w["centres"], stream=dg.STREAM_BASE)
-    xq = dg.gaussian_mixture(w["n_query"], w["d"], w["centres"], stream=dg.STREAM_QUERY)
-    return xt, xb, xq
+    if w["kind"] == "sift":
+        gen = lambda n, s: dg.sift_like(n, w["d"], w["centres"], stream=s)      # noqa: E731
+    else:
+        gen = lambda n, s: dg.gaussian_mixture(n, w["d"], w["centres"], stream=s)  # noqa: E731
+    return gen(w["n_train"], dg.STREAM_TRAIN), gen(w["n_base"], dg.STREAM_BASE), gen(w["n_query"], dg.STREAM_QUERY)
 
 
 def build_index(w, xt, xb):
@@ -150,31 +169,51 @@ def build_index(w, xt, xb):
     p = lc.lc_default_params(w["d"], w["M1"], w["M2"], use_opq=w["opq"])
     h = lc.lc_create(p)
     t0 = time.time()
-    lc.lc_train(h, xt)
+    lc.lc_train(h, xt.astype(np.float32))
     t1 = time.time()
-    lc.lc_add(h, xb)
+    if xb.dtype == np.uint8:
+        lc.lc_add_u8(h, xb)
+    else:
+        lc.lc_add(h, xb)
     t2 = time.time()
     log(f"index: train {t1 - t0:.1f} s, add {t2 - t1:.1f} s")
     return h, t2 - t0
 
 
 def exact_nn(xb, xq, device):
-    """Exact nearest neighbour of each query: FP32 distances on the GPU to pick 16
-    candidates, then an FP64 recheck on the host (measurement only)."""
+    """Exact nearest neighbour of each query and its squared distance: FP32 distances on the
+    GPU to pick 16 candidates, then an FP64 recheck on the host (measurement only)."""
     import torch
-    X = torch.from_numpy(xb).to(device)
+    X = torch.from_numpy(xb).to(device).float()
     xx = (X * X).sum(1)
+    chunk = int(max(64, min(1024, (4 << 30) // (4 * len(xb)))))    # <= 4 GB of distances at a time
     out = np.empty(len(xq), np.int64)
-    for a in range(0, len(xq), 1024):
-        Q = torch.from_numpy(xq[a:a + 1024]).to(device)
+    out_d = np.empty(len(xq), np.float64)
+    for a in range(0, len(xq), chunk):
+        Q = torch.from_numpy(xq[a:a + chunk]).to(device).float()
         D = xx[None, :] - 2.0 * (Q @ X.T)
         cand = torch.topk(D, 16, dim=1, largest=False).indices.cpu().numpy()
-        q64 = xq[a:a + 1024].astype(np.float64)
+        del D
+        q64 = xq[a:a + chunk].astype(np.float64)
         for i in range(len(cand)):
             c = np.sort(cand[i])
             dd = ((xb[c].astype(np.float64) - q64[i]) ** 2).sum(1)
-            out[a + i] = c[np.lexsort((c, dd))[0]]
-    return out
+            j = np.lexsort((c, dd))[0]
+            out[a + i], out_d[a + i] = c[j], dd[j]
+    del X, xx
+    torch.cuda.empty_cache()
+    return out, out_d
+
+
+def recall_at_1(top1, xb, xq, gt_d):
+    """Fraction of the first len(gt_d) queries whose returned first neighbour is at the exact
+    nearest-neighbour distance (equal distances count: integer-valued vectors tie exactly)."""
+    n = len(gt_d)
+    ids = top1[:n]
+    ok = ids >= 0
+    d = np.full(n, np.inf)
+    d[ok] = ((xb[ids[ok]].astype(np.float64) - xq[:n][ok].astype(np.float64)) ** 2).sum(1)
+    return float((d <= gt_d).mean())
 
 
 def oracle_view(h, w):
@@ -189,12 +228,30 @@ def oracle_view(h, w):
                        max_level=int(ex["levels"].max()), levels=ex["levels"])
 
 
-def time_oracle(oix, xq, k, ef, budget_s):
+def uneven_ef(w, n, scale=1.0):
+    """Per-query efSearch of an uneven workload (None otherwise), scaled for the sweeps."""
+    if "uneven" not in w:
+        return None
+    from paper_1804_09996_gb300 import datagen as dg
+    e = dg.uneven_ef(n, choices=w["uneven"])
+    return np.maximum(1, np.round(e * scale)).astype(np.int32)
+
+
+def oracle_batch(oix, q, k, ef, efq=None):
+    """The oracle on a batch of queries: one efSearch, or each query's own (efq)."""
     import oracle
+    if efq is None:
+        return oracle.search(oix, q, k, ef)
+    for e in np.unique(efq):
+        oracle.search(oix, q[efq == e], k, int(e))
+
+
+def time_oracle(oix, xq, k, ef, budget_s, efq=None):
     done, t0 = 0, time.perf_counter()
     while done < len(xq) and time.perf_counter() - t0 < budget_s:
-        oracle.search(oix, xq[done:done + 50], k, ef)
-        done += min(50, len(xq) - done)
+        n = min(50, len(xq) - done)
+        oracle_batch(oix, xq[done:done + n], k, ef, None if efq is None else efq[done:done + n])
+        done += n
     return done, time.perf_counter() - t0
 
 
@@ -312,13 +369,14 @@ def run_reference(args, w, ws, rank):
     oix = oracle_view(h, w)
     lc.lc_free(h)
     sample = 200 if w["n_base"] >= 100_000 else len(xq)
+    efq = uneven_ef(w, len(xq))
     for s in range(args.warmup):
         oracle.search(oix, xq[:20], args.k, args.ef)
     times = []
     for s in range(args.steps):
-        q = xq[(s * sample) % len(xq):(s * sample) % len(xq) + sample]
+        a = (s * sample) % len(xq)
         t0 = time.perf_counter()
-        oracle.search(oix, q, args.k, args.ef)
+        oracle_batch(oix, xq[a:a + sample], args.k, args.ef, None if efq is None else efq[a:a + sample])
         times.append(time.perf_counter() - t0)
     qps = sample * args.steps / sum(times)
     line = {
@@ -326,8 +384,8 @@ def run_reference(args, w, ws, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": w["desc"], "k": args.k, "efSearch": args.ef,
-                   "queries_per_step": sample},
+        "config": {"workload": args.workload, "desc": w["desc"], "k": args.k,
+                   "efSearch": "per query" if efq is not None else args.ef, "queries_per_step": sample},
         "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle",
                          "sample": f"{sample} queries per step of the {len(xq)}-query set, 1 thread, FP64"},
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -369,8 +427,13 @@ def main():
     torch.cuda.set_device(dev)
     xt, xb, xq = make_data(w)
     h, build_s = build_index(w, xt, xb)
-    gt = exact_nn(xb, xq, f"cuda:{dev}")
+    del xt
+    n_gt = min(len(xq), w.get("gt_sample", len(xq)))
+    gt, gt_d = exact_nn(xb, xq[:n_gt], f"cuda:{dev}")
     nq, k, d = len(xq), args.k, w["d"]
+    u8 = xq.dtype == np.uint8
+    qtype = lc.LC_QUERY_U8 if u8 else lc.LC_QUERY_F32
+    uneven = "uneven" in w
     q = torch.from_numpy(xq).cuda()
     ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
     dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
@@ -379,9 +442,20 @@ def main():
     stream = torch.cuda.Stream()
     lc.lc_profile(h, True)
 
-    def measure(sp, steps):
+    def params(level, mode, prec=lc.LC_LUT_FP32):
+        """Search parameters at one sweep level: efSearch, or (uneven workloads) the factor
+        every query's own efSearch is scaled by; returns (sp, host efq or None)."""
+        efq = uneven_ef(w, nq, level)
+        ef = int(efq.max()) if uneven else int(level)
+        sp = lc.lc_default_search_params(k, ef, mode=mode, beam=args.beam if mode == lc.LC_MODE_BATCHED else 1,
+                                         lut_prec=prec)
+        return sp, efq
+
+    def measure(form, steps):
+        sp, efq = form
+        de = None if efq is None else torch.from_numpy(efq).cuda()
         for _ in range(max(3, args.warmup)):
-            lc.lc_search(h, q, nq, sp, ids, dists, stats, stream)
+            lc.lc_search_ex(h, q, qtype, nq, sp, de, ids, dists, stats, stream)
         stream.synchronize()
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -393,7 +467,7 @@ def main():
             with torch.cuda.stream(stream):
                 flush.sum(dtype=torch.int64)          # read 256 MB: evicts L2 without dirty lines
                 ev0[s].record(stream)
-            lc.lc_search(h, q, nq, sp, ids, dists, stats, stream)
+            lc.lc_search_ex(h, q, qtype, nq, sp, de, ids, dists, stats, stream)
             ev1[s].record(stream)
             wm, rm = lc.lc_profile_read(h)
             walk_ms.append(wm)
@@ -404,74 +478,85 @@ def main():
         ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)])), ws)
         got = ids.cpu().numpy()
         return dict(ms=ms, qps=nq * ws / (ms / 1e3), walk_ms=float(np.mean(walk_ms)),
-                    refine_ms=float(np.mean(refine_ms)), recall=float((got[:, 0] == gt).mean()),
+                    refine_ms=float(np.mean(refine_ms)), recall=recall_at_1(got[:, 0], xb, xq, gt_d),
                     stats=stats.cpu().numpy().astype(np.int64), wall=wall)
 
     clocks = Clocks(dev)
-    sp_plain = lc.lc_default_search_params(k, args.ef)
+    base_level = 1.0 if uneven else args.ef
+    # sweep levels of the batched forms: efSearch values, or scale factors of the per-query ones
+    levels = ((0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 1.0, 1.25, 1.5, 2.0) if uneven else
+              sorted({e for e in (16, 24, 32, 40, 48, 56, 64, 80, 96, 128) if e <= max(2 * args.ef, 16)}))
     batched = None
     if args.mode == "batched":
-        sp_b = lc.lc_default_search_params(k, args.ef, mode=lc.LC_MODE_BATCHED, beam=args.beam)
-        batched = measure(sp_b, args.steps)
-        batched.update(ef=args.ef, sweep=[])
+        f_b = params(base_level, lc.LC_MODE_BATCHED)
+        batched = measure(f_b, args.steps)
+        batched.update(ef=base_level, sweep=[])
         plain, target = None, batched["recall"]
-        best, best_sp, best_name = batched, sp_b, f"batched(beam={args.beam})"
+        best, best_form, best_name = batched, f_b, f"batched(beam={args.beam})"
     else:
-        plain = measure(sp_plain, args.steps)
+        f_p = params(base_level, lc.LC_MODE_PLAIN)
+        plain = measure(f_p, args.steps)
+        plain.update(ef=base_level)
         target = plain["recall"]
-        best, best_sp, best_name = plain, sp_plain, "plain"
+        best, best_form, best_name = plain, f_p, "plain"
     forms = {}
     if args.mode == "both" and args.beam > 1:
-        # the cheapest efSearch at which each faster form reaches the plain form's recall
+        # the cheapest level at which each faster form reaches the plain form's recall
         for name, prec in (("batched", lc.LC_LUT_FP32), ("batched_fp16", lc.LC_LUT_FP16)):
             sweep = []
-            for ef_b in sorted({e for e in (16, 24, 32, 40, 48, 56, 64, 80, 96, 128) if e <= max(2 * args.ef, 16)}):
-                sp_b = lc.lc_default_search_params(k, ef_b, mode=lc.LC_MODE_BATCHED, beam=args.beam, lut_prec=prec)
-                r = measure(sp_b, max(10, args.steps // 5))
-                sweep.append((ef_b, r["recall"], r["qps"]))
+            for lv in levels:
+                r = measure(params(lv, lc.LC_MODE_BATCHED, prec), max(10, args.steps // 5))
+                sweep.append((lv, r["recall"], r["qps"]))
                 if r["recall"] >= target:
                     break
-            ef_b = sweep[-1][0]
-            sp_b = lc.lc_default_search_params(k, ef_b, mode=lc.LC_MODE_BATCHED, beam=args.beam, lut_prec=prec)
-            r = measure(sp_b, args.steps)
-            r.update(ef=ef_b, sweep=sweep, sp=sp_b)
+            lv = sweep[-1][0]
+            f_b = params(lv, lc.LC_MODE_BATCHED, prec)
+            r = measure(f_b, args.steps)
+            r.update(ef=lv, sweep=sweep)
             forms[name] = r
             if r["recall"] >= target and r["qps"] > best["qps"]:
-                best, best_sp = r, sp_b
+                best, best_form = r, f_b
                 best_name = f"batched(beam={args.beam}){', fp16 codebook' if prec else ''}"
         batched = forms.get("batched")
     clk = clocks.stop()
     if args.mode == "both" and best is not plain:   # leave the headline's counters in `stats`
-        measure(best_sp, 3)
+        measure(best_form, 3)
         best = dict(best, stats=stats.cpu().numpy().astype(np.int64))
 
     # walk kernel: algorithmic bytes per launch, from its own counters
     st = best["stats"]
     M1 = w["M1"]
     R = max(10, k)
-    b_walk = int((st[:, 1] * 128 + (st[:, 0] + st[:, 2]) * M1).sum() + nq * (4 * d + 4 * d + 4 * R))
+    qbytes = d * (1 if u8 else 4) + (4 if uneven else 0)
+    b_walk = int((st[:, 1] * 128 + (st[:, 0] + st[:, 2]) * M1).sum() + nq * (qbytes + 4 * d + 4 * R))
     walk_s = best["walk_ms"] / 1e3
     peak, peak_src = peaks()
     achieved = b_walk / walk_s / 1e9
     traffic = None if "fp16" in best_name else profiled_traffic(args.workload, "plain" if best_name == "plain" else "batched")
 
     # e2e through the same C ABI call with pinned host buffers
+    best_sp, best_efq = best_form
     hq = torch.from_numpy(xq).pin_memory()
+    he = None if best_efq is None else torch.from_numpy(best_efq).pin_memory()
     hi = torch.empty((nq, k), dtype=torch.int32).pin_memory()
     hd = torch.empty((nq, k), dtype=torch.float32).pin_memory()
     lc.lc_profile(h, False)
-    lc.lc_search(h, hq.numpy(), nq, best_sp, hi.numpy(), hd.numpy())
+
+    def e2e_call():
+        lc.lc_search_ex(h, hq.numpy(), qtype, nq, best_sp, None if he is None else he.numpy(), hi.numpy(), hd.numpy())
+
+    e2e_call()
     e2e_t = []
     for s in range(max(3, args.steps // 2)):
         flush.sum(dtype=torch.int64)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lc.lc_search(h, hq.numpy(), nq, best_sp, hi.numpy(), hd.numpy())
+        e2e_call()
         e2e_t.append(time.perf_counter() - t0)
     e2e = nq / float(np.mean(e2e_t))
 
     served = None
-    if args.serve and ws == 1:
+    if args.serve and ws == 1 and not uneven and not u8:
         served = measure_serving(lc, h, xq, gt, k, args, best_sp)
 
     cpu = None
@@ -479,10 +564,11 @@ def main():
         import oracle
         oracle.build()
         oix = oracle_view(h, w)
-        n_done, el = time_oracle(oix, xq, k, args.ef, args.cpu_budget)
+        efq0 = uneven_ef(w, nq)
+        n_done, el = time_oracle(oix, xq, k, args.ef, args.cpu_budget, efq0)
         cpu = {"value": n_done / el, "unit": "queries/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {n_done} of the {nq} queries, k={k}, efSearch={args.ef}, plain, "
-                         f"1 thread, FP64"}
+               "sample": f"first {n_done} of the {nq} queries, k={k}, "
+                         f"{'per-query efSearch' if uneven else f'efSearch={args.ef}'}, plain, 1 thread, FP64"}
     lc.lc_free(h)
     if rank != 0:
         return
@@ -501,7 +587,9 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "k": k, "headline_form": best_name,
                    "recall_target": target, "recall_at_1": best["recall"], "queries_per_step": nq,
-                   "plain": None if plain is None else summary(plain, args.ef),
+                   "recall_queries": n_gt,
+                   "efSearch_levels": ("factor applied to every query's own efSearch" if uneven else "efSearch"),
+                   "plain": None if plain is None else summary(plain, plain["ef"]),
                    "batched": None if batched is None else summary(
                        batched, batched["ef"], {"beam": args.beam, "sweep": batched["sweep"]}),
                    "batched_fp16": None if "batched_fp16" not in forms else summary(
@@ -515,7 +603,8 @@ def main():
                      "frac": achieved / peak, "traffic": traffic, "kernel": "walk_kernel",
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": b_walk},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
+        "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": int(hq.numel() * hq.element_size()) + (
+                    0 if he is None else int(he.numel() * 4)),
                 "d2h_bytes_per_step": nq * k * 8},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,

@@ -119,6 +119,10 @@ lc_status lc_train(lc_index *ix, const float *xt, int64_t nt);
  * LC_ERR_STATE (not trained), LC_ERR_OOM. */
 lc_status lc_add(lc_index *ix, const float *x, int64_t n);
 
+/* lc_add for uint8 vectors x [n][d] (integer-valued descriptors, Section 5.1), converted
+ * exactly to float32 on the host first (n * d * 4 bytes of host memory for the call). */
+lc_status lc_add_u8(lc_index *ix, const uint8_t *x, int64_t n);
+
 /* k-NN search for nq queries q [nq][d] (float32): ADC walk over the nested graphs, then
  * re-rank of the shortlist with the refined reconstruction (Section 4.1, 4.3).
  * Outputs: ids [nq][k] (int32, -1 where fewer than k results), dists [nq][k] (float32
@@ -135,6 +139,23 @@ lc_status lc_add(lc_index *ix, const float *x, int64_t n);
  * pointers report it as stats n_dist = -1 for that query). */
 lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
                     int32_t *ids, float *dists, int32_t *stats, void *stream);
+
+/* Query element types of lc_search_ex. */
+enum { LC_QUERY_F32 = 0, LC_QUERY_U8 = 1 };
+
+/* lc_search with two generalisations (the search itself is the one of Section 2, 4.1, 4.3):
+ * - qtype LC_QUERY_U8: q points to uint8 queries [nq][d] (integer-valued descriptors such as
+ *   SIFT, Section 5.1), converted exactly to float32 on the device; LC_QUERY_F32: float32
+ *   [nq][d] as in lc_search.
+ * - ef non-NULL: per-query efSearch [nq] (int32, same memory kind as q).  Query i walks with
+ *   ef' = max(ef[i], k); sp->ef is the bound every ef[i] must respect (it sizes the per-query
+ *   state, so a small bound keeps more queries in flight).  Host arrays are checked
+ *   (LC_ERR_ARG for ef[i] outside 1..sp->ef); device arrays are clamped into 1..sp->ef.
+ *   Each query's result equals that of lc_search with sp->ef = ef[i].
+ * Everything else (pointer kinds, outputs, errors, stream semantics) is as lc_search;
+ * lc_search(...) is lc_search_ex with LC_QUERY_F32 and ef = NULL. */
+lc_status lc_search_ex(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_search_params *sp,
+                       const int32_t *ef, int32_t *ids, float *dists, int32_t *stats, void *stream);
 
 /* Replaces the index's content with caller-provided host arrays (copied): rotation R
  * [d][d] (y' = R y), level-1 and level-2 centroids C1, C2 [256][d] (full width: row c holds

@@ -140,22 +140,44 @@ lc_status lc_add(lc_index *ix, const float *x, int64_t n)
     }
 }
 
-lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
-                    int32_t *ids, float *dists, int32_t *stats, void *stream)
+lc_status lc_add_u8(lc_index *ix, const uint8_t *x, int64_t n)
+{
+    set_error("");
+    if (!ix || (!x && n > 0) || n < 0) { set_error("null index or vectors, or negative count"); return LC_ERR_ARG; }
+    std::vector<float> xf;
+    try {
+        xf.resize((size_t)n * ix->p.d);
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory converting %lld uint8 vectors", (long long)n);
+        return LC_ERR_OOM;
+    }
+    for (size_t i = 0; i < xf.size(); i++) xf[i] = (float)x[i];
+    return lc_add(ix, xf.data(), n);
+}
+
+lc_status lc_search_ex(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_search_params *sp,
+                       const int32_t *ef, int32_t *ids, float *dists, int32_t *stats, void *stream)
 {
     set_error("");
     if (!ix || !sp) { set_error("null index or search parameters"); return LC_ERR_ARG; }
     if (nq < 0 || (nq > 0 && (!q || !ids || !dists))) { set_error("null query or output buffer"); return LC_ERR_ARG; }
+    if (qtype != LC_QUERY_F32 && qtype != LC_QUERY_U8) { set_error("query type %d is neither LC_QUERY_F32 nor LC_QUERY_U8", qtype); return LC_ERR_ARG; }
     lc_status cs = check_search_params(sp);
     if (cs != LC_OK) return cs;
     if (!ix->trained) { set_error("search before lc_train/lc_import"); return LC_ERR_STATE; }
     if (ix->n > 0 && !ix->has_codebook) { set_error("index has no regression codebook"); return LC_ERR_STATE; }
     try {
-        return lc::search(ix, q, nq, sp, ids, dists, stats, stream);
+        return lc::search(ix, q, qtype, nq, sp, nq > 0 ? ef : nullptr, ids, dists, stats, stream);
     } catch (const std::bad_alloc &) {
         set_error("out of host memory during search");
         return LC_ERR_OOM;
     }
+}
+
+lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
+                    int32_t *ids, float *dists, int32_t *stats, void *stream)
+{
+    return lc_search_ex(ix, q, LC_QUERY_F32, nq, sp, nullptr, ids, dists, stats, stream);
 }
 
 lc_status lc_import(lc_index *ix, int64_t n, const float *R, const float *C1, const float *C2,

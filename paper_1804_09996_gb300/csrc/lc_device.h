@@ -27,6 +27,7 @@ struct DeviceIndex {
     unsigned long long *counter = nullptr;
     // staging for host-pointer calls
     float *q_st = nullptr; size_t q_cap = 0;
+    int32_t *ef_st = nullptr; size_t ef_cap = 0;
     int32_t *ids_st = nullptr; float *d_st = nullptr; int32_t *s_st = nullptr; size_t out_cap = 0;
     // profiling
     bool profile = false;
@@ -60,7 +61,10 @@ struct SearchScratch {
 lc_status upload(lc_index *ix);
 lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl);
 // Queues the walk (and refinement) on `st`; q, ids, dists, stats are device pointers.
+// q8 (uint8 queries [nq][d], replacing q) and efq (per-query efSearch [nq]) are optional
+// device pointers.
 lc_status run_search(DeviceIndex *dv, const SearchPlan &pl, const float *q, int64_t nq, int32_t *ids,
-                     float *dists, int32_t *stats, const SearchScratch &sc, cudaStream_t st, bool profile);
+                     float *dists, int32_t *stats, const SearchScratch &sc, cudaStream_t st, bool profile,
+                     const uint8_t *q8 = nullptr, const int32_t *efq = nullptr);
 
 }  // namespace lc

@@ -61,8 +61,8 @@ void decode_all(const lc_index *ix, std::vector<float> &xh);
 int n_threads(const lc_params &p);
 
 // Device search (lc_search.cu).
-lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
-                 int32_t *ids, float *dists, int32_t *stats, void *stream);
+lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_search_params *sp,
+                 const int32_t *efq, int32_t *ids, float *dists, int32_t *stats, void *stream);
 lc_status profile_enable(lc_index *ix, int on);
 lc_status merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, int k, const int64_t *offsets,
                      int32_t *ids_out, float *dists_out, void *stream);

@@ -52,7 +52,7 @@ void device_free(DeviceIndex *dv)
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
-    cfree(dv->q_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
+    cfree(dv->q_st); cfree(dv->ef_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
     for (auto &e : dv->ev) if (e) cudaEventDestroy(e);
     if (cur >= 0) cudaSetDevice(cur);
     delete dv;
@@ -67,6 +67,9 @@ struct SplitTab {
 
 struct WalkArgs {
     const float *Q;
+    const uint8_t *Q8;     // non-null: the queries are uint8 [nq][d] (Q unused)
+    const int32_t *efq;    // non-null: per-query efSearch [nq], clamped to 1..efp
+    int k;
     int64_t nq;
     int d;
     const float *Rt, *C1;
@@ -75,7 +78,7 @@ struct WalkArgs {
     const int32_t *adj0, *upper_off, *upper_adj;
     int32_t ep;
     int max_level;
-    int efp;          // ef' = max(ef, k)
+    int efp;          // ef' = max(ef, k); with efq, the largest any query may use
     int efcap;        // efp rounded up to a multiple of 32
     int R;            // shortlist length (refine) or k (no refinement)
     int refine;
@@ -408,12 +411,23 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         if (lane == 0) q = atomicAdd(a.counter, 1ull);
         q = __shfl_sync(FULL, q, 0);
         if (q >= a.nq) break;
-        // rotation y' = R y (fixed order u = 0..d-1)
-        const float *y = a.Q + q * d;
-        for (int t = lane; t < d; t += 32) {
-            float s = 0.f;
-            for (int u = 0; u < d; u++) s = fmaf(__ldg(a.Rt + (int64_t)u * d + t), __ldg(y + u), s);
-            yq[t] = s;
+        // this query's ef' = max(ef, k)
+        const int efp = a.efq ? max(min(max(__ldg(a.efq + q), 1), a.efp), a.k) : a.efp;
+        // rotation y' = R y (fixed order u = 0..d-1); uint8 queries convert exactly to FP32
+        if (a.Q8) {
+            const uint8_t *y = a.Q8 + q * d;
+            for (int t = lane; t < d; t += 32) {
+                float s = 0.f;
+                for (int u = 0; u < d; u++) s = fmaf(__ldg(a.Rt + (int64_t)u * d + t), (float)__ldg(y + u), s);
+                yq[t] = s;
+            }
+        } else {
+            const float *y = a.Q + q * d;
+            for (int t = lane; t < d; t += 32) {
+                float s = 0.f;
+                for (int u = 0; u < d; u++) s = fmaf(__ldg(a.Rt + (int64_t)u * d + t), __ldg(y + u), s);
+                yq[t] = s;
+            }
         }
         for (int i = lane; i < H; i += 32) hash[i] = -1;
         __syncwarp();
@@ -525,7 +539,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             __syncwarp();
             if (ns == 0) { scan_from = pos0; continue; }
             // score the fresh nodes 32 at a time; keep those that can enter W
-            const uint64_t wmax = wn == a.efp ? W[wn - 1] : ~0ull;
+            const uint64_t wmax = wn == efp ? W[wn - 1] : ~0ull;
             int nc = 0;
             for (int ch = 0; ch < ns; ch += 32) {
                 const int nf = min(32, ns - ch);
@@ -546,10 +560,10 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                 cand[r] = mk;
             }
             __syncwarp();
-            // merge W (wn keys) with the nc candidates into the other buffer, keep efp
+            // merge W (wn keys) with the nc candidates into the other buffer, keep ef'
             uint64_t *W2 = wkey + (buf ^ 1) * a.efcap;
             uint8_t *F2 = wflag + (buf ^ 1) * a.efcap;
-            const int wn2 = min(a.efp, wn + nc);
+            const int wn2 = min(efp, wn + nc);
             for (int p = lane; p < wn; p += 32) {
                 const uint64_t key = W[p];
                 int lo = 0, hi = nc;                     // candidates below key
@@ -560,7 +574,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                 const int np = p + lo;
                 if (np < wn2) { W2[np] = key; F2[np] = F[p]; }
             }
-            int first_new = a.efp;
+            int first_new = efp;
             for (int m0 = lane; m0 < nc; m0 += 32) {
                 const uint64_t ck = cand[m0];
                 int lo = 0, hi = wn;                     // W members below the candidate
@@ -1037,10 +1051,11 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
 }
 
 lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int64_t nq, int32_t *dids,
-                     float *ddists, int32_t *dstats, const SearchScratch &sc, cudaStream_t st, bool profile)
+                     float *ddists, int32_t *dstats, const SearchScratch &sc, cudaStream_t st, bool profile,
+                     const uint8_t *dq8, const int32_t *defq)
 {
     WalkArgs wa{};
-    wa.Q = dq; wa.nq = nq; wa.d = dv->d;
+    wa.Q = dq; wa.Q8 = dq8; wa.efq = defq; wa.k = P.k; wa.nq = nq; wa.d = dv->d;
     wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.C1h = static_cast<const __half *>(dv->C1h); wa.codes1 = dv->codes1;
     wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
     wa.ep = dv->ep; wa.max_level = dv->max_level;
@@ -1107,8 +1122,8 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
     return LC_OK;
 }
 
-lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_params *sp,
-                 int32_t *ids, float *dists, int32_t *stats, void *stream_)
+lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_search_params *sp,
+                 const int32_t *efq, int32_t *ids, float *dists, int32_t *stats, void *stream_)
 {
     cudaStream_t st = (cudaStream_t)stream_;
     const int k = sp->k;
@@ -1122,11 +1137,20 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
         return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
     };
     int kq = kind(q), ki = kind(ids), kd = kind(dists), ks = stats ? kind(stats) : kq;
-    if (kq != ki || kq != kd || kq != ks) {
-        set_error("query and output pointers must all be host or all be device memory");
+    int ke = efq ? kind(efq) : kq;
+    if (kq != ki || kq != kd || kq != ks || kq != ke) {
+        set_error("query, efSearch and output pointers must all be host or all be device memory");
         return LC_ERR_ARG;
     }
     const bool dev_ptrs = kq == 1;
+    const bool u8 = qtype == LC_QUERY_U8;
+    if (efq && !dev_ptrs) {
+        for (int64_t i = 0; i < nq; i++)
+            if (efq[i] < 1 || efq[i] > sp->ef) {
+                set_error("efSearch of query %lld is %d, outside 1..%d", (long long)i, efq[i], sp->ef);
+                return LC_ERR_ARG;
+            }
+    }
     lc_status rs = upload(ix);
     if (rs != LC_OK) return rs;
     DeviceIndex *dv = ix->dev;
@@ -1134,7 +1158,8 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
     rs = plan_search(dv, std::max<int64_t>(nq, 1), sp, &P);
     if (rs != LC_OK) return rs;
     if (nq == 0) return LC_OK;
-    const float *dq = q;
+    const void *dq = q;
+    const int32_t *defq = efq;
     int32_t *dids = ids, *dstats = stats;
     float *ddists = dists;
     if (!dev_ptrs) {
@@ -1153,11 +1178,17 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
             }
             dv->out_cap = need;
         }
-        if (cudaMemcpyAsync(dv->q_st, q, sizeof(float) * nq * dv->d, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        if (efq && !grow(dv->ef_st, dv->ef_cap, (size_t)nq)) {
+            set_error("cudaMalloc failed for efSearch staging");
+            return LC_ERR_OOM;
+        }
+        if (cudaMemcpyAsync(dv->q_st, q, (u8 ? 1 : sizeof(float)) * nq * dv->d, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            (efq && cudaMemcpyAsync(dv->ef_st, efq, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st) != cudaSuccess)) {
             set_error("query upload failed: %s", cudaGetErrorString(cudaGetLastError()));
             return LC_ERR_CUDA;
         }
         dq = dv->q_st;
+        if (efq) defq = dv->ef_st;
         dids = dv->ids_st;
         ddists = dv->d_st;
         dstats = dv->s_st;
@@ -1184,7 +1215,8 @@ lc_status search(lc_index *ix, const float *q, int64_t nq, const lc_search_param
     sc.spill = dv->spill;
     sc.status = dv->status;
     sc.counter = dv->counter;
-    rs = run_search(dv, P, dq, nq, dids, ddists, dstats, sc, st, dv->profile);
+    rs = run_search(dv, P, u8 ? nullptr : static_cast<const float *>(dq), nq, dids, ddists, dstats, sc, st,
+                    dv->profile, u8 ? static_cast<const uint8_t *>(dq) : nullptr, defq);
     if (rs != LC_OK) return rs;
     if (!dev_ptrs) {
         cudaMemcpyAsync(ids, dids, sizeof(int32_t) * nq * k, cudaMemcpyDeviceToHost, st);
@@ -1292,7 +1324,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.codes1 = dv->codes1;
     wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
     wa.ep = dv->ep; wa.max_level = dv->max_level;
-    wa.efp = efp; wa.efcap = (int)align_up(efp, 32);
+    wa.efp = efp; wa.efcap = (int)align_up(efp, 32); wa.k = k;
     wa.R = k; wa.refine = 0;
     wa.beam = 1;
     wa.hash_log = std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));

@@ -17,9 +17,11 @@ LC_OK, LC_ERR_ARG, LC_ERR_OOM, LC_ERR_STATE, LC_ERR_CUDA = 0, 1, 2, 3, 4
 LC_ERR_TIMEOUT, LC_ERR_BUDGET, LC_ERR_IO, LC_ERR_CAPACITY = 5, 6, 7, 8
 LC_MODE_PLAIN, LC_MODE_BATCHED = 0, 1
 LC_LUT_FP32, LC_LUT_FP16 = 0, 1
+LC_QUERY_F32, LC_QUERY_U8 = 0, 1
 
 EXPORTED = [
-    "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_search",
+    "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_add_u8",
+    "lc_search", "lc_search_ex",
     "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
     "lc_profile_read", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
     "lc_serve_open", "lc_serve_submit", "lc_serve_poll", "lc_serve_close", "lc_merge_topk",
@@ -69,7 +71,9 @@ def lib() -> ctypes.CDLL:
         "lc_create": (I, [P, P]),
         "lc_train": (I, [P, P, I64]),
         "lc_add": (I, [P, P, I64]),
+        "lc_add_u8": (I, [P, P, I64]),
         "lc_search": (I, [P, P, I64, P, P, P, P, P]),
+        "lc_search_ex": (I, [P, P, I, I64, P, P, P, P, P, P]),
         "lc_import": (I, [P, I64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int32]),
         "lc_size": (I64, [P]),
         "lc_upper_rows": (I64, [P]),
@@ -151,6 +155,11 @@ def lc_add(ix, x: np.ndarray):
     _check(lib().lc_add(ix, _ptr(x), x.shape[0]))
 
 
+def lc_add_u8(ix, x: np.ndarray):
+    x = np.ascontiguousarray(x, np.uint8)
+    _check(lib().lc_add_u8(ix, _ptr(x), x.shape[0]))
+
+
 def lc_search(ix, q, nq: int, sp: lc_search_params, ids, dists, stats=None, stream=None):
     """q [nq][d] float32, ids [nq][k] int32, dists [nq][k] float32, stats [nq][3] int32 or
     None: all numpy (host) or all torch CUDA tensors (device; queued on ``stream``, a
@@ -160,6 +169,16 @@ def lc_search(ix, q, nq: int, sp: lc_search_params, ids, dists, stats=None, stre
         s = s.cuda_stream
     _check(lib().lc_search(ix, _ptr(q), nq, ctypes.byref(sp), _ptr(ids), _ptr(dists), _ptr(stats),
                            ctypes.c_void_p(s) if s else None))
+
+
+def lc_search_ex(ix, q, qtype: int, nq: int, sp: lc_search_params, ef, ids, dists, stats=None, stream=None):
+    """lc_search with uint8 queries (qtype LC_QUERY_U8, q [nq][d] uint8) and/or per-query
+    efSearch (ef [nq] int32, or None); buffers as lc_search."""
+    s = stream
+    if s is not None and hasattr(s, "cuda_stream"):
+        s = s.cuda_stream
+    _check(lib().lc_search_ex(ix, _ptr(q), qtype, nq, ctypes.byref(sp), _ptr(ef), _ptr(ids), _ptr(dists),
+                              _ptr(stats), ctypes.c_void_p(s) if s else None))
 
 
 def lc_search_walk_noalloc(ix, q, nq: int, k: int, ef: int, ids, dists, stats=None, stream=None):

@@ -21,7 +21,7 @@ def built():
 def header_functions():
     src = open(os.path.join(ROOT, "include", "lc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lc_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lc_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_every_declared_symbol_is_exported():
@@ -119,5 +119,26 @@ def test_import_rejects_bad_graphs(mix3k):
         with pytest.raises(lc.LcError):
             lc.lc_import(h, ix.N, ix.R, ix.C1, ix.C2, ix.codes1, ix.codes2, ix.beta, ix.B, ix.adj0,
                          ix.levels, ix.upper_adj, ep_bad)
+    finally:
+        lc.lc_free(h)
+
+
+def test_search_ex_argument_errors_without_gpu(mix3k):
+    # both checks happen on the host before any device work
+    ix, _, xq = mix3k
+    h = _import(ix)
+    try:
+        q = np.ascontiguousarray(xq[:4], np.float32)
+        ids = np.empty((4, 10), np.int32)
+        ds = np.empty((4, 10), np.float32)
+        sp = lc.lc_default_search_params(10, 64)
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_search_ex(h, q, 7, 4, sp, None, ids, ds)
+        assert e.value.status == lc.LC_ERR_ARG and "query type" in e.value.message
+        for bad in (0, 65):
+            efq = np.array([16, bad, 32, 64], np.int32)
+            with pytest.raises(lc.LcError) as e:
+                lc.lc_search_ex(h, q, lc.LC_QUERY_F32, 4, sp, efq, ids, ds)
+            assert e.value.status == lc.LC_ERR_ARG and "query 1" in e.value.message
     finally:
         lc.lc_free(h)

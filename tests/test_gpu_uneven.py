@@ -1,0 +1,122 @@
+"""Per-query efSearch and uint8 queries (lc_search_ex), the shape of the 10M SIFT-like
+workload: integer-valued uint8 descriptors (Section 5.1) searched with efSearch drawn per
+query from {16, 32, 64, 128, 256}.
+
+Each query's result must be the oracle's at that query's own efSearch (same bar as the
+plain parity tests), and bit-identical to lc_search run with that efSearch for all queries;
+uint8 queries must give exactly the results of the same values passed as float32."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_09996_gb300 import datagen, lc
+
+from test_gpu_parity import compare, gpu_search, handle
+
+pytestmark = pytest.mark.gpu
+
+
+def search_ex(h, q, k, ef_bound, efq, beam=1, u8=False, device=True):
+    import torch
+    nq = len(q)
+    sp = lc.lc_default_search_params(k, ef_bound)
+    if beam > 1:
+        sp.mode, sp.beam = lc.LC_MODE_BATCHED, beam
+    qt = lc.LC_QUERY_U8 if u8 else lc.LC_QUERY_F32
+    q = np.ascontiguousarray(q, np.uint8 if u8 else np.float32)
+    efq = None if efq is None else np.ascontiguousarray(efq, np.int32)
+    if device:
+        dq = torch.from_numpy(q).cuda()
+        de = None if efq is None else torch.from_numpy(efq).cuda()
+        ids = torch.full((nq, k), -7, dtype=torch.int32, device="cuda")
+        ds = torch.full((nq, k), -7.0, dtype=torch.float32, device="cuda")
+        st = torch.full((nq, 3), -7, dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        lc.lc_search_ex(h, dq, qt, nq, sp, de, ids, ds, st, s)
+        s.synchronize()
+        return ids.cpu().numpy(), ds.cpu().numpy(), st.cpu().numpy()
+    ids = np.full((nq, k), -7, np.int32)
+    ds = np.full((nq, k), -7.0, np.float32)
+    st = np.full((nq, 3), -7, np.int32)
+    lc.lc_search_ex(h, q, qt, nq, sp, efq, ids, ds, st)
+    return ids, ds, st
+
+
+def oracle_uneven(ix, xq, k, efq, beam=1):
+    """The oracle at each query's own efSearch, assembled row by row."""
+    ref = None
+    for ef in np.unique(efq):
+        rows = np.flatnonzero(efq == ef)
+        r = oracle.search(ix, xq[rows], k, int(ef), beam=beam)
+        if ref is None:
+            ref = {key: np.empty((len(xq),) + np.shape(v)[1:], np.asarray(v).dtype) for key, v in r.items()
+                   if key in ("ids", "dists", "stats", "gap")}
+        for key in ref:
+            ref[key][rows] = r[key]
+    return ref
+
+
+@pytest.mark.parametrize("name", ["opq3k", "sift2k"])
+@pytest.mark.parametrize("beam", [1, 4])
+def test_uneven_ef_parity(request, name, beam):
+    ix, xb, xq = request.getfixturevalue(name)
+    h = handle(name, ix)
+    efq = datagen.uneven_ef(len(xq))
+    assert len(np.unique(efq)) == 5
+    ref = oracle_uneven(ix, xq, 10, efq, beam)
+    compare(ref, *search_ex(h, xq, 10, 256, efq, beam), max_exempt=0.15)
+
+
+@pytest.mark.parametrize("device", [True, False])
+def test_uneven_equals_uniform_per_group(opq3k, device):
+    ix, xb, xq = opq3k
+    h = handle("opq3k", ix)
+    efq = datagen.uneven_ef(len(xq), choices=(4, 16, 40, 100, 300))
+    got = search_ex(h, xq, 10, 300, efq, device=device)
+    for ef in np.unique(efq):
+        rows = np.flatnonzero(efq == ef)
+        alone = gpu_search(h, xq[rows], 10, int(ef))
+        for a, b in zip(got, alone):
+            assert np.array_equal(a[rows], b), f"ef={ef}"
+
+
+def test_device_ef_clamped_to_bound(opq3k):
+    # device arrays are not read on the host: values outside 1..bound are clamped
+    ix, xb, xq = opq3k
+    h = handle("opq3k", ix)
+    q = xq[:40]
+    efq = np.where(np.arange(40) % 2 == 0, 1000, -5).astype(np.int32)
+    got = search_ex(h, q, 10, 64, efq)
+    hi = gpu_search(h, q, 10, 64)
+    lo = gpu_search(h, q, 10, 1)
+    for a, b, c in zip(got, hi, lo):
+        assert np.array_equal(a[0::2], b[0::2])
+        assert np.array_equal(a[1::2], c[1::2])
+
+
+def test_host_ef_out_of_range_rejected(opq3k):
+    ix, xb, xq = opq3k
+    h = handle("opq3k", ix)
+    efq = np.full(len(xq), 32, np.int32)
+    efq[7] = 65
+    with pytest.raises(lc.LcError) as e:
+        search_ex(h, xq, 10, 64, efq, device=False)
+    assert e.value.status == lc.LC_ERR_ARG
+
+
+@pytest.mark.parametrize("device", [True, False])
+@pytest.mark.parametrize("uneven", [False, True])
+def test_u8_queries(sift2k, device, uneven):
+    ix, xb, xq = sift2k
+    h = handle("sift2k", ix)
+    assert np.array_equal(xq, np.clip(np.round(xq), 0, 255))      # integer-valued descriptors
+    q8 = xq.astype(np.uint8)
+    efq = datagen.uneven_ef(len(xq)) if uneven else None
+    bound = 256 if uneven else 128
+    a = search_ex(h, q8, 10, bound, efq, u8=True, device=device)
+    b = search_ex(h, xq, 10, bound, efq, u8=False, device=device)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    ref = oracle_uneven(ix, xq, 10, efq) if uneven else oracle.search(ix, xq, 10, bound)
+    # the widest searches make the most deciding comparisons, hence the most near-ties
+    compare(ref, *a, max_exempt=0.25)

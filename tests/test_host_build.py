@@ -109,3 +109,24 @@ def test_add_in_two_calls_keeps_ids_and_structure():
         assert (adj[700:] >= 0).sum(1).min() >= 1
     finally:
         lc.lc_free(h)
+
+
+def test_add_u8_equals_add_of_the_same_values():
+    d = 32
+    xt = dg.sift_like(1500, d, 32, stream=dg.STREAM_TRAIN)
+    xb = dg.sift_like(800, d, 32, stream=dg.STREAM_BASE)
+    assert np.array_equal(xb, np.round(xb)) and xb.min() >= 0 and xb.max() <= 255
+    out = []
+    for u8 in (False, True):
+        h = lc.lc_create(lc.lc_default_params(d, 16, 8, use_opq=0, kmeans_iters=5))
+        try:
+            lc.lc_train(h, xt)
+            if u8:
+                lc.lc_add_u8(h, xb.astype(np.uint8))
+            else:
+                lc.lc_add(h, xb)
+            out.append(lc.lc_export(h, d, 16, 8))
+        finally:
+            lc.lc_free(h)
+    for key in out[0]:
+        assert np.array_equal(np.asarray(out[0][key]), np.asarray(out[1][key])), key
