@@ -93,8 +93,9 @@ typedef struct {
     int64_t N;
     int d, M1, M2, deg, deg_up, max_level;
     int32_t ep;
-    const float *R, *C1, *C2, *B;
-    const uint8_t *codes1, *codes2, *beta;
+    const float *R, *C1, *C2, *B;   /* B: [bM][bK][9] */
+    int bM, bK;                      /* regression blocks, codewords per block */
+    const uint8_t *codes1, *codes2, *beta;   /* beta: [N][bM] (unused when bK = 1) */
     const int32_t *adj0, *upper_off, *upper_adj;
 } orc_index;
 
@@ -197,22 +198,23 @@ static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, in
 
 int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1,
                const float *C2, const uint8_t *codes1, const uint8_t *codes2,
-               const uint8_t *beta, const float *B, int deg, const int32_t *adj0, int deg_up,
+               const uint8_t *beta, const float *B, int bM, int bK, int deg, const int32_t *adj0, int deg_up,
                const int32_t *upper_off, const int32_t *upper_adj, int32_t ep, int max_level,
                int64_t nq, const float *Q, int k, int ef, int shortlist, int beam, int tcap,
                const float *C1w, int32_t *ids, double *dists, int32_t *stats, double *min_gap,
                int32_t *w_ids, double *w_dists, int32_t *w_size)
 {
-    orc_index ix = {N, d, M1, M2, deg, deg_up, max_level, ep, R, C1, C2, B,
+    orc_index ix = {N, d, M1, M2, deg, deg_up, max_level, ep, R, C1, C2, B, bM, bK,
                     codes1, codes2, beta, adj0, upper_off, upper_adj};
     int efp = ef > k ? ef : k;                               /* ef' = max(efSearch, k) */
     /* the walk's codebook: C1 itself, or a variant of it (e.g. rounded to FP16); the
        refinement always decodes with C1 */
     if (!C1w) C1w = C1;
-    int off1[256], len1[256], off2[256], len2[256];
-    if (M1 > 256 || M2 > 256 || k < 1) return -1;
+    int off1[256], len1[256], off2[256], len2[256], offb[256], lenb[256];
+    if (M1 > 256 || M2 > 256 || bM < 1 || bM > 256 || bM > d || bK < 1 || bK > 256 || k < 1) return -1;
     split_offsets(d, M1, off1, len1);
     split_offsets(d, M2, off2, len2);
+    split_offsets(d, bM, offb, lenb);       /* regression blocks (Section 4.3, product codebook) */
 
     double *yr = malloc(sizeof(double) * d);
     double *lut = malloc(sizeof(double) * 256 * M1);
@@ -411,16 +413,21 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
             if (Rn < k) Rn = k;
             if (Rn > wn) Rn = wn;
             if (Rn > 0 && Rn < wn) note_gap(&g, wd[Rn - 1], wi[Rn - 1], wd[Rn], wi[Rn], 1);
-            /* Refined reconstruction y^ = sum_j beta_j q(v_j), G = [q(x), q(g1..g8)] */
+            /* Refined reconstruction y^ = sum_j beta_j q(v_j), G = [q(x), q(g1..g8)]; with a
+               product codebook each block of coordinates takes the weights of its own
+               codeword (one codeword per block: the shared 0-byte weights) */
             for (int r = 0; r < Rn; r++) {
                 int32_t i = wi[r];
-                const float *bv = B + (int64_t)beta[i] * (ORC_KBETA + 1);
                 for (int t = 0; t < d; t++) yh[t] = 0.0;
                 for (int j = 0; j <= ORC_KBETA; j++) {
                     int32_t v = j == 0 ? i : adj0[(int64_t)i * deg + (j - 1)];
                     if (j > 0 && (j - 1 >= deg || v < 0)) continue;     /* zero column */
                     decode2(&ix, off1, len1, off2, len2, v, xh);
-                    for (int t = 0; t < d; t++) yh[t] += (double)bv[j] * xh[t];
+                    for (int m = 0; m < bM; m++) {
+                        int b = bK > 1 ? beta[(int64_t)i * bM + m] : 0;
+                        double w = (double)B[((int64_t)m * bK + b) * (ORC_KBETA + 1) + j];
+                        for (int t = offb[m]; t < offb[m] + lenb[m]; t++) yh[t] += w * xh[t];
+                    }
                 }
                 /* Exact squared L2 to the refined reconstruction */
                 double s = 0.0;

@@ -13,6 +13,11 @@ Paper passages (Section 4.2, 4.3):
     L'(B) = sum_x min_beta ||x - beta^T G(x)||^2: k-means on per-vector least-squares
     weights to initialise, then alternate assignment (argmin) and per-cluster least squares.
 
+  * product regression codebook: the coordinates split into M blocks, one codebook per
+    block, the block of the estimate being beta^j(x)^T G^j(x) (G^j: the block's columns of
+    G); M bytes per vector.  The 0-byte weights beta* per block are the same with one
+    codeword per block and nothing stored per vector.
+
 Readings where the paper is silent: a neighbour slot that the graph leaves empty (-1)
 contributes a zero row; codeword 0 is reserved as e0 = (1, 0, ..., 0) and never updated,
 so that no vector is refined worse than q(x); a small ridge 1e-10 * trace(A) / 9 keeps the
@@ -23,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .codec import kmeans
+from .codec import kmeans, splits
 
 KBETA = 8
 NBETA = 256
@@ -117,3 +122,53 @@ def losses_assigned(G: np.ndarray, x: np.ndarray, B: np.ndarray, a: np.ndarray) 
     Y = np.einsum("nj,njd->nd", B[a], G)
     r = x - Y
     return np.einsum("nd,nd->n", r, r)
+
+
+def train_product(G: np.ndarray, x: np.ndarray, n_blocks: int, n_beta: int = NBETA, iters: int = 10,
+                  seed: int = 0, history: list | None = None) -> np.ndarray:
+    """Product regression codebook (Section 4.3): coordinates split into ``n_blocks``
+    contiguous blocks (the PQ split rule: the first d mod M blocks one wider), each block
+    with its own codebook of ``n_beta`` weight vectors minimising that block's loss, which is
+    the whole loss restricted to the block's coordinates (the losses of the blocks add up).
+    ``n_beta`` = 1: the 0-byte weights beta* of Section 4.2, one per block (no per-vector
+    code, and no reserved e0).  Returns B [n_blocks][n_beta][9]; ``history`` receives one
+    list of EM losses per block."""
+    d = x.shape[1]
+    off, ln = splits(d, n_blocks)
+    B = np.empty((n_blocks, n_beta, KBETA + 1))
+    for m in range(n_blocks):
+        cols = slice(off[m], off[m] + ln[m])
+        Gm, xm = G[:, :, cols], x[:, cols]
+        if n_beta == 1:
+            B[m, 0] = beta_star(Gm, xm)
+        else:
+            h: list = []
+            B[m] = train_codebook(Gm, xm, n_beta=n_beta, iters=iters, seed=seed + 101 * m, history=h)
+            if history is not None:
+                history.append(h)
+    return B
+
+
+def assign_product(G: np.ndarray, x: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Per-vector, per-block codeword: argmin of the block's loss, ties to the lowest index.
+    Returns [n][n_blocks] (all zero with one codeword per block)."""
+    n_blocks, n_beta = B.shape[0], B.shape[1]
+    out = np.zeros((x.shape[0], n_blocks), np.int64)
+    if n_beta == 1:
+        return out
+    off, ln = splits(x.shape[1], n_blocks)
+    for m in range(n_blocks):
+        cols = slice(off[m], off[m] + ln[m])
+        out[:, m] = assign_codewords(G[:, :, cols], x[:, cols], B[m])
+    return out
+
+
+def reconstruct(G: np.ndarray, B: np.ndarray, codes: np.ndarray) -> np.ndarray:
+    """Refined vectors [n][d]: block m is sum_j B[m][codes[:, m]][j] * G[:, j, block m]."""
+    n_blocks = B.shape[0]
+    off, ln = splits(G.shape[2], n_blocks)
+    out = np.empty((G.shape[0], G.shape[2]))
+    for m in range(n_blocks):
+        cols = slice(off[m], off[m] + ln[m])
+        out[:, cols] = np.einsum("nj,njd->nd", B[m][codes[:, m]], G[:, :, cols])
+    return out

@@ -38,7 +38,8 @@ def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: boo
     N = ix.codes1.shape[0]
     rc = lib().orc_search(
         N, ix.d, ix.M1, ix.M2, ptr(ix.R), ptr(ix.C1), ptr(ix.C2), ptr(ix.codes1),
-        ptr(ix.codes2), ptr(ix.beta), ptr(ix.B), ix.adj0.shape[1], ptr(ix.adj0),
+        ptr(ix.codes2), ptr(np.ascontiguousarray(ix.beta, np.uint8)), ptr(np.ascontiguousarray(ix.B, np.float32)),
+        getattr(ix, "bM", 1), getattr(ix, "bK", 256), ix.adj0.shape[1], ptr(ix.adj0),
         ix.upper_adj.shape[1], ptr(ix.upper_off),
         ptr(ix.upper_adj) if ix.upper_adj.shape[0] > 0 else None, ix.ep, ix.max_level,
         nq, ptr(Q), k, ef, shortlist, beam, tcap,

@@ -107,3 +107,78 @@ def test_gmatrix_rows_follow_adjacency(mix3k):
                 assert np.array_equal(G[i, j + 1], xh[v])
             else:
                 assert not G[i, j + 1].any()
+
+
+# ---- product regression codebook and 0-byte weights per block (Section 4.2, 4.3) ----
+
+def _blocks(d, M):
+    # contiguous blocks, the first d mod M one coordinate wider (written out independently)
+    sizes = [d // M + (1 if j < d % M else 0) for j in range(M)]
+    starts = np.cumsum([0] + sizes[:-1])
+    return [np.arange(a, a + s) for a, s in zip(starts, sizes)]
+
+
+def test_product_zero_byte_is_blockwise_pseudoinverse(rng):
+    # one codeword per block: each block's weights solve the least squares restricted to
+    # that block's coordinates (Section 4.2's closed form, per block)
+    G, x = _toy(rng, n=200, d=13)
+    B = refine.train_product(G, x, 4, 1)
+    assert B.shape == (4, 1, 9)
+    for m, cols in enumerate(_blocks(13, 4)):
+        Y = np.concatenate([G[i][:, cols].T for i in range(len(x))], 0)
+        X = np.concatenate([x[i][cols] for i in range(len(x))], 0)
+        assert np.allclose(B[m, 0], np.linalg.lstsq(Y, X, rcond=None)[0], rtol=1e-8, atol=1e-9)
+    assert not np.any(refine.assign_product(G, x, B))        # nothing stored per vector
+
+
+def test_product_zero_byte_never_worse_than_shared(rng):
+    # the shared beta* is one feasible choice in every block, so the blockwise optimum
+    # cannot lose to it on the training set
+    G, x = _toy(rng, n=300, d=12)
+    bs = refine.beta_star(G, x)
+    Bp = refine.train_product(G, x, 3, 1)
+    whole = sum(np.sum((x[i] - bs @ G[i]) ** 2) for i in range(len(x)))
+    prod = 0.0
+    for m, cols in enumerate(_blocks(12, 3)):
+        prod += sum(np.sum((x[i][cols] - Bp[m, 0] @ G[i][:, cols]) ** 2) for i in range(len(x)))
+    assert prod <= whole * (1 + 1e-12)
+
+
+def test_product_assignment_is_blockwise_exhaustive_argmin(rng):
+    G, x = _toy(rng, n=30, d=13)
+    B = rng.standard_normal((4, 32, 9)) * 0.3
+    B[:, 0] = refine.e0()
+    a = refine.assign_product(G, x, B)
+    for m, cols in enumerate(_blocks(13, 4)):
+        for i in range(30):
+            errs = [np.sum((x[i][cols] - B[m, c] @ G[i][:, cols]) ** 2) for c in range(32)]
+            assert a[i, m] == int(np.argmin(errs))
+
+
+def test_product_codebook_e0_and_per_block_bound(rng):
+    # codeword 0 of every block is e0, so every block's error is at most that of q(x)
+    G, x = _toy(rng, n=400, d=16)
+    hist = []
+    B = refine.train_product(G, x, 4, 16, iters=4, history=hist)
+    assert np.array_equal(B[:, 0], np.tile(refine.e0(), (4, 1)))
+    a = refine.assign_product(G, x, B)
+    for m, cols in enumerate(_blocks(16, 4)):
+        got = np.array([np.sum((x[i][cols] - B[m, a[i, m]] @ G[i][:, cols]) ** 2) for i in range(len(x))])
+        base = np.array([np.sum((x[i][cols] - G[i][0, cols]) ** 2) for i in range(len(x))])
+        assert np.all(got <= base * (1 + 1e-12) + 1e-15)
+    # EM per block: its loss never increases
+    assert len(hist) == 4
+    for h in hist:
+        for u, v in zip(h, h[1:]):
+            assert v <= u * (1 + 1e-12)
+
+
+def test_reconstruct_blocks(rng):
+    G, x = _toy(rng, n=20, d=10)
+    B = rng.standard_normal((3, 5, 9))
+    codes = rng.integers(0, 5, size=(20, 3))
+    y = refine.reconstruct(G, B, codes)
+    for m, cols in enumerate(_blocks(10, 3)):
+        for i in range(20):
+            ref = sum(B[m, codes[i, m], j] * G[i, j, cols] for j in range(9))
+            assert np.allclose(y[i, cols], ref, rtol=1e-12, atol=1e-14)

@@ -375,3 +375,32 @@ def test_tcap_large_is_no_cap(mix3k):
     assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["stats"], b["stats"])
     c = oracle.search(ix, xq[:50], k=10, ef=64, tcap=120)
     assert (c["stats"][:, 0] < 120 + 32).all() and (c["stats"][:, 0] <= a["stats"][:, 0]).all()
+
+
+@pytest.mark.parametrize("bM,bK", [(4, 16), (1, 1), (3, 1)])
+def test_exhaustive_rerank_product_codebook(opq3k, bM, bK):
+    # the re-rank with a product codebook (or the 0-byte weights) is the brute-force order
+    # of the refined reconstructions, assembled block by block here
+    from oracle.index import with_regression
+    ix, xb, xq = opq3k
+    ixp = with_regression(ix, bM, bK, beta_train_n=1500, beta_iters=3)
+    N, k = ix.N, 30
+    r = oracle.search(ixp, xq[:3], k=k, ef=N, shortlist=N)
+    xh = ix.decoded()
+    G = refine.gmatrix(xh, ix.adj0, np.arange(N))
+    B = np.reshape(ixp.B, (bM, bK, 9)).astype(np.float64)
+    beta = np.reshape(ixp.beta, (N, bM)).astype(np.int64)
+    sizes = [ix.d // bM + (1 if j < ix.d % bM else 0) for j in range(bM)]
+    yhat = np.zeros((N, ix.d))
+    t0 = 0
+    for m, s in enumerate(sizes):
+        w = B[m][beta[:, m]] if bK > 1 else np.tile(B[m][0], (N, 1))
+        for j in range(9):
+            yhat[:, t0:t0 + s] += w[:, j:j + 1] * G[:, j, t0:t0 + s]
+        t0 += s
+    yr = xq[:3].astype(np.float64) @ ix.R.astype(np.float64).T
+    for q in range(3):
+        d = ((yr[q][None] - yhat) ** 2).sum(1)
+        order = np.lexsort((np.arange(N), d))[:k]
+        np.testing.assert_allclose(r["dists"][q], d[order], rtol=1e-11)
+        assert np.array_equal(r["ids"][q], order)
