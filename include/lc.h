@@ -63,6 +63,13 @@ typedef struct {
     int batch_max;         /* largest insertion batch (4096); 1 = sequential insertion */
     int n_threads;         /* host threads for train/add; 0 = all hardware threads */
     uint64_t seed;         /* seeds every random choice of the build */
+    int beta_M;            /* regression blocks (Section 4.3, product codebook): the coordinates
+                              split into beta_M contiguous blocks (the PQ split rule), each with
+                              its own codebook; 1..min(32, d), default 1 */
+    int beta_K;            /* codewords per block, 1..256 (256).  > 1: codeword 0 of every
+                              block is e0 and beta_M bytes are stored per vector; 1: the 0-byte
+                              refinement of Section 4.2 (one least-squares weight vector per
+                              block, shared by all vectors, nothing stored per vector) */
 } lc_params;
 
 /* Fills *p with the defaults above for dimension d and code sizes M1, M2. */
@@ -160,12 +167,14 @@ lc_status lc_search_ex(lc_index *ix, const void *q, int qtype, int64_t nq, const
 /* Replaces the index's content with caller-provided host arrays (copied): rotation R
  * [d][d] (y' = R y), level-1 and level-2 centroids C1, C2 [256][d] (full width: row c holds
  * centroid c of every sub-space in that sub-space's coordinates), codes1 [n][M1],
- * codes2 [n][M2], beta [n] (codeword ids), regression codebook B [256][9], level-0
+ * codes2 [n][M2], beta [n][beta_M] (codeword id per regression block, each < beta_K; all
+ * zero when beta_K = 1), regression codebooks B [beta_M][beta_K][9] (Section 4.3; with the
+ * default beta_M = 1, beta_K = 256: beta [n] and B [256][9]), level-0
  * adjacency adj0 [n][32] (-1 padded, first 8 entries = the neighbours of G(x)), levels [n],
  * upper_adj [sum(levels)][32] (node i with level L >= 1 owns L consecutive rows, levels 1..L,
  * in id order), entry point ep (a node of maximal level).  Sub-space split: M blocks of
  * contiguous dimensions, the first (d mod M) of size ceil(d/M).  The index becomes trained
- * and searchable.  Errors: LC_ERR_ARG (shapes, ids out of range), LC_ERR_OOM. */
+ * and searchable.  Errors: LC_ERR_ARG (shapes, ids or codewords out of range), LC_ERR_OOM. */
 lc_status lc_import(lc_index *ix, int64_t n, const float *R, const float *C1, const float *C2,
                     const uint8_t *codes1, const uint8_t *codes2, const uint8_t *beta,
                     const float *B, const int32_t *adj0, const int32_t *levels,

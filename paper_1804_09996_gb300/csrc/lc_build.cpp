@@ -681,7 +681,8 @@ struct NormalEq {
 
 static inline int tri(int i, int j) { return i <= j ? i * 9 - i * (i - 1) / 2 + (j - i) : tri(j, i); }
 
-static void normal_eq(const lc_index *ix, int64_t i, const float *x, NormalEq &ne)
+// Normal equations of vector i over the coordinates [t0, t1) (one regression block).
+static void normal_eq(const lc_index *ix, int64_t i, const float *x, int t0, int t1, NormalEq &ne)
 {
     int d = ix->p.d;
     const float *G[9];
@@ -693,17 +694,17 @@ static void normal_eq(const lc_index *ix, int64_t i, const float *x, NormalEq &n
     for (int a = 0; a < 9; a++) {
         double s = 0;
         if (G[a])
-            for (int t = 0; t < d; t++) s += (double)G[a][t] * x[t];
+            for (int t = t0; t < t1; t++) s += (double)G[a][t] * x[t];
         ne.b[a] = s;
         for (int c = a; c < 9; c++) {
             double u = 0;
             if (G[a] && G[c])
-                for (int t = 0; t < d; t++) u += (double)G[a][t] * G[c][t];
+                for (int t = t0; t < t1; t++) u += (double)G[a][t] * G[c][t];
             ne.A[tri(a, c)] = u;
         }
     }
     double xx = 0;
-    for (int t = 0; t < d; t++) xx += (double)x[t] * x[t];
+    for (int t = t0; t < t1; t++) xx += (double)x[t] * x[t];
     ne.xx = xx;
 }
 
@@ -756,12 +757,13 @@ static inline double quad_loss(const NormalEq &ne, const double *beta)
     return s;
 }
 
-static int argmin_codeword(const NormalEq &ne, const std::vector<double> &Bd)
+// argmin over the K codewords Bd [K][9] (ties to the lowest index)
+static int argmin_codeword(const NormalEq &ne, const double *Bd, int K)
 {
     int best = 0;
     double bl = INFINITY;
-    for (int c = 0; c < NBETA; c++) {
-        double l = quad_loss(ne, Bd.data() + c * 9);
+    for (int c = 0; c < K; c++) {
+        double l = quad_loss(ne, Bd + c * 9);
         if (l < bl) { bl = l; best = c; }
     }
     return best;
@@ -769,54 +771,84 @@ static int argmin_codeword(const NormalEq &ne, const std::vector<double> &Bd)
 
 }  // namespace
 
+// Regression codebooks (Section 4.3), one per block of coordinates (the product codebook;
+// one block = the plain codebook): trained on a seeded subset of the vectors just added.
+// beta_K > 1: k-means of the per-vector least-squares weights initialises codewords
+// 1..K-1 (codeword 0 stays e0), then EM alternates argmin assignment and per-cluster least
+// squares.  beta_K = 1: the shared least-squares weights beta* of Section 4.2 per block.
 static void train_codebook(lc_index *ix, const float *xr, int64_t first, int64_t count, int nt)
 {
     const lc_params &p = ix->p;
+    const int bM = p.beta_M, bK = p.beta_K;
+    std::vector<int> off, len;
+    splits(p.d, bM, off, len);
     auto sub = sample(count, std::min<int64_t>(count, p.beta_train_n), p.seed + 5);
     int64_t ns = (int64_t)sub.size();
     std::vector<NormalEq> ne(ns);
     std::vector<double> per((size_t)ns * 9);
-    parallel_for(ns, nt, 1024, [&](int64_t a, int64_t b, int) {
-        for (int64_t s = a; s < b; s++) {
-            int64_t i = sub[s];
-            normal_eq(ix, first + i, xr + i * p.d, ne[s]);
-            ridge_solve(ne[s].A, ne[s].b, per.data() + s * 9);
-        }
-    });
-    std::vector<double> Bd((size_t)NBETA * 9, 0.0);
-    for (int c = 0; c < NBETA; c++) Bd[(size_t)c * 9] = 1.0;        // e0 everywhere to start
-    int K = (int)std::min<int64_t>(NBETA - 1, ns);
-    if (K > 0) kmeans<double>(per.data(), ns, 9, 9, K, 25, p.seed + 31, Bd.data() + 9, false, nt);
-    std::vector<int32_t> as(ns);
-    for (int it = 0; it < p.beta_iters; it++) {
-        parallel_for(ns, nt, 2048, [&](int64_t a, int64_t b, int) {
-            for (int64_t s = a; s < b; s++) as[s] = argmin_codeword(ne[s], Bd);
+    std::vector<double> Ball((size_t)bM * bK * 9, 0.0);
+    for (int m = 0; m < bM; m++) {
+        const int t0 = off[m], t1 = off[m] + len[m];
+        parallel_for(ns, nt, 1024, [&](int64_t a, int64_t b, int) {
+            for (int64_t s = a; s < b; s++) {
+                int64_t i = sub[s];
+                normal_eq(ix, first + i, xr + i * p.d, t0, t1, ne[s]);
+                if (bK > 1) ridge_solve(ne[s].A, ne[s].b, per.data() + s * 9);
+            }
         });
-        std::vector<double> SA((size_t)NBETA * 45, 0.0), Sb((size_t)NBETA * 9, 0.0);
-        std::vector<int64_t> cnt(NBETA, 0);
-        for (int64_t s = 0; s < ns; s++) {
-            int c = as[s];
-            cnt[c]++;
-            for (int k = 0; k < 45; k++) SA[(size_t)c * 45 + k] += ne[s].A[k];
-            for (int k = 0; k < 9; k++) Sb[(size_t)c * 9 + k] += ne[s].b[k];
+        double *Bd = Ball.data() + (size_t)m * bK * 9;
+        if (bK == 1) {
+            double SA[45] = {}, Sb[9] = {};
+            for (int64_t s = 0; s < ns; s++) {
+                for (int k = 0; k < 45; k++) SA[k] += ne[s].A[k];
+                for (int k = 0; k < 9; k++) Sb[k] += ne[s].b[k];
+            }
+            ridge_solve(SA, Sb, Bd);
+            continue;
         }
-        for (int c = 1; c < NBETA; c++)
-            if (cnt[c] > 0) ridge_solve(SA.data() + (size_t)c * 45, Sb.data() + (size_t)c * 9, Bd.data() + (size_t)c * 9);
+        for (int c = 0; c < bK; c++) Bd[(size_t)c * 9] = 1.0;          // e0 everywhere to start
+        int K = (int)std::min<int64_t>(bK - 1, ns);
+        if (K > 0) kmeans<double>(per.data(), ns, 9, 9, K, 25, p.seed + 31 + 101 * (uint64_t)m, Bd + 9, false, nt);
+        std::vector<int32_t> as(ns);
+        for (int it = 0; it < p.beta_iters; it++) {
+            parallel_for(ns, nt, 2048, [&](int64_t a, int64_t b, int) {
+                for (int64_t s = a; s < b; s++) as[s] = argmin_codeword(ne[s], Bd, bK);
+            });
+            std::vector<double> SA((size_t)bK * 45, 0.0), Sb((size_t)bK * 9, 0.0);
+            std::vector<int64_t> cnt(bK, 0);
+            for (int64_t s = 0; s < ns; s++) {
+                int c = as[s];
+                cnt[c]++;
+                for (int k = 0; k < 45; k++) SA[(size_t)c * 45 + k] += ne[s].A[k];
+                for (int k = 0; k < 9; k++) Sb[(size_t)c * 9 + k] += ne[s].b[k];
+            }
+            for (int c = 1; c < bK; c++)
+                if (cnt[c] > 0) ridge_solve(SA.data() + (size_t)c * 45, Sb.data() + (size_t)c * 9, Bd + (size_t)c * 9);
+        }
     }
-    ix->B.resize((size_t)NBETA * 9);
-    for (size_t k = 0; k < ix->B.size(); k++) ix->B[k] = (float)Bd[k];
+    ix->B.resize(Ball.size());
+    for (size_t k = 0; k < ix->B.size(); k++) ix->B[k] = (float)Ball[k];
     ix->has_codebook = true;
 }
 
+// Each vector's codeword per block: argmin of the block's loss under the index's codebooks.
 static void assign_codewords(lc_index *ix, const float *xr, int64_t first, int64_t count, int nt)
 {
+    const int bM = ix->p.beta_M, bK = ix->p.beta_K;
+    if (bK == 1) {
+        std::fill(ix->beta.begin() + first * bM, ix->beta.begin() + (first + count) * bM, 0);
+        return;
+    }
+    std::vector<int> off, len;
+    splits(ix->p.d, bM, off, len);
     std::vector<double> Bd(ix->B.begin(), ix->B.end());
     parallel_for(count, nt, 1024, [&](int64_t a, int64_t b, int) {
         NormalEq ne;
-        for (int64_t i = a; i < b; i++) {
-            normal_eq(ix, first + i, xr + i * ix->p.d, ne);
-            ix->beta[first + i] = (uint8_t)argmin_codeword(ne, Bd);
-        }
+        for (int64_t i = a; i < b; i++)
+            for (int m = 0; m < bM; m++) {
+                normal_eq(ix, first + i, xr + i * ix->p.d, off[m], off[m] + len[m], ne);
+                ix->beta[(first + i) * bM + m] = (uint8_t)argmin_codeword(ne, Bd.data() + (size_t)m * bK * 9, bK);
+            }
     });
 }
 
@@ -851,7 +883,7 @@ lc_status build_add(lc_index *ix, const float *x, int64_t n)
     rotate(x, n, d, ix->R.data(), xr.data(), nt);
     ix->codes1.resize((size_t)total * p.M1);
     ix->codes2.resize((size_t)total * p.M2);
-    ix->beta.resize((size_t)total, 0);
+    ix->beta.resize((size_t)total * p.beta_M, 0);
     ix->xh.resize((size_t)total * d);
     uint8_t *c1 = ix->codes1.data() + first * p.M1;
     uint8_t *c2 = ix->codes2.data() + first * p.M2;

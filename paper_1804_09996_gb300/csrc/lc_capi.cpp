@@ -35,6 +35,11 @@ static lc_status check_params(const lc_params *p)
         return LC_ERR_ARG;
     }
     if (p->batch_max < 1) { set_error("batch_max must be >= 1"); return LC_ERR_ARG; }
+    if (p->beta_M < 1 || p->beta_M > MAX_BETA_M || p->beta_M > p->d) {
+        set_error("beta_M = %d outside 1..min(%d, d)", p->beta_M, MAX_BETA_M);
+        return LC_ERR_ARG;
+    }
+    if (p->beta_K < 1 || p->beta_K > NBETA) { set_error("beta_K = %d outside 1..%d", p->beta_K, NBETA); return LC_ERR_ARG; }
     return LC_OK;
 }
 
@@ -83,6 +88,8 @@ void lc_default_params(lc_params *p, int d, int M1, int M2)
     p->batch_max = 4096;
     p->n_threads = 0;
     p->seed = 1804;
+    p->beta_M = 1;
+    p->beta_K = NBETA;
 }
 
 void lc_default_search_params(lc_search_params *p, int k, int ef)
@@ -189,9 +196,11 @@ lc_status lc_import(lc_index *ix, int64_t n, const float *R, const float *C1, co
     if (!ix || !R || !C1 || !C2 || !B || n < 0) { set_error("null argument"); return LC_ERR_ARG; }
     if (n > 0 && (!codes1 || !codes2 || !beta || !adj0 || !levels)) { set_error("null array"); return LC_ERR_ARG; }
     if (n > (int64_t)0x7fffffff) { set_error("too many vectors"); return LC_ERR_ARG; }
-    const int d = ix->p.d, M1 = ix->p.M1, M2 = ix->p.M2;
+    const int d = ix->p.d, M1 = ix->p.M1, M2 = ix->p.M2, bM = ix->p.beta_M, bK = ix->p.beta_K;
     int64_t rows = 0;
     int maxl = -1;
+    for (int64_t i = 0; i < n * bM; i++)
+        if (beta[i] >= bK) { set_error("codeword %d of vector %lld exceeds beta_K - 1 = %d", beta[i], (long long)(i / bM), bK - 1); return LC_ERR_ARG; }
     for (int64_t i = 0; i < n; i++) {
         if (levels[i] < 0 || levels[i] > MAX_LEVEL) { set_error("level of node %lld outside 0..%d", (long long)i, MAX_LEVEL); return LC_ERR_ARG; }
         rows += levels[i];
@@ -218,10 +227,10 @@ lc_status lc_import(lc_index *ix, int64_t n, const float *R, const float *C1, co
         ix->R.assign(R, R + (size_t)d * d);
         ix->C1.assign(C1, C1 + (size_t)KSUB * d);
         ix->C2.assign(C2, C2 + (size_t)KSUB * d);
-        ix->B.assign(B, B + (size_t)NBETA * (KBETA + 1));
+        ix->B.assign(B, B + (size_t)bM * bK * (KBETA + 1));
         ix->codes1.assign(codes1, codes1 + (size_t)n * M1);
         ix->codes2.assign(codes2, codes2 + (size_t)n * M2);
-        ix->beta.assign(beta, beta + (size_t)n);
+        ix->beta.assign(beta, beta + (size_t)n * bM);
         ix->adj0.assign(adj0, adj0 + (size_t)n * DEG);
         ix->levels.assign(levels, levels + (size_t)n);
         ix->upper_adj.assign(upper_adj, upper_adj + (size_t)rows * DEG);
@@ -273,10 +282,10 @@ lc_status lc_export(const lc_index *ix, float *R, float *C1, float *C2, uint8_t 
     return LC_OK;
 }
 
-// File format (little-endian, native layouts): "LCIDX001", lc_params, int64 n, int64 upper
-// rows, int32 ep, int32 max_level, int32 trained, int32 has_codebook, then R, C1, C2, B,
-// codes1, codes2, beta, adj0, levels, upper_adj.
-static const char MAGIC[8] = {'L', 'C', 'I', 'D', 'X', '0', '0', '1'};
+// File format (little-endian, native layouts): "LCIDX002", lc_params, int64 n, int64 upper
+// rows, int32 ep, int32 max_level, int32 trained, int32 has_codebook, then R, C1, C2,
+// B [beta_M][beta_K][9], codes1, codes2, beta [n][beta_M], adj0, levels, upper_adj.
+static const char MAGIC[8] = {'L', 'C', 'I', 'D', 'X', '0', '0', '2'};
 
 lc_status lc_save(const lc_index *ix, const char *path)
 {
@@ -291,7 +300,7 @@ lc_status lc_save(const lc_index *ix, const char *path)
               std::fwrite(&ix->n, 8, 1, f) == 1 && std::fwrite(&rows, 8, 1, f) == 1 &&
               std::fwrite(hdr, 4, 4, f) == 4;
     auto put = [&](const void *p, size_t bytes) { if (ok && bytes) ok = std::fwrite(p, 1, bytes, f) == bytes; };
-    std::vector<float> Bz((size_t)NBETA * (KBETA + 1), 0.f);
+    std::vector<float> Bz((size_t)ix->p.beta_M * ix->p.beta_K * (KBETA + 1), 0.f);
     put(ix->R.data(), ix->R.size() * 4);
     put(ix->C1.data(), ix->C1.size() * 4);
     put(ix->C2.data(), ix->C2.size() * 4);
@@ -339,10 +348,10 @@ lc_status lc_load(const char *path, lc_index **out)
         get(R, (size_t)d * d);
         get(C1, (size_t)KSUB * d);
         get(C2, (size_t)KSUB * d);
-        get(B, (size_t)NBETA * (KBETA + 1));
+        get(B, (size_t)p.beta_M * p.beta_K * (KBETA + 1));
         get(codes1, (size_t)n * p.M1);
         get(codes2, (size_t)n * p.M2);
-        get(beta, (size_t)n);
+        get(beta, (size_t)n * p.beta_M);
         get(adj0, (size_t)n * DEG);
         get(levels, (size_t)n);
         get(upper, (size_t)rows * DEG);

@@ -18,6 +18,7 @@ struct DeviceIndex {
     void *C1h = nullptr;          // C1 rounded to FP16 (device __half), for the FP16 mode
     uint8_t *codes1 = nullptr, *codes2b = nullptr;   // codes2b: residual codes padded to M2P bytes, codeword id last
     int M2P = 0;
+    int bM = 1, bK = 256;         // regression blocks and codewords per block (B: [bM][bK][9])
     int32_t *adj0 = nullptr, *upper_off = nullptr, *upper_adj = nullptr;
     // scratch of lc_search, grown on demand
     float *yq = nullptr; size_t yq_cap = 0;

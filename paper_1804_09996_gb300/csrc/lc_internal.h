@@ -11,7 +11,8 @@ namespace lc {
 
 constexpr int KSUB = 256;     // centroids per sub-quantiser (8-bit codes)
 constexpr int KBETA = 8;      // neighbours in G(x)
-constexpr int NBETA = 256;    // regression codebook size
+constexpr int NBETA = 256;    // largest regression codebook (per block)
+constexpr int MAX_BETA_M = 32; // most regression blocks (product codebook)
 constexpr int DEG = 32;       // graph degree at every level
 constexpr int MAX_LEVEL = 15; // level cap
 constexpr int MAX_EF = 1024;  // largest ef' = max(efSearch, k)
@@ -37,8 +38,9 @@ struct lc_index {
     int64_t n = 0;
     std::vector<float> R;               // [d][d], y' = R y
     std::vector<float> C1, C2;          // [256][d] full-width centroids
-    std::vector<uint8_t> codes1, codes2, beta;
-    std::vector<float> B;               // [256][9]
+    std::vector<uint8_t> codes1, codes2;
+    std::vector<uint8_t> beta;          // [n][beta_M] codeword per block (zeros when beta_K = 1)
+    std::vector<float> B;               // [beta_M][beta_K][9]
     std::vector<int32_t> adj0;          // [n][32]
     std::vector<float> adj0_d;          // build-side: distance of each row entry to its owner
     std::vector<int32_t> levels;        // [n]

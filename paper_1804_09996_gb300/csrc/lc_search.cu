@@ -628,13 +628,15 @@ struct RefineArgs {
     const float *yq;
     const int32_t *shortlist;
     int64_t nq;
-    int R, k, d, M1, M2P;           // M2P: padded row of the residual codes (codeword id last)
+    int R, k, d, M1, M2P;           // M2P: padded row of the residual codes (codeword ids last)
+    int BM, BK;                     // regression blocks, codewords per block (B: [BM][BK][9])
     const float *C1, *C2, *B;
     const uint8_t *codes1, *codes2b;
     const int32_t *adj0;
     int32_t *ids_out;
     float *dists_out;
     uint8_t sub1[256], sub2[256];   // sub-space of each dimension, per level
+    uint8_t subb[256];              // regression block of each dimension
 };
 
 constexpr int REF_CH = 8;            // candidates staged at a time
@@ -647,11 +649,11 @@ __host__ __device__ inline int pow2_at_least(int r)
 }
 
 // Per-warp shared memory of the refinement kernel.
-__host__ __device__ inline size_t refine_smem(int M1, int M2P, int R)
+__host__ __device__ inline size_t refine_smem(int M1, int M2P, int R, int BM)
 {
     size_t o = 0;
     o += (size_t)REF_CH * 9 * 4;            // vertex ids
-    o += (size_t)REF_CH * 9 * 4;            // weights
+    o += (size_t)REF_CH * 9 * 4 * BM;       // weights, per regression block
     o += (size_t)REF_CH * 9 * M1;           // level-1 code rows
     o += (size_t)REF_CH * 9 * M2P;          // level-2 code rows (+ codeword id)
     o += (size_t)pow2_at_least(R) * 8;      // keys
@@ -662,7 +664,7 @@ __host__ __device__ inline size_t refine_smem(int M1, int M2P, int R)
 // multiple of 128, so lane t reading coordinate t of any centroid hits bank t mod 32);
 // otherwise only C1 does and C2 is read through the cache.  DU: coordinates per lane
 // (d = 32 DU), or 8 with bounds checks for other d <= 256.
-template <bool C2_SHARED, int DU>
+template <bool C2_SHARED, int DU, bool PROD>
 __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -681,11 +683,12 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
     __syncthreads();
     const float *C2 = C2_SHARED ? C2s : a.C2;
     const size_t cb = (size_t)(C2_SHARED ? 2 : 1) * 256 * d * 4;
-    unsigned char *base = smem_raw + cb + (size_t)warp * refine_smem(M1, M2P, a.R);
+    const int BM = PROD ? a.BM : 1;
+    unsigned char *base = smem_raw + cb + (size_t)warp * refine_smem(M1, M2P, a.R, BM);
     const int RP = pow2_at_least(a.R);
     int32_t *vid = reinterpret_cast<int32_t *>(base);
-    float *wt = reinterpret_cast<float *>(base + REF_CH * 9 * 4);
-    uint8_t *st1 = base + REF_CH * 9 * 8;
+    float *wt = reinterpret_cast<float *>(base + REF_CH * 9 * 4);       // [REF_CH][BM][9]
+    uint8_t *st1 = base + REF_CH * 9 * 4 * (1 + BM);
     uint8_t *st2 = st1 + REF_CH * 9 * M1;
     uint64_t *keys = reinterpret_cast<uint64_t *>(st2 + REF_CH * 9 * M2P);
     const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -693,13 +696,15 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
     const int r1 = M1 / 16, r2 = M2P / 16;          // 16-byte pieces per row
     // sub-spaces of this lane's coordinates t = lane + 32 u (read once: indexing the
     // parameter space with a per-lane index would serialise)
-    int s1v[DU], s2v[DU];
+    int s1v[DU], s2v[DU], sbv[DU];
 #pragma unroll
     for (int u = 0; u < DU; u++) {
         const int t = lane + 32 * u;
         s1v[u] = t < d ? a.sub1[t] : 0;
         s2v[u] = t < d ? a.sub2[t] : 0;
+        sbv[u] = PROD && t < d ? a.subb[t] : 0;
     }
+    const int nb = a.BK > 1 ? BM : 0;               // codeword bytes at the end of a row
 
     for (int64_t q = gwarp; q < a.nq; q += nwarps) {
         const int32_t *sl = a.shortlist + q * a.R;
@@ -717,18 +722,22 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
             // loads of a phase are all issued before any is used
             if (lane < nc) {
                 const int32_t i = sl[c0 + lane];
-                const int b = a.codes2b[(int64_t)i * M2P + M2P - 1];
+                const uint8_t *crow = a.codes2b + (int64_t)i * M2P + M2P - nb;
                 const int4 *ar = reinterpret_cast<const int4 *>(a.adj0 + (int64_t)i * DEG);
                 const int4 a0 = __ldg(ar), a1 = __ldg(ar + 1);
-                float w[9];
-#pragma unroll
-                for (int j = 0; j < 9; j++) w[j] = __ldg(a.B + b * 9 + j);
                 int32_t *vr = vid + lane * 9;
                 vr[0] = i;
                 vr[1] = a0.x; vr[2] = a0.y; vr[3] = a0.z; vr[4] = a0.w;
                 vr[5] = a1.x; vr[6] = a1.y; vr[7] = a1.z; vr[8] = a1.w;
+                for (int m = 0; m < BM; m++) {
+                    const int b = nb ? crow[m] : 0;
+                    const float *bw = a.B + ((int64_t)m * a.BK + b) * 9;
+                    float w[9];
 #pragma unroll
-                for (int j = 0; j < 9; j++) wt[lane * 9 + j] = w[j];
+                    for (int j = 0; j < 9; j++) w[j] = __ldg(bw + j);
+#pragma unroll
+                    for (int j = 0; j < 9; j++) wt[(lane * BM + m) * 9 + j] = w[j];
+                }
             }
             __syncwarp();
             // stage both code rows of every vertex: 16-byte pieces, six loads in flight per lane
@@ -768,12 +777,14 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
                 for (int j = 0; j < 9; j++) {
                     const int tt = r * 9 + j;
                     if (vid[tt] < 0) continue;
-                    const float w = wt[tt];
+                    const float w0 = wt[r * BM * 9 + j];
                     const uint8_t *c1r = st1 + tt * M1, *c2r = st2 + tt * M2P;
 #pragma unroll
                     for (int u = 0; u < DU; u++) {
                         const int t = lane + 32 * u;
                         if (DU == 8 && t >= d) continue;
+                        // the weight of this coordinate's regression block
+                        const float w = PROD ? wt[(r * BM + sbv[u]) * 9 + j] : w0;
                         const float x = C1s[(int)c1r[s1v[u]] * d + t] + C2[(int)c2r[s2v[u]] * d + t];
                         yh[u] = fmaf(w, x, yh[u]);
                     }
@@ -871,12 +882,15 @@ lc_status upload(lc_index *ix)
         for (int u = 0; u < d; u++) Rt[(size_t)u * d + t] = ix->R[(size_t)t * d + u];
     std::vector<int32_t> off(ix->n);
     for (int64_t i = 0; i < ix->n; i++) off[i] = (int32_t)ix->upper_off[i];
-    // residual codes with the codeword id in the last byte of a 16-byte-aligned row
-    const int M2 = ix->p.M2, M2P = (int)align_up((size_t)M2 + 1, 16);
+    // residual codes, then the regression codeword ids (one per block; none with the
+    // 0-byte weights) in the last bytes of a 16-byte-aligned row
+    const int M2 = ix->p.M2, bM = ix->p.beta_M, bK = ix->p.beta_K;
+    const int nb = bK > 1 ? bM : 0;
+    const int M2P = (int)align_up((size_t)M2 + nb, 16);
     std::vector<uint8_t> c2b((size_t)ix->n * M2P, 0);
     for (int64_t i = 0; i < ix->n; i++) {
         std::memcpy(c2b.data() + i * M2P, ix->codes2.data() + i * M2, M2);
-        c2b[i * M2P + M2P - 1] = ix->beta[i];
+        for (int m = 0; m < nb; m++) c2b[i * M2P + M2P - nb + m] = ix->beta[i * bM + m];
     }
     std::vector<__half> c1h(ix->C1.size());
     for (size_t i = 0; i < c1h.size(); i++) c1h[i] = __float2half_rn(ix->C1[i]);   // round to nearest even
@@ -897,6 +911,8 @@ lc_status upload(lc_index *ix)
     dv->M1 = ix->p.M1;
     dv->M2 = ix->p.M2;
     dv->M2P = M2P;
+    dv->bM = bM;
+    dv->bK = bK;
     dv->ep = ix->ep;
     dv->max_level = ix->max_level < 0 ? 0 : ix->max_level;
     ix->dev_dirty = false;
@@ -948,11 +964,16 @@ using RefineFn = void (*)(const RefineArgs);
 
 // Refinement instantiation: codebooks placement and coordinates per lane (3 for d = 96,
 // 4 for d = 128, else the checked 8).
-static RefineFn refine_kernel_for(bool both, int d)
+static RefineFn refine_kernel_for(bool both, int d, bool prod)
 {
-    if (d == 96) return both ? refine_kernel<true, 3> : refine_kernel<false, 3>;
-    if (d == 128) return both ? refine_kernel<true, 4> : refine_kernel<false, 4>;
-    return both ? refine_kernel<true, 8> : refine_kernel<false, 8>;
+    if (prod) {
+        if (d == 96) return both ? refine_kernel<true, 3, true> : refine_kernel<false, 3, true>;
+        if (d == 128) return both ? refine_kernel<true, 4, true> : refine_kernel<false, 4, true>;
+        return both ? refine_kernel<true, 8, true> : refine_kernel<false, 8, true>;
+    }
+    if (d == 96) return both ? refine_kernel<true, 3, false> : refine_kernel<false, 3, false>;
+    if (d == 128) return both ? refine_kernel<true, 4, false> : refine_kernel<false, 4, false>;
+    return both ? refine_kernel<true, 8, false> : refine_kernel<false, 8, false>;
 }
 
 // Dispatch on (sub-space width variant, codebook element type).
@@ -1025,7 +1046,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     if (P.refine) {
         P.yq_elems = (size_t)nq * dv->d;
         P.sl_elems = (size_t)nq * P.R;
-        const size_t per = refine_smem(dv->M1, dv->M2P, P.R);
+        const size_t per = refine_smem(dv->M1, dv->M2P, P.R, dv->bM);
         const size_t cbytes = (size_t)256 * dv->d * 4;
         // both codebooks in shared memory when that leaves room for at least 4 warps
         P.rboth = 2 * cbytes + 4 * per <= MAX_SMEM_PER_BLOCK;
@@ -1036,7 +1057,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
         }
         P.rw = (int)std::min<size_t>(16, (MAX_SMEM_PER_BLOCK - cb) / per);
         P.rsm = cb + per * P.rw;
-        auto kern = refine_kernel_for(P.rboth, dv->d);
+        auto kern = refine_kernel_for(P.rboth, dv->d, dv->bM > 1);
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM_PER_BLOCK) != cudaSuccess) {
             set_error("refine kernel configuration failed: %s", cudaGetErrorString(cudaGetLastError()));
             return LC_ERR_CUDA;
@@ -1106,7 +1127,11 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         splits(dv->d, dv->M2, o2, l2);
         for (int j = 0; j < dv->M1; j++) for (int t = off[j]; t < off[j] + len[j]; t++) ra.sub1[t] = (uint8_t)j;
         for (int j = 0; j < dv->M2; j++) for (int t = o2[j]; t < o2[j] + l2[j]; t++) ra.sub2[t] = (uint8_t)j;
-        auto kern = refine_kernel_for(P.rboth, dv->d);
+        std::vector<int> ob, lb;
+        splits(dv->d, dv->bM, ob, lb);
+        for (int m = 0; m < dv->bM; m++) for (int t = ob[m]; t < ob[m] + lb[m]; t++) ra.subb[t] = (uint8_t)m;
+        ra.BM = dv->bM; ra.BK = dv->bK;
+        auto kern = refine_kernel_for(P.rboth, dv->d, dv->bM > 1);
         kern<<<P.rgrid, P.rw * 32, P.rsm, st>>>(ra);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) {

@@ -45,7 +45,7 @@ class lc_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "d", "M1", "M2", "use_opq", "deg", "deg_upper", "level_ratio", "ef_construction",
         "beta_train_n", "beta_iters", "kmeans_iters", "opq_iters", "batch_max", "n_threads")] + [
-        ("seed", ctypes.c_uint64)]
+        ("seed", ctypes.c_uint64), ("beta_M", ctypes.c_int), ("beta_K", ctypes.c_int)]
 
 
 class lc_search_params(ctypes.Structure):
@@ -259,12 +259,16 @@ def lc_upper_rows(ix) -> int:
     return int(lib().lc_upper_rows(ix))
 
 
-def lc_export(ix, d: int, M1: int, M2: int) -> dict:
+def lc_export(ix, d: int, M1: int, M2: int, beta_M: int = 1, beta_K: int = 256) -> dict:
+    """The index arrays (layouts of lc_import).  With one regression block beta is [n] and B
+    [beta_K][9]; with beta_M blocks, [n][beta_M] and [beta_M][beta_K][9]."""
     n, rows = lc_size(ix), lc_upper_rows(ix)
     out = dict(R=np.empty((d, d), np.float32), C1=np.empty((256, d), np.float32),
                C2=np.empty((256, d), np.float32), codes1=np.empty((n, M1), np.uint8),
-               codes2=np.empty((n, M2), np.uint8), beta=np.empty(n, np.uint8),
-               B=np.empty((256, 9), np.float32), adj0=np.empty((n, 32), np.int32),
+               codes2=np.empty((n, M2), np.uint8),
+               beta=np.empty(n, np.uint8) if beta_M == 1 else np.empty((n, beta_M), np.uint8),
+               B=np.empty((beta_K, 9) if beta_M == 1 else (beta_M, beta_K, 9), np.float32),
+               adj0=np.empty((n, 32), np.int32),
                levels=np.empty(n, np.int32), upper_adj=np.empty((rows, 32), np.int32))
     ep = ctypes.c_int32()
     order = ["R", "C1", "C2", "codes1", "codes2", "beta", "B", "adj0", "levels", "upper_adj"]

@@ -41,6 +41,12 @@ def test_param_validation():
         lc.lc_create(lc.lc_default_params(96, 32, 16, deg=16))
     with pytest.raises(lc.LcError):
         lc.lc_create(lc.lc_default_params(300, 32, 16))
+    for bm, bk in ((0, 256), (33, 256), (4, 0), (4, 257)):
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_create(lc.lc_default_params(96, 32, 16, beta_M=bm, beta_K=bk))
+        assert e.value.status == lc.LC_ERR_ARG and "beta_" in e.value.message
+    p = lc.lc_default_params(96, 32, 16)
+    assert (p.beta_M, p.beta_K) == (1, 256)
 
 
 def test_state_errors_without_gpu():
@@ -140,5 +146,37 @@ def test_search_ex_argument_errors_without_gpu(mix3k):
             with pytest.raises(lc.LcError) as e:
                 lc.lc_search_ex(h, q, lc.LC_QUERY_F32, 4, sp, efq, ids, ds)
             assert e.value.status == lc.LC_ERR_ARG and "query 1" in e.value.message
+    finally:
+        lc.lc_free(h)
+
+
+@pytest.mark.parametrize("bM,bK", [(4, 16), (3, 1)])
+def test_product_codebook_import_export_and_file(mix3k, tmp_path, bM, bK):
+    # product regression codebook (beta [n][bM], B [bM][bK][9]) and the 0-byte weights
+    from oracle.index import with_regression
+    ix, _, _ = mix3k
+    ixp = with_regression(ix, bM, bK, beta_train_n=1000, beta_iters=2)
+    h = lc.lc_create(lc.lc_default_params(ix.d, ix.M1, ix.M2, beta_M=bM, beta_K=bK))
+    try:
+        lc.lc_import(h, ix.N, ix.R, ix.C1, ix.C2, ix.codes1, ix.codes2, ixp.beta, ixp.B, ix.adj0,
+                     ix.levels, ix.upper_adj, ix.ep)
+        ex = lc.lc_export(h, ix.d, ix.M1, ix.M2, bM, bK)
+        assert np.array_equal(ex["beta"], ixp.beta) and np.array_equal(ex["B"], ixp.B)
+        path = str(tmp_path / "p.lc")
+        lc.lc_save(h, path)
+        h2 = lc.lc_load(path)
+        try:
+            ex2 = lc.lc_export(h2, ix.d, ix.M1, ix.M2, bM, bK)
+            for k in ex:
+                assert np.array_equal(np.asarray(ex[k]), np.asarray(ex2[k])), k
+        finally:
+            lc.lc_free(h2)
+        if bK > 1:
+            bad = ixp.beta.copy()
+            bad[5, 1] = bK
+            with pytest.raises(lc.LcError) as e:
+                lc.lc_import(h, ix.N, ix.R, ix.C1, ix.C2, ix.codes1, ix.codes2, bad, ixp.B, ix.adj0,
+                             ix.levels, ix.upper_adj, ix.ep)
+            assert e.value.status == lc.LC_ERR_ARG and "codeword" in e.value.message
     finally:
         lc.lc_free(h)

@@ -130,3 +130,42 @@ def test_add_u8_equals_add_of_the_same_values():
             lc.lc_free(h)
     for key in out[0]:
         assert np.array_equal(np.asarray(out[0][key]), np.asarray(out[1][key])), key
+
+
+
+@pytest.mark.parametrize("bM,bK", [(4, 16), (3, 1)])
+def test_product_codebook_build(bM, bK):
+    # the library's product regression codebook (Section 4.3) and 0-byte weights per block
+    # (Section 4.2): e0 first in every block, every codeword the blockwise argmin under the
+    # library's own codebooks, and (0-byte, trained on every vector) the blockwise least
+    # squares of the oracle
+    d, M1, M2, n = 48, 16, 16, 1500
+    xt = dg.gaussian_mixture(3000, d, 32, stream=dg.STREAM_TRAIN)
+    xb = dg.gaussian_mixture(n, d, 32, stream=dg.STREAM_BASE)
+    h = lc.lc_create(lc.lc_default_params(d, M1, M2, use_opq=0, kmeans_iters=6, beta_M=bM, beta_K=bK,
+                                          beta_iters=3, beta_train_n=n))
+    try:
+        lc.lc_train(h, xt)
+        lc.lc_add(h, xb)
+        ex = lc.lc_export(h, d, M1, M2, bM, bK)
+    finally:
+        lc.lc_free(h)
+    B, beta = ex["B"].astype(np.float64), ex["beta"].astype(np.int64)
+    assert B.shape == (bM, bK, 9) and beta.shape == (n, bM)
+    xr = xb.astype(np.float64) @ ex["R"].astype(np.float64).T
+    xh = codec.pq_decode(ex["codes1"], ex["C1"].astype(np.float64), M1) + \
+        codec.pq_decode(ex["codes2"], ex["C2"].astype(np.float64), M2)
+    G = refine.gmatrix(xh, ex["adj0"], np.arange(n))
+    if bK == 1:
+        assert not beta.any()
+        ref = refine.train_product(G, xr, bM, 1)
+        np.testing.assert_allclose(B, ref, rtol=1e-4, atol=1e-5)
+        return
+    assert np.array_equal(B[:, 0], np.tile(refine.e0(), (bM, 1)))
+    best = refine.assign_product(G, xr, B)
+    assert (best == beta).mean() > 0.98
+    y_lib = refine.reconstruct(G, B, beta)
+    y_best = refine.reconstruct(G, B, best)
+    e_lib = ((xr - y_lib) ** 2).sum(1)
+    assert np.all(e_lib <= ((xr - y_best) ** 2).sum(1) * (1 + 1e-5) + 1e-9)
+    assert np.all(e_lib <= ((xr - xh) ** 2).sum(1) * (1 + 1e-5) + 1e-9)
