@@ -103,6 +103,9 @@ typedef struct {
     int beam;        /* LC_MODE_BATCHED: expansions per step, 2..8 (ignored in PLAIN mode) */
     int max_dist;    /* search-time cap T (Section 3.1): 0 = none; > 0: the level-0 search stops
                         before an expansion once T distances have been computed there */
+    int warps;       /* walk queries in flight per thread block: 0 = as many as fit in shared
+                        memory (at most 16); 1..16 = at most that many.  Results do not depend
+                        on it (a launch-shape knob for the autotuner) */
 } lc_search_params;
 
 void lc_default_search_params(lc_search_params *p, int k, int ef);
@@ -268,6 +271,31 @@ lc_status lc_serve_poll(lc_server *s, int timeout_ms, int *n_completed);
 /* Cancels queued requests (callback status LC_ERR_STATE), waits for and delivers those on the
  * device, and frees the server (NULL is a no-op). */
 lc_status lc_serve_close(lc_server *s);
+
+/* Captured search plans (the batched-serving form: one persistent walk kernel takes the
+ * queries of a batch off a work queue; the whole search is recorded once into a CUDA graph).
+ * lc_plan_create fixes the parameters *sp, the query type (LC_QUERY_F32 / LC_QUERY_U8) and
+ * whether queries carry their own efSearch (per_query_ef: then every ef[i] must lie in
+ * 1..sp->ef; values outside are clamped, as lc_search_ex with device arrays), allocates
+ * device buffers for up to nq_max queries, and captures the search over them.  The index
+ * must be non-empty; it is uploaded to the current device if needed.
+ * lc_plan_buffers returns the plan's device buffers (any pointer may be NULL): q [nq_max][d]
+ * (float32 or uint8), ef [nq_max] int32 (NULL without per_query_ef; initialised to sp->ef),
+ * ids [nq_max][k], dists [nq_max][k], stats [nq_max][3], laid out as in lc_search.  The plan
+ * owns them; they stay valid until lc_plan_free.
+ * lc_plan_run queues one graph launch on `stream` for the first nq (0..nq_max) queries of
+ * q; results are those lc_search(_ex) returns for the same queries and parameters.  Errors:
+ * LC_ERR_STATE if the index was changed (lc_add, lc_import) or the current device differs
+ * since the plan was made, LC_ERR_CUDA.  Runs of one plan must not overlap on the device
+ * (they share the plan's buffers): queue them on one stream or wait in between.
+ * lc_plan_free releases the plan; free plans before their index. */
+typedef struct lc_plan lc_plan;
+lc_status lc_plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype,
+                         int per_query_ef, lc_plan **out);
+lc_status lc_plan_buffers(const lc_plan *pl, void **q, int32_t **ef, int32_t **ids, float **dists,
+                          int32_t **stats);
+lc_status lc_plan_run(lc_plan *pl, int64_t nq, void *stream);
+void lc_plan_free(lc_plan *pl);
 
 /* Kernel timing: after lc_profile(ix, 1) every lc_search records CUDA events on its stream
  * around the walk kernel and the refinement kernel; lc_profile_read waits for the last

@@ -56,6 +56,7 @@ lc_status check_search_params(const lc_search_params *sp)
         return LC_ERR_ARG;
     }
     if (sp->max_dist < 0) { set_error("max_dist must be >= 0"); return LC_ERR_ARG; }
+    if (sp->warps < 0 || sp->warps > 16) { set_error("warps = %d outside 0..16", sp->warps); return LC_ERR_ARG; }
     if (sp->visited_log != 0 && (sp->visited_log < 10 || sp->visited_log > 14)) {
         set_error("visited_log = %d outside 10..14", sp->visited_log);
         return LC_ERR_ARG;
@@ -186,6 +187,42 @@ lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_pa
 {
     return lc_search_ex(ix, q, LC_QUERY_F32, nq, sp, nullptr, ids, dists, stats, stream);
 }
+
+lc_status lc_plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype,
+                         int per_query_ef, lc_plan **out)
+{
+    set_error("");
+    if (!ix || !sp || !out) { set_error("null index, parameters or output"); return LC_ERR_ARG; }
+    *out = nullptr;
+    if (nq_max < 1 || nq_max > ((int64_t)1 << 31)) { set_error("nq_max = %lld outside 1..2^31", (long long)nq_max); return LC_ERR_ARG; }
+    if (qtype != LC_QUERY_F32 && qtype != LC_QUERY_U8) { set_error("query type %d is neither LC_QUERY_F32 nor LC_QUERY_U8", qtype); return LC_ERR_ARG; }
+    lc_status cs = check_search_params(sp);
+    if (cs != LC_OK) return cs;
+    if (!ix->trained) { set_error("plan before lc_train/lc_import"); return LC_ERR_STATE; }
+    if (ix->n > 0 && !ix->has_codebook) { set_error("index has no regression codebook"); return LC_ERR_STATE; }
+    try {
+        return lc::plan_create(ix, nq_max, sp, qtype, per_query_ef, out);
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory making a plan");
+        return LC_ERR_OOM;
+    }
+}
+
+lc_status lc_plan_buffers(const lc_plan *pl, void **q, int32_t **ef, int32_t **ids, float **dists, int32_t **stats)
+{
+    set_error("");
+    if (!pl) { set_error("null plan"); return LC_ERR_ARG; }
+    return lc::plan_buffers(pl, q, ef, ids, dists, stats);
+}
+
+lc_status lc_plan_run(lc_plan *pl, int64_t nq, void *stream)
+{
+    set_error("");
+    if (!pl) { set_error("null plan"); return LC_ERR_ARG; }
+    return lc::plan_run(pl, nq, stream);
+}
+
+void lc_plan_free(lc_plan *pl) { lc::plan_free(pl); }
 
 lc_status lc_import(lc_index *ix, int64_t n, const float *R, const float *C1, const float *C2,
                     const uint8_t *codes1, const uint8_t *codes2, const uint8_t *beta,

@@ -35,6 +35,7 @@ struct DeviceIndex {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bool ev_valid = false, has_refine = false;
     int num_sms = 0;
+    uint64_t gen = 0;             // changes with every upload (plans check it)
 };
 
 // Launch configuration of one search and the scratch it needs.
@@ -60,6 +61,7 @@ struct SearchScratch {
 };
 
 lc_status upload(lc_index *ix);
+
 lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl);
 // Queues the walk (and refinement) on `st`; q, ids, dists, stats are device pointers.
 // q8 (uint8 queries [nq][d], replacing q) and efq (per-query efSearch [nq]) are optional

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -915,6 +916,8 @@ lc_status upload(lc_index *ix)
     dv->bK = bK;
     dv->ep = ix->ep;
     dv->max_level = ix->max_level < 0 ? 0 : ix->max_level;
+    static std::atomic<uint64_t> uploads{0};
+    dv->gen = ++uploads;
     ix->dev_dirty = false;
     return LC_OK;
 }
@@ -928,14 +931,16 @@ static int ilog2_ceil(int64_t x)
 
 constexpr size_t MAX_SMEM_PER_BLOCK = 227 * 1024;
 
-// Warps per CTA: as many as fit next to the codebook (at most MAX_WALK_WARPS).
+// Warps per CTA: as many as fit next to the codebook (at most MAX_WALK_WARPS, and at most
+// want if want > 0).
 template <int M1, int D1, typename CT>
-static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int *wpc_out,
+static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int want, int *wpc_out,
                                int *grid_out, size_t *smem_out)
 {
     size_t c1 = walk_c1_bytes(wa.d, sizeof(CT));
     if (c1 + smem_per_warp > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
     int wpc = (int)std::min<size_t>(MAX_WALK_WARPS, (MAX_SMEM_PER_BLOCK - c1) / smem_per_warp);
+    if (want > 0) wpc = std::min(wpc, want);
     size_t smem = c1 + smem_per_warp * wpc;
     // the attribute is an upper bound: set to the maximum, so plans made in any order (the
     // server plans at submission and launches later) all remain launchable
@@ -978,17 +983,32 @@ static RefineFn refine_kernel_for(bool both, int d, bool prod)
 
 // Dispatch on (sub-space width variant, codebook element type).
 template <typename CT>
-static cudaError_t launch_any(int variant, int M1, const WalkArgs &wa, size_t per_warp, int sms, int *wpc,
-                              int *grid, size_t *smem)
+static cudaError_t launch_any(int variant, int M1, const WalkArgs &wa, size_t per_warp, int sms, int want,
+                              int *wpc, int *grid, size_t *smem)
 {
     switch (variant) {
-    case 1: return launch_walk<16, 6, CT>(wa, per_warp, sms, wpc, grid, smem);
-    case 2: return launch_walk<32, 3, CT>(wa, per_warp, sms, wpc, grid, smem);
-    case 3: return launch_walk<64, 2, CT>(wa, per_warp, sms, wpc, grid, smem);
+    case 1: return launch_walk<16, 6, CT>(wa, per_warp, sms, want, wpc, grid, smem);
+    case 2: return launch_walk<32, 3, CT>(wa, per_warp, sms, want, wpc, grid, smem);
+    case 3: return launch_walk<64, 2, CT>(wa, per_warp, sms, want, wpc, grid, smem);
     default:
-        if (M1 == 16) return launch_walk<16, 0, CT>(wa, per_warp, sms, wpc, grid, smem);
-        if (M1 == 32) return launch_walk<32, 0, CT>(wa, per_warp, sms, wpc, grid, smem);
-        return launch_walk<64, 0, CT>(wa, per_warp, sms, wpc, grid, smem);
+        if (M1 == 16) return launch_walk<16, 0, CT>(wa, per_warp, sms, want, wpc, grid, smem);
+        if (M1 == 32) return launch_walk<32, 0, CT>(wa, per_warp, sms, want, wpc, grid, smem);
+        return launch_walk<64, 0, CT>(wa, per_warp, sms, want, wpc, grid, smem);
+    }
+}
+
+// The walk instantiation a plan launches (for finding its node in a captured graph).
+template <typename CT>
+static const void *walk_fn(int variant, int M1)
+{
+    switch (variant) {
+    case 1: return (const void *)walk_kernel<16, 6, CT>;
+    case 2: return (const void *)walk_kernel<32, 3, CT>;
+    case 3: return (const void *)walk_kernel<64, 2, CT>;
+    default:
+        if (M1 == 16) return (const void *)walk_kernel<16, 0, CT>;
+        if (M1 == 32) return (const void *)walk_kernel<32, 0, CT>;
+        return (const void *)walk_kernel<64, 0, CT>;
     }
 }
 
@@ -1030,8 +1050,8 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     wa.nq = nq;
     wa.d = dv->d;
     P.half = sp->lut_prec == LC_LUT_FP16;
-    cudaError_t ce = P.half ? launch_any<__half>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem)
-                            : launch_any<float>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, &P.wpc, &P.grid, &P.smem);
+    cudaError_t ce = P.half ? launch_any<__half>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem)
+                            : launch_any<float>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem);
     if (ce == cudaErrorInvalidConfiguration) {
         set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
                   "lower efSearch or visited_log", P.per_warp, walk_c1_bytes(dv->d, P.half ? 2 : 4));
@@ -1367,7 +1387,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     int grid = 0, wpc = 1;
     size_t smem = 0;
     cudaError_t ce;
-    ce = launch_any<float>(variant, dv->M1, wa, per_warp, dv->num_sms, &wpc, &grid, &smem);
+    ce = launch_any<float>(variant, dv->M1, wa, per_warp, dv->num_sms, 0, &wpc, &grid, &smem);
     if (ce != cudaSuccess) {
         set_error("walk kernel configuration failed: %s", cudaGetErrorString(ce));
         return ce == cudaErrorInvalidConfiguration ? LC_ERR_CAPACITY : LC_ERR_CUDA;
@@ -1466,6 +1486,201 @@ lc_status merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, 
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         set_error("merge kernel launch failed: %s", cudaGetErrorString(ce));
+        return LC_ERR_CUDA;
+    }
+    return LC_OK;
+}
+
+
+// ------------------------------------------------------------------------------------------
+// Captured searches.  A plan fixes the search parameters and a largest batch, owns its device
+// buffers (queries, per-query efSearch, outputs and the walk's scratch) and records the whole
+// search -- counter and status resets, walk, re-rank -- into one CUDA graph, so that a call
+// is a single graph launch with no planning, allocation or attribute calls on the host.  A
+// batch smaller than the largest updates the batch size in the two kernel nodes of the
+// executable graph (launches already queued keep the size they were launched with).
+}  // namespace lc
+
+struct lc_plan {
+    lc_index *ix = nullptr;
+    uint64_t gen = 0;
+    int device = -1;
+    lc::SearchPlan P;
+    int qtype = LC_QUERY_F32;
+    bool per_query_ef = false;
+    int64_t nq_max = 0, nq_cur = 0;
+    void *q = nullptr;
+    int32_t *ef = nullptr, *ids = nullptr, *stats = nullptr;
+    float *dists = nullptr;
+    lc::SearchScratch sc;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t walk_node = nullptr, refine_node = nullptr;
+    cudaKernelNodeParams walk_kp{}, refine_kp{};
+    lc::WalkArgs wa{};
+    lc::RefineArgs ra{};
+};
+
+namespace lc {
+
+void plan_free(lc_plan *pl)
+{
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    cfree(pl->q); cfree(pl->ef); cfree(pl->ids); cfree(pl->dists); cfree(pl->stats);
+    cfree(pl->sc.yq); cfree(pl->sc.shortlist); cfree(pl->sc.spill); cfree(pl->sc.status); cfree(pl->sc.counter);
+    delete pl;
+}
+
+lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype, int per_query_ef,
+                      lc_plan **out)
+{
+    lc_status rs = upload(ix);
+    if (rs != LC_OK) return rs;
+    DeviceIndex *dv = ix->dev;
+    if (dv->n == 0) {
+        set_error("plans need a non-empty index");
+        return LC_ERR_STATE;
+    }
+    lc_plan *pl = new lc_plan();
+    pl->ix = ix;
+    pl->gen = dv->gen;
+    pl->device = dv->device;
+    pl->qtype = qtype;
+    pl->per_query_ef = per_query_ef != 0;
+    pl->nq_max = nq_max;
+    pl->nq_cur = nq_max;
+    rs = plan_search(dv, nq_max, sp, &pl->P);
+    if (rs != LC_OK) { plan_free(pl); return rs; }
+    const SearchPlan &P = pl->P;
+    const int d = dv->d, k = sp->k;
+    auto alloc = [&](auto *&p, size_t bytes) { return cudaMalloc(&p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
+    bool ok = alloc(pl->q, (size_t)nq_max * d * (qtype == LC_QUERY_U8 ? 1 : 4)) &&
+              (!pl->per_query_ef || alloc(pl->ef, (size_t)nq_max * 4)) &&
+              alloc(pl->ids, (size_t)nq_max * k * 4) && alloc(pl->dists, (size_t)nq_max * k * 4) &&
+              alloc(pl->stats, (size_t)nq_max * 12) && alloc(pl->sc.spill, P.spill_elems * 4) &&
+              alloc(pl->sc.status, 4) && alloc(pl->sc.counter, 8) &&
+              (!P.refine || (alloc(pl->sc.yq, P.yq_elems * 4) && alloc(pl->sc.shortlist, P.sl_elems * 4)));
+    if (!ok) {
+        plan_free(pl);
+        set_error("cudaMalloc failed for the plan's buffers");
+        return LC_ERR_OOM;
+    }
+    if (pl->per_query_ef) {
+        // every query starts at the plan's efSearch until the caller writes its own
+        std::vector<int32_t> e((size_t)nq_max, sp->ef);
+        cudaMemcpy(pl->ef, e.data(), e.size() * 4, cudaMemcpyHostToDevice);
+    }
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        plan_free(pl);
+        set_error("stream creation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return LC_ERR_CUDA;
+    }
+    cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        const bool u8 = qtype == LC_QUERY_U8;
+        rs = run_search(dv, P, u8 ? nullptr : static_cast<const float *>(pl->q), nq_max, pl->ids, pl->dists,
+                        pl->stats, pl->sc, st, false, u8 ? static_cast<const uint8_t *>(pl->q) : nullptr,
+                        pl->per_query_ef ? pl->ef : nullptr);
+        cudaError_t ce2 = cudaStreamEndCapture(st, &pl->graph);
+        if (rs == LC_OK && ce2 != cudaSuccess) ce = ce2;
+    }
+    cudaStreamDestroy(st);
+    if (ce != cudaSuccess || rs != LC_OK) {
+        if (rs == LC_OK) set_error("capture of the search failed: %s", cudaGetErrorString(ce));
+        plan_free(pl);
+        return rs == LC_OK ? LC_ERR_CUDA : rs;
+    }
+    // find the two kernel nodes whose batch size a smaller call updates
+    const void *wf = P.half ? walk_fn<__half>(P.variant, dv->M1) : walk_fn<float>(P.variant, dv->M1);
+    const void *rf = P.refine ? (const void *)refine_kernel_for(P.rboth, d, dv->bM > 1) : nullptr;
+    size_t nn = 0;
+    cudaGraphGetNodes(pl->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(pl->graph, nodes.data(), &nn);
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if (cudaGraphKernelNodeGetParams(nd, &kp) != cudaSuccess) continue;
+        if (kp.func == wf) {
+            pl->walk_node = nd;
+            pl->walk_kp = kp;
+            pl->wa = *static_cast<const WalkArgs *>(kp.kernelParams[0]);
+        } else if (rf && kp.func == rf) {
+            pl->refine_node = nd;
+            pl->refine_kp = kp;
+            pl->ra = *static_cast<const RefineArgs *>(kp.kernelParams[0]);
+        }
+    }
+    if (!pl->walk_node || (P.refine && !pl->refine_node)) {
+        plan_free(pl);
+        set_error("captured search graph lacks its kernels");
+        return LC_ERR_CUDA;
+    }
+    ce = cudaGraphInstantiate(&pl->exec, pl->graph, 0);
+    if (ce != cudaSuccess) {
+        plan_free(pl);
+        set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
+        return LC_ERR_CUDA;
+    }
+    *out = pl;
+    return LC_OK;
+}
+
+lc_status plan_buffers(const lc_plan *pl, void **q, int32_t **ef, int32_t **ids, float **dists, int32_t **stats)
+{
+    if (q) *q = pl->q;
+    if (ef) *ef = pl->ef;
+    if (ids) *ids = pl->ids;
+    if (dists) *dists = pl->dists;
+    if (stats) *stats = pl->stats;
+    return LC_OK;
+}
+
+lc_status plan_run(lc_plan *pl, int64_t nq, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nq < 0 || nq > pl->nq_max) {
+        set_error("nq = %lld outside 0..%lld", (long long)nq, (long long)pl->nq_max);
+        return LC_ERR_ARG;
+    }
+    lc_index *ix = pl->ix;
+    if (ix->dev_dirty || !ix->dev || ix->dev->gen != pl->gen) {
+        set_error("the index changed since the plan was made; make a new plan");
+        return LC_ERR_STATE;
+    }
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != pl->device) {
+        set_error("plan made on device %d, current device is %d", pl->device, dev);
+        return LC_ERR_STATE;
+    }
+    if (nq == 0) return LC_OK;
+    if (nq != pl->nq_cur) {
+        pl->wa.nq = nq;
+        void *wp[1] = {&pl->wa};
+        cudaKernelNodeParams kp = pl->walk_kp;
+        kp.kernelParams = wp;
+        cudaError_t ce = cudaGraphExecKernelNodeSetParams(pl->exec, pl->walk_node, &kp);
+        if (ce == cudaSuccess && pl->refine_node) {
+            pl->ra.nq = nq;
+            void *rp[1] = {&pl->ra};
+            cudaKernelNodeParams kr = pl->refine_kp;
+            kr.kernelParams = rp;
+            ce = cudaGraphExecKernelNodeSetParams(pl->exec, pl->refine_node, &kr);
+        }
+        if (ce != cudaSuccess) {
+            set_error("updating the plan's batch size failed: %s", cudaGetErrorString(ce));
+            return LC_ERR_CUDA;
+        }
+        pl->nq_cur = nq;
+    }
+    cudaError_t ce = cudaGraphLaunch(pl->exec, st);
+    if (ce != cudaSuccess) {
+        set_error("graph launch failed: %s", cudaGetErrorString(ce));
         return LC_ERR_CUDA;
     }
     return LC_OK;

@@ -25,6 +25,7 @@ EXPORTED = [
     "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
     "lc_profile_read", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
     "lc_serve_open", "lc_serve_submit", "lc_serve_poll", "lc_serve_close", "lc_merge_topk",
+    "lc_plan_create", "lc_plan_buffers", "lc_plan_run", "lc_plan_free",
 ]
 
 # void (*lc_request_cb)(void *user, uint64_t req_id, lc_status status, const int32_t *ids,
@@ -49,7 +50,7 @@ class lc_params(ctypes.Structure):
 
 
 class lc_search_params(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam", "max_dist")]
+    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam", "max_dist", "warps")]
 
 
 _lib = None
@@ -88,6 +89,10 @@ def lib() -> ctypes.CDLL:
         "lc_serve_poll": (I, [P, I, P]),
         "lc_serve_close": (I, [P]),
         "lc_profile_read": (I, [P, P, P]),
+        "lc_plan_create": (I, [P, I64, P, I, I, P]),
+        "lc_plan_buffers": (I, [P, P, P, P, P, P]),
+        "lc_plan_run": (I, [P, I64, P]),
+        "lc_plan_free": (None, [P]),
         "lc_free": (None, [P]),
         "lc_last_error": (ctypes.c_char_p, []),
     }
@@ -301,3 +306,48 @@ def lc_profile_read(ix):
 def lc_free(ix):
     if ix:
         lib().lc_free(ix)
+
+
+class _DeviceView:
+    """A device buffer described by __cuda_array_interface__ (for torch.as_tensor)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def lc_plan_create(ix, nq_max: int, sp: lc_search_params, qtype: int = LC_QUERY_F32,
+                   per_query_ef: bool = False) -> ctypes.c_void_p:
+    pl = ctypes.c_void_p()
+    _check(lib().lc_plan_create(ix, nq_max, ctypes.byref(sp), qtype, int(per_query_ef), ctypes.byref(pl)))
+    return pl
+
+
+def lc_plan_buffers(pl) -> dict:
+    """Device addresses of the plan's buffers (ef is 0 without per-query efSearch)."""
+    ptrs = [ctypes.c_void_p() for _ in range(5)]
+    _check(lib().lc_plan_buffers(pl, *[ctypes.byref(p) for p in ptrs]))
+    return {n: int(p.value or 0) for n, p in zip(("q", "ef", "ids", "dists", "stats"), ptrs)}
+
+
+def lc_plan_tensors(pl, nq_max: int, d: int, k: int, qtype: int = LC_QUERY_F32) -> dict:
+    """The plan's buffers as torch CUDA tensors (views, no copy): q, ef (or None), ids,
+    dists, stats, each with nq_max rows."""
+    import torch
+    b = lc_plan_buffers(pl)
+    view = lambda ptr, shape, ts: torch.as_tensor(_DeviceView(ptr, shape, ts), device="cuda")  # noqa: E731
+    return {"q": view(b["q"], (nq_max, d), "|u1" if qtype == LC_QUERY_U8 else "<f4"),
+            "ef": view(b["ef"], (nq_max,), "<i4") if b["ef"] else None,
+            "ids": view(b["ids"], (nq_max, k), "<i4"), "dists": view(b["dists"], (nq_max, k), "<f4"),
+            "stats": view(b["stats"], (nq_max, 3), "<i4")}
+
+
+def lc_plan_run(pl, nq: int, stream=None):
+    s = stream
+    if s is not None and hasattr(s, "cuda_stream"):
+        s = s.cuda_stream
+    _check(lib().lc_plan_run(pl, nq, ctypes.c_void_p(s) if s else None))
+
+
+def lc_plan_free(pl):
+    lib().lc_plan_free(pl)

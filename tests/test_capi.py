@@ -180,3 +180,20 @@ def test_product_codebook_import_export_and_file(mix3k, tmp_path, bM, bK):
             assert e.value.status == lc.LC_ERR_ARG and "codeword" in e.value.message
     finally:
         lc.lc_free(h)
+
+
+def test_plan_argument_errors_without_gpu(mix3k):
+    ix, _, _ = mix3k
+    h = _import(ix)
+    try:
+        sp = lc.lc_default_search_params(10, 64)
+        for nq_max, qt in ((0, lc.LC_QUERY_F32), (16, 5)):
+            with pytest.raises(lc.LcError) as e:
+                lc.lc_plan_create(h, nq_max, sp, qt)
+            assert e.value.status == lc.LC_ERR_ARG
+        bad = lc.lc_default_search_params(10, 64, warps=17)
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_plan_create(h, 16, bad)
+        assert e.value.status == lc.LC_ERR_ARG and "warps" in e.value.message
+    finally:
+        lc.lc_free(h)
