@@ -81,9 +81,9 @@ def kernel_hash():
 
 
 def profiled_traffic(workload: str, form: str):
-    """DRAM bytes per walk launch of the given form ('plain' or 'batched') from the committed
-    ncu summary, if it was taken on the current kernel source (its 'kernel_source_sha256_16'
-    line must match)."""
+    """DRAM bytes per walk launch of the given form (e.g. 'batched_fp16_ef48') from the
+    committed ncu summary, if it was taken on the current kernel source (its
+    'kernel_source_sha256_16' line must match)."""
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         txt = open(f).read()
         m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
@@ -162,6 +162,15 @@ def make_data(w):
     else:
         gen = lambda n, s: dg.gaussian_mixture(n, w["d"], w["centres"], stream=s)  # noqa: E731
     return gen(w["n_train"], dg.STREAM_TRAIN), gen(w["n_base"], dg.STREAM_BASE), gen(w["n_query"], dg.STREAM_QUERY)
+
+
+def extra_queries(w, start, n):
+    """Queries of the same distribution, disjoint from the measured ones (the autotuner's
+    sample)."""
+    from paper_1804_09996_gb300 import datagen as dg
+    if w["kind"] == "sift":
+        return dg.sift_like(n, w["d"], w["centres"], stream=dg.STREAM_QUERY, start=start)
+    return dg.gaussian_mixture(n, w["d"], w["centres"], stream=dg.STREAM_QUERY, start=start)
 
 
 def build_index(w, xt, xb):
@@ -408,6 +417,8 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[20000, 50000, 100000, 200000],
                     help="open-loop offered loads, queries per second")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="target duration of each open-loop point")
+    ap.add_argument("--lut", default="fp32", choices=["fp32", "fp16"],
+                    help="level-1 codebook precision of the single form run by --mode plain / batched")
     ap.add_argument("--mode", default="both", choices=["both", "plain", "batched"],
                     help="both: plain sets the recall target, batched is swept to reach it; "
                          "plain / batched: that form only, at --ef")
@@ -487,14 +498,15 @@ def main():
     levels = ((0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 1.0, 1.25, 1.5, 2.0) if uneven else
               sorted({e for e in (16, 24, 32, 40, 48, 56, 64, 80, 96, 128) if e <= max(2 * args.ef, 16)}))
     batched = None
+    lut1 = lc.LC_LUT_FP16 if args.lut == "fp16" else lc.LC_LUT_FP32
     if args.mode == "batched":
-        f_b = params(base_level, lc.LC_MODE_BATCHED)
+        f_b = params(base_level, lc.LC_MODE_BATCHED, lut1)
         batched = measure(f_b, args.steps)
         batched.update(ef=base_level, sweep=[])
         plain, target = None, batched["recall"]
-        best, best_form, best_name = batched, f_b, f"batched(beam={args.beam})"
+        best, best_form, best_name = batched, f_b, f"batched(beam={args.beam}){', fp16 codebook' if lut1 else ''}"
     else:
-        f_p = params(base_level, lc.LC_MODE_PLAIN)
+        f_p = params(base_level, lc.LC_MODE_PLAIN, lut1 if args.mode == "plain" else lc.LC_LUT_FP32)
         plain = measure(f_p, args.steps)
         plain.update(ef=base_level)
         target = plain["recall"]
@@ -518,6 +530,27 @@ def main():
                 best, best_form = r, f_b
                 best_name = f"batched(beam={args.beam}){', fp16 codebook' if prec else ''}"
         batched = forms.get("batched")
+        if not uneven:
+            # the library's autotuner on a disjoint sample with its exact neighbours
+            xs = extra_queries(w, nq, min(2000, nq))
+            gs, _ = exact_nn(xb, xs, f"cuda:{dev}")
+            t0 = time.perf_counter()
+            tr = lc.lc_autotune(h, xs, gs.astype(np.int32), k=k, ef=args.ef, allow_fp16=True, max_beam=8, reps=3)
+            tune_s = time.perf_counter() - t0
+            f_t = (lc.lc_search_params.from_buffer_copy(tr.sp), None)
+            r = measure(f_t, args.steps)
+            sp_t = f_t[0]
+            r.update(ef=sp_t.ef, tune={"sample_queries": len(xs), "sample_recall": tr.recall,
+                                        "sample_target": tr.target, "candidates": tr.tried,
+                                        "seconds": round(tune_s, 2), "beam": sp_t.beam if sp_t.mode else 1,
+                                        "mode": "batched" if sp_t.mode else "plain",
+                                        "codebook": "fp16" if sp_t.lut_prec else "fp32",
+                                        "warps": sp_t.warps, "visited_log": sp_t.visited_log})
+            forms["tuned"] = r
+            if r["recall"] >= target and r["qps"] > best["qps"]:
+                best, best_form = r, f_t
+                best_name = (f"autotuned ({r['tune']['mode']}, beam {r['tune']['beam']}, "
+                             f"{r['tune']['codebook']} codebook, efSearch {sp_t.ef})")
     clk = clocks.stop()
     if args.mode == "both" and best is not plain:   # leave the headline's counters in `stats`
         measure(best_form, 3)
@@ -532,7 +565,11 @@ def main():
     walk_s = best["walk_ms"] / 1e3
     peak, peak_src = peaks()
     achieved = b_walk / walk_s / 1e9
-    traffic = None if "fp16" in best_name else profiled_traffic(args.workload, "plain" if best_name == "plain" else "batched")
+    # DRAM traffic from the committed ncu summary of the same kernel build and form, if any
+    bsp = best_form[0]
+    form_key = None if (bsp.warps or bsp.visited_log or (bsp.mode and bsp.beam != args.beam)) else (
+        ("batched" if bsp.mode else "plain") + ("_fp16" if bsp.lut_prec else "") + f"_ef{bsp.ef}")
+    traffic = profiled_traffic(args.workload, form_key) if form_key else None
 
     # e2e through the same C ABI call with pinned host buffers
     best_sp, best_efq = best_form
@@ -554,6 +591,44 @@ def main():
         e2e_call()
         e2e_t.append(time.perf_counter() - t0)
     e2e = nq / float(np.mean(e2e_t))
+
+    # small batches: per-call latency of lc_search (host-side planning + 4 launches) against
+    # a captured plan (one CUDA graph launch), same parameters, device-resident queries
+    small = None
+    if ws == 1:
+        small = []
+        pl = lc.lc_plan_create(h, 256, best_sp, qtype, best_efq is not None)
+        try:
+            pt = lc.lc_plan_tensors(pl, 256, d, k, qtype)
+            pt["q"].copy_(q[:256])
+            if best_efq is not None:
+                pt["ef"].copy_(torch.from_numpy(best_efq[:256]))
+            de_s = None if best_efq is None else torch.from_numpy(best_efq[:256]).cuda()
+            for nb in (1, 16, 256):
+                row = {"queries": nb}
+                for kind in ("lc_search", "plan"):
+                    def call():
+                        if kind == "plan":
+                            lc.lc_plan_run(pl, nb, stream)
+                        else:
+                            lc.lc_search_ex(h, q[:nb], qtype, nb, best_sp, None if de_s is None else de_s[:nb],
+                                            ids[:nb], dists[:nb], stats[:nb], stream)
+                    for _ in range(20):
+                        call()
+                    stream.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    reps = 200
+                    t0 = time.perf_counter()
+                    e0.record(stream)
+                    for _ in range(reps):
+                        call()
+                    e1.record(stream)
+                    e1.synchronize()
+                    row[kind + "_us_per_call"] = 1e3 * e0.elapsed_time(e1) / reps
+                    row[kind + "_host_us_per_call"] = 1e6 * (time.perf_counter() - t0) / reps
+                small.append(row)
+        finally:
+            lc.lc_plan_free(pl)
 
     served = None
     if args.serve and ws == 1 and not uneven and not u8:
@@ -596,6 +671,9 @@ def main():
                        forms["batched_fp16"], forms["batched_fp16"]["ef"],
                        {"beam": args.beam, "sweep": forms["batched_fp16"]["sweep"],
                         "codebook": "level-1 codebook rounded to FP16 in the walk, FP32 arithmetic"}),
+                   "tuned": None if "tuned" not in forms else summary(forms["tuned"], forms["tuned"]["ef"],
+                                                                      {"autotune": forms["tuned"]["tune"]}),
+                   "small_batches": small,
                    "served": served,
                    "l2": "flushed before every step (256 MB read, outside the timed span)",
                    "index_build_s": round(build_s, 1), "parallelism": f"replicas x{ws}"},

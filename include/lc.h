@@ -272,6 +272,34 @@ lc_status lc_serve_poll(lc_server *s, int timeout_ms, int *n_completed);
  * device, and frees the server (NULL is a no-op). */
 lc_status lc_serve_close(lc_server *s);
 
+/* Autotuner.  Chooses search parameters on a sample of queries q [n][d] (host float32) with
+ * optional exact nearest-neighbour ids gt [n] (host int32; NULL: the top-1 of the plain search
+ * at 4x efSearch stands in).  The plain FP32 search at tp->ef sets the 1-recall@1 target on
+ * the sample.  Stage 1 tries every beam width 1, 2, 4 .. tp->max_beam with the FP32 and (if
+ * tp->allow_fp16) the FP16 codebook, each at the smallest efSearch of the ladder
+ * {2, 3, 4, 5, 6, 7, 8, 10, 12, 16} x ef/8 that reaches the target, and keeps the fastest.
+ * Stage 2 times launch shapes for it (visited_log 0/10/11/12 x warps 0/4/8/12), which do not
+ * change results, and keeps the fastest.  Times are medians of tp->reps searches of the
+ * sample with device-resident queries (CUDA events; caches stay warm between repetitions).
+ * out->sp receives the parameters (k and shortlist as tp->k and the default), out->ms,
+ * out->recall their time and recall on the sample, out->target and out->base_ms those of
+ * the plain search at ef, out->tried the number of candidates timed.
+ * Errors: LC_ERR_ARG, LC_ERR_STATE (untrained or empty index), LC_ERR_CUDA, LC_ERR_OOM. */
+typedef struct {
+    int k;           /* neighbours, 1..256 */
+    int ef;          /* efSearch of the plain reference, 1..1024 */
+    int allow_fp16;  /* 1: also try the FP16 level-1 codebook */
+    int max_beam;    /* largest beam width tried, 1..8 (1: plain only) */
+    int reps;        /* timed repetitions per candidate, >= 1 */
+} lc_tune_params;
+typedef struct {
+    lc_search_params sp;
+    float ms, recall, target, base_ms;
+    int tried;
+} lc_tune_result;
+lc_status lc_autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, const lc_tune_params *tp,
+                      lc_tune_result *out);
+
 /* Captured search plans (the batched-serving form: one persistent walk kernel takes the
  * queries of a batch off a work queue; the whole search is recorded once into a CUDA graph).
  * lc_plan_create fixes the parameters *sp, the query type (LC_QUERY_F32 / LC_QUERY_U8) and

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU = ["lc_search.cu"]
-CPP = ["lc_capi.cpp", "lc_build.cpp", "lc_serve.cpp"]
+CPP = ["lc_capi.cpp", "lc_build.cpp", "lc_serve.cpp", "lc_tune.cpp"]
 
 
 def _nvcc() -> str:

@@ -1,6 +1,7 @@
 // C ABI of liblc.so (declared in include/lc.h): argument checking, index state, import,
 // export and the on-disk format.  The build lives in lc_build.cpp and the GPU search in
 // lc_search.cu.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -186,6 +187,24 @@ lc_status lc_search(lc_index *ix, const float *q, int64_t nq, const lc_search_pa
                     int32_t *ids, float *dists, int32_t *stats, void *stream)
 {
     return lc_search_ex(ix, q, LC_QUERY_F32, nq, sp, nullptr, ids, dists, stats, stream);
+}
+
+lc_status lc_autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, const lc_tune_params *tp,
+                      lc_tune_result *out)
+{
+    set_error("");
+    if (!ix || !q || !tp || !out || n < 1) { set_error("null argument or empty sample"); return LC_ERR_ARG; }
+    if (tp->k < 1 || tp->k > MAX_K || tp->ef < 1 || std::max(tp->ef, tp->k) > MAX_EF) { set_error("k or ef out of range"); return LC_ERR_ARG; }
+    if (tp->max_beam < 1 || tp->max_beam > 8 || tp->reps < 1) { set_error("max_beam outside 1..8 or reps < 1"); return LC_ERR_ARG; }
+    if (!ix->trained || ix->n == 0) { set_error("autotune needs a trained, non-empty index"); return LC_ERR_STATE; }
+    if (!ix->has_codebook) { set_error("index has no regression codebook"); return LC_ERR_STATE; }
+    std::memset(out, 0, sizeof(*out));
+    try {
+        return lc::autotune(ix, q, n, gt, tp, out);
+    } catch (const std::bad_alloc &) {
+        set_error("out of host memory during autotune");
+        return LC_ERR_OOM;
+    }
 }
 
 lc_status lc_plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype,

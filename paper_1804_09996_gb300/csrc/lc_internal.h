@@ -71,6 +71,9 @@ lc_status merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, 
 lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef, int32_t *ids,
                               float *dists, int32_t *stats, void *stream);
 lc_status profile_read(lc_index *ix, float *walk_ms, float *refine_ms);
+// Autotuner (lc_tune.cpp).
+lc_status autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, const lc_tune_params *tp,
+                   lc_tune_result *out);
 // Captured searches (lc_plan_*), lc_search.cu.
 lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype, int per_query_ef,
                       lc_plan **out);

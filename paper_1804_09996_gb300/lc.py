@@ -25,7 +25,7 @@ EXPORTED = [
     "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
     "lc_profile_read", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
     "lc_serve_open", "lc_serve_submit", "lc_serve_poll", "lc_serve_close", "lc_merge_topk",
-    "lc_plan_create", "lc_plan_buffers", "lc_plan_run", "lc_plan_free",
+    "lc_plan_create", "lc_plan_buffers", "lc_plan_run", "lc_plan_free", "lc_autotune",
 ]
 
 # void (*lc_request_cb)(void *user, uint64_t req_id, lc_status status, const int32_t *ids,
@@ -51,6 +51,15 @@ class lc_params(ctypes.Structure):
 
 class lc_search_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam", "max_dist", "warps")]
+
+
+class lc_tune_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "allow_fp16", "max_beam", "reps")]
+
+
+class lc_tune_result(ctypes.Structure):
+    _fields_ = [("sp", lc_search_params)] + [(n, ctypes.c_float) for n in ("ms", "recall", "target", "base_ms")] + [
+        ("tried", ctypes.c_int)]
 
 
 _lib = None
@@ -89,6 +98,7 @@ def lib() -> ctypes.CDLL:
         "lc_serve_poll": (I, [P, I, P]),
         "lc_serve_close": (I, [P]),
         "lc_profile_read": (I, [P, P, P]),
+        "lc_autotune": (I, [P, P, I64, P, P, P]),
         "lc_plan_create": (I, [P, I64, P, I, I, P]),
         "lc_plan_buffers": (I, [P, P, P, P, P, P]),
         "lc_plan_run": (I, [P, I64, P]),
@@ -351,3 +361,15 @@ def lc_plan_run(pl, nq: int, stream=None):
 
 def lc_plan_free(pl):
     lib().lc_plan_free(pl)
+
+
+def lc_autotune(ix, q: np.ndarray, gt=None, k: int = 10, ef: int = 64, allow_fp16: bool = True,
+                max_beam: int = 8, reps: int = 3) -> lc_tune_result:
+    """Tune the search on a host sample q [n][d] (float32) with optional exact neighbour ids
+    gt [n]; returns the lc_tune_result (see include/lc.h)."""
+    q = np.ascontiguousarray(q, np.float32)
+    g = None if gt is None else np.ascontiguousarray(gt, np.int32)
+    tp = lc_tune_params(k=k, ef=ef, allow_fp16=int(allow_fp16), max_beam=max_beam, reps=reps)
+    out = lc_tune_result()
+    _check(lib().lc_autotune(ix, _ptr(q), q.shape[0], _ptr(g), ctypes.byref(tp), ctypes.byref(out)))
+    return out

@@ -197,3 +197,15 @@ def test_plan_argument_errors_without_gpu(mix3k):
         assert e.value.status == lc.LC_ERR_ARG and "warps" in e.value.message
     finally:
         lc.lc_free(h)
+
+
+def test_autotune_argument_errors_without_gpu(mix3k):
+    ix, _, xq = mix3k
+    h = _import(ix)
+    try:
+        for kw in (dict(k=0), dict(max_beam=9), dict(reps=0), dict(ef=2000)):
+            with pytest.raises(lc.LcError) as e:
+                lc.lc_autotune(h, xq[:10], **kw)
+            assert e.value.status == lc.LC_ERR_ARG
+    finally:
+        lc.lc_free(h)
