@@ -535,12 +535,13 @@ def main():
             xs = extra_queries(w, nq, min(2000, nq))
             gs, _ = exact_nn(xb, xs, f"cuda:{dev}")
             t0 = time.perf_counter()
-            tr = lc.lc_autotune(h, xs, gs.astype(np.int32), k=k, ef=args.ef, allow_fp16=True, max_beam=8, reps=3)
+            tr = lc.lc_autotune(h, xs, gs.astype(np.int32), k=k, ef=args.ef, allow_fp16=True, max_beam=8, reps=3,
+                                batch=nq)
             tune_s = time.perf_counter() - t0
             f_t = (lc.lc_search_params.from_buffer_copy(tr.sp), None)
             r = measure(f_t, args.steps)
             sp_t = f_t[0]
-            r.update(ef=sp_t.ef, tune={"sample_queries": len(xs), "sample_recall": tr.recall,
+            r.update(ef=sp_t.ef, tune={"sample_queries": len(xs), "timed_batch": nq, "sample_recall": tr.recall,
                                         "sample_target": tr.target, "candidates": tr.tried,
                                         "seconds": round(tune_s, 2), "beam": sp_t.beam if sp_t.mode else 1,
                                         "mode": "batched" if sp_t.mode else "plain",

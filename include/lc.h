@@ -280,7 +280,8 @@ lc_status lc_serve_close(lc_server *s);
  * {2, 3, 4, 5, 6, 7, 8, 10, 12, 16} x ef/8 that reaches the target, and keeps the fastest.
  * Stage 2 times launch shapes for it (visited_log 0/10/11/12 x warps 0/4/8/12), which do not
  * change results, and keeps the fastest.  Times are medians of tp->reps searches of the
- * sample with device-resident queries (CUDA events; caches stay warm between repetitions).
+ * sample (repeated up to tp->batch queries) with device-resident queries (CUDA events; caches
+ * stay warm between repetitions); recall counts each sample query once.
  * out->sp receives the parameters (k and shortlist as tp->k and the default), out->ms,
  * out->recall their time and recall on the sample, out->target and out->base_ms those of
  * the plain search at ef, out->tried the number of candidates timed.
@@ -291,6 +292,9 @@ typedef struct {
     int allow_fp16;  /* 1: also try the FP16 level-1 codebook */
     int max_beam;    /* largest beam width tried, 1..8 (1: plain only) */
     int reps;        /* timed repetitions per candidate, >= 1 */
+    int batch;       /* queries per timed search: the sample repeated up to this many (the batch
+                        size the parameters are for: launch shapes that win on a small batch
+                        can lose on a large one); 0 = the sample as it is */
 } lc_tune_params;
 typedef struct {
     lc_search_params sp;

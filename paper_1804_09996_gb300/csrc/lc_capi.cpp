@@ -195,7 +195,10 @@ lc_status lc_autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt
     set_error("");
     if (!ix || !q || !tp || !out || n < 1) { set_error("null argument or empty sample"); return LC_ERR_ARG; }
     if (tp->k < 1 || tp->k > MAX_K || tp->ef < 1 || std::max(tp->ef, tp->k) > MAX_EF) { set_error("k or ef out of range"); return LC_ERR_ARG; }
-    if (tp->max_beam < 1 || tp->max_beam > 8 || tp->reps < 1) { set_error("max_beam outside 1..8 or reps < 1"); return LC_ERR_ARG; }
+    if (tp->max_beam < 1 || tp->max_beam > 8 || tp->reps < 1 || tp->batch < 0) {
+        set_error("max_beam outside 1..8, reps < 1 or batch < 0");
+        return LC_ERR_ARG;
+    }
     if (!ix->trained || ix->n == 0) { set_error("autotune needs a trained, non-empty index"); return LC_ERR_STATE; }
     if (!ix->has_codebook) { set_error("index has no regression codebook"); return LC_ERR_STATE; }
     std::memset(out, 0, sizeof(*out));

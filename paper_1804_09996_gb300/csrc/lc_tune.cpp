@@ -20,7 +20,8 @@ struct Sample {
     float *q = nullptr;
     int32_t *ids = nullptr;
     float *dists = nullptr;
-    int64_t n = 0;
+    int64_t n = 0;        // distinct sample queries (recall)
+    int64_t nb = 0;       // queries per timed search (the sample repeated)
     int k = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -45,12 +46,12 @@ struct Measured {
 Measured measure(lc_index *ix, Sample &s, const lc_search_params &sp, int reps, const std::vector<int32_t> *ref)
 {
     Measured m;
-    m.status = search(ix, s.q, LC_QUERY_F32, s.n, &sp, nullptr, s.ids, s.dists, nullptr, s.st);
+    m.status = search(ix, s.q, LC_QUERY_F32, s.nb, &sp, nullptr, s.ids, s.dists, nullptr, s.st);
     if (m.status != LC_OK) return m;
     std::vector<float> t;
     for (int r = 0; r < reps; r++) {
         cudaEventRecord(s.e0, s.st);
-        m.status = search(ix, s.q, LC_QUERY_F32, s.n, &sp, nullptr, s.ids, s.dists, nullptr, s.st);
+        m.status = search(ix, s.q, LC_QUERY_F32, s.nb, &sp, nullptr, s.ids, s.dists, nullptr, s.st);
         cudaEventRecord(s.e1, s.st);
         if (m.status != LC_OK) return m;
         if (cudaEventSynchronize(s.e1) != cudaSuccess) {
@@ -88,17 +89,21 @@ lc_status autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, c
     const int d = ix->p.d;
     Sample s;
     s.n = n;
+    s.nb = std::max<int64_t>(n, tp->batch);
     s.k = tp->k;
-    if (cudaMalloc(&s.q, (size_t)n * d * 4) != cudaSuccess || cudaMalloc(&s.ids, (size_t)n * tp->k * 4) != cudaSuccess ||
-        cudaMalloc(&s.dists, (size_t)n * tp->k * 4) != cudaSuccess ||
+    if (cudaMalloc(&s.q, (size_t)s.nb * d * 4) != cudaSuccess || cudaMalloc(&s.ids, (size_t)s.nb * tp->k * 4) != cudaSuccess ||
+        cudaMalloc(&s.dists, (size_t)s.nb * tp->k * 4) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&s.e0) != cudaSuccess || cudaEventCreate(&s.e1) != cudaSuccess) {
         set_error("autotune: device allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
         return LC_ERR_OOM;
     }
-    if (cudaMemcpy(s.q, q, (size_t)n * d * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-        set_error("autotune: sample upload failed");
-        return LC_ERR_CUDA;
+    for (int64_t a = 0; a < s.nb; a += n) {
+        const int64_t c = std::min(n, s.nb - a);
+        if (cudaMemcpy(s.q + a * d, q, (size_t)c * d * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("autotune: sample upload failed");
+            return LC_ERR_CUDA;
+        }
     }
     const int reps = std::max(1, tp->reps);
     // reference top-1: the caller's exact neighbours, or the plain search at 4x efSearch

@@ -54,7 +54,7 @@ class lc_search_params(ctypes.Structure):
 
 
 class lc_tune_params(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "allow_fp16", "max_beam", "reps")]
+    _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "allow_fp16", "max_beam", "reps", "batch")]
 
 
 class lc_tune_result(ctypes.Structure):
@@ -364,12 +364,12 @@ def lc_plan_free(pl):
 
 
 def lc_autotune(ix, q: np.ndarray, gt=None, k: int = 10, ef: int = 64, allow_fp16: bool = True,
-                max_beam: int = 8, reps: int = 3) -> lc_tune_result:
+                max_beam: int = 8, reps: int = 3, batch: int = 0) -> lc_tune_result:
     """Tune the search on a host sample q [n][d] (float32) with optional exact neighbour ids
-    gt [n]; returns the lc_tune_result (see include/lc.h)."""
+    gt [n], timing batches of ``batch`` queries; returns the lc_tune_result (include/lc.h)."""
     q = np.ascontiguousarray(q, np.float32)
     g = None if gt is None else np.ascontiguousarray(gt, np.int32)
-    tp = lc_tune_params(k=k, ef=ef, allow_fp16=int(allow_fp16), max_beam=max_beam, reps=reps)
+    tp = lc_tune_params(k=k, ef=ef, allow_fp16=int(allow_fp16), max_beam=max_beam, reps=reps, batch=batch)
     out = lc_tune_result()
     _check(lib().lc_autotune(ix, _ptr(q), q.shape[0], _ptr(g), ctypes.byref(tp), ctypes.byref(out)))
     return out

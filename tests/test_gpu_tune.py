@@ -19,12 +19,12 @@ def _search(h, q, sp):
     return ids, ds
 
 
-@pytest.mark.parametrize("with_gt", [True, False])
-def test_autotune_meets_target(mix10k, with_gt):
+@pytest.mark.parametrize("with_gt,batch", [(True, 0), (False, 0), (True, 4000)])
+def test_autotune_meets_target(mix10k, with_gt, batch):
     ix, xb, xq = mix10k
     h = handle("mix10k", ix)
     gt = oracle.knn(xb, xq, 1)[0][:, 0].astype(np.int32) if with_gt else None
-    r = lc.lc_autotune(h, xq, gt, k=10, ef=48, reps=2)
+    r = lc.lc_autotune(h, xq, gt, k=10, ef=48, reps=2, batch=batch)
     assert r.tried > 10
     assert r.recall >= r.target > 0.3
     assert r.ms <= r.base_ms
