@@ -417,6 +417,8 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[20000, 50000, 100000, 200000],
                     help="open-loop offered loads, queries per second")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="target duration of each open-loop point")
+    ap.add_argument("--visited-log", type=int, default=0,
+                    help="visited table size 2^v of the single form run by --mode plain / batched (0: automatic)")
     ap.add_argument("--lut", default="fp32", choices=["fp32", "fp16"],
                     help="level-1 codebook precision of the single form run by --mode plain / batched")
     ap.add_argument("--mode", default="both", choices=["both", "plain", "batched"],
@@ -453,13 +455,13 @@ def main():
     stream = torch.cuda.Stream()
     lc.lc_profile(h, True)
 
-    def params(level, mode, prec=lc.LC_LUT_FP32):
+    def params(level, mode, prec=lc.LC_LUT_FP32, vlog=0):
         """Search parameters at one sweep level: efSearch, or (uneven workloads) the factor
         every query's own efSearch is scaled by; returns (sp, host efq or None)."""
         efq = uneven_ef(w, nq, level)
         ef = int(efq.max()) if uneven else int(level)
         sp = lc.lc_default_search_params(k, ef, mode=mode, beam=args.beam if mode == lc.LC_MODE_BATCHED else 1,
-                                         lut_prec=prec)
+                                         lut_prec=prec, visited_log=vlog)
         return sp, efq
 
     def measure(form, steps):
@@ -500,13 +502,13 @@ def main():
     batched = None
     lut1 = lc.LC_LUT_FP16 if args.lut == "fp16" else lc.LC_LUT_FP32
     if args.mode == "batched":
-        f_b = params(base_level, lc.LC_MODE_BATCHED, lut1)
+        f_b = params(base_level, lc.LC_MODE_BATCHED, lut1, args.visited_log)
         batched = measure(f_b, args.steps)
         batched.update(ef=base_level, sweep=[])
         plain, target = None, batched["recall"]
         best, best_form, best_name = batched, f_b, f"batched(beam={args.beam}){', fp16 codebook' if lut1 else ''}"
     else:
-        f_p = params(base_level, lc.LC_MODE_PLAIN, lut1 if args.mode == "plain" else lc.LC_LUT_FP32)
+        f_p = params(base_level, lc.LC_MODE_PLAIN, *((lut1, args.visited_log) if args.mode == "plain" else ()))
         plain = measure(f_p, args.steps)
         plain.update(ef=base_level)
         target = plain["recall"]

@@ -15,7 +15,8 @@ struct DeviceIndex {
     int32_t ep = -1;
     float *Rt = nullptr;          // [d][d], Rt[u*d + t] = R[t][u]
     float *C1 = nullptr, *C2 = nullptr, *B = nullptr;
-    void *C1h = nullptr;          // C1 rounded to FP16 (device __half), for the FP16 mode
+    float *C1w = nullptr;         // C1 in the walk's shared-memory layout (FP32)
+    void *C1h = nullptr;          // the same rounded to FP16 (device __half), for the FP16 mode
     uint8_t *codes1 = nullptr, *codes2b = nullptr;   // codes2b: residual codes padded to M2P bytes, codeword id last
     int M2P = 0;
     int bM = 1, bK = 256;         // regression blocks and codewords per block (B: [bM][bK][9])

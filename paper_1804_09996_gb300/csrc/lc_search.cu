@@ -49,7 +49,7 @@ void device_free(DeviceIndex *dv)
     int cur = -1;
     cudaGetDevice(&cur);
     if (dv->device >= 0) cudaSetDevice(dv->device);
-    cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B); cfree(dv->C1h);
+    cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B); cfree(dv->C1h); cfree(dv->C1w);
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
@@ -74,7 +74,7 @@ struct WalkArgs {
     int64_t nq;
     int d;
     const float *Rt, *C1;
-    const __half *C1h;     // the same codebook in FP16 (FP16 mode)
+    const __half *C1h;     // the same codebook in FP16 (FP16 mode); both in the walk's layout
     const uint8_t *codes1;
     const int32_t *adj0, *upper_off, *upper_adj;
     int32_t ep;
@@ -108,8 +108,25 @@ struct WalkSmem {
     size_t yq, stage, wkey, wflag, cand, cunsorted, slot, rowbuf, hash, total;
 };
 
+// Layout of the walk's level-1 codebook.  With a uniform split (D1 > 0) in FP16, and with
+// D1 = 2 in FP32, it is interleaved by sub-space: the P values (D1 rounded up to 2, 4 or 8)
+// of centroid c in sub-space j sit at (c * M1 + j) * P, so a lane's sub-space term takes one
+// vector load and the lanes of one shared-memory phase hit distinct banks.  Otherwise row c
+// holds centroid c of every sub-space in its own coordinates ([256][d]); with D1 = 3 in FP32
+// (3 j + u mod 32 is a permutation of the lanes) that is already conflict-free.
+__host__ __device__ constexpr bool walk_il(int D1, int es) { return D1 > 0 && (es == 2 || D1 == 2); }
+__host__ __device__ constexpr int walk_pad(int D1) { return D1 <= 2 ? 2 : (D1 <= 4 ? 4 : 8); }
 // bytes of the level-1 codebook in shared memory (es = 4: FP32, es = 2: FP16)
-__host__ __device__ inline size_t walk_c1_bytes(int d, size_t es = 4) { return align_up((size_t)256 * d * es, 128); }
+__host__ __device__ inline size_t walk_c1_bytes(int d, int M1, int D1, size_t es)
+{
+    return align_up(walk_il(D1, (int)es) ? (size_t)256 * M1 * walk_pad(D1) * es : (size_t)256 * d * es, 128);
+}
+// compile-time sub-space width of the uniform splits 96/16, 96/32 and 128/64 (0: other)
+__host__ __device__ constexpr int walk_variant_d1(int variant) { return variant == 1 ? 6 : variant == 2 ? 3 : variant == 3 ? 2 : 0; }
+inline int walk_variant(int M1, int d)
+{
+    return (M1 == 16 && d == 96) ? 1 : (M1 == 32 && d == 96) ? 2 : (M1 == 64 && d == 128) ? 3 : 0;
+}
 
 __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
@@ -201,27 +218,71 @@ template <int M1, int D1>
 struct LaneGeo {
     static constexpr int NSUB = M1 == 64 ? 2 : 1;
     static constexpr int DMAX = D1 > 0 ? D1 : (M1 == 16 ? 16 : (M1 == 32 ? 8 : 4));   // d <= 256
-    int off[NSUB], len[NSUB];
+    int off[NSUB], len[NSUB], j[NSUB];
     float y[NSUB][DMAX];
 };
+
+__device__ __forceinline__ void half2_to_f(uint32_t w, float &a, float &b)
+{
+    const __half2 h = *reinterpret_cast<const __half2 *>(&w);
+    a = __low2float(h);
+    b = __high2float(h);
+}
+
+// The coordinates of centroid c in this lane's k-th sub-space, as FP32.
+template <int M1, int D1, typename CT>
+__device__ __forceinline__ void load_row(const CT *C1s, int d, int c, const LaneGeo<M1, D1> &g, int k,
+                                         float (&x)[LaneGeo<M1, D1>::DMAX])
+{
+    constexpr int DMAX = LaneGeo<M1, D1>::DMAX;
+    if constexpr (walk_il(D1, (int)sizeof(CT))) {
+        constexpr int P = walk_pad(D1);
+        const CT *p = C1s + ((size_t)c * M1 + g.j[k]) * P;
+        float t[P];
+        if constexpr (sizeof(CT) == 4) {                   // FP32, P = 2
+            const float2 f = *reinterpret_cast<const float2 *>(p);
+            t[0] = f.x;
+            t[1] = f.y;
+        } else if constexpr (P == 2) {
+            half2_to_f(*reinterpret_cast<const uint32_t *>(p), t[0], t[1]);
+        } else if constexpr (P == 4) {
+            const uint2 w = *reinterpret_cast<const uint2 *>(p);
+            half2_to_f(w.x, t[0], t[1]);
+            half2_to_f(w.y, t[2], t[3]);
+        } else {
+            const uint4 w = *reinterpret_cast<const uint4 *>(p);
+            half2_to_f(w.x, t[0], t[1]);
+            half2_to_f(w.y, t[2], t[3]);
+            half2_to_f(w.z, t[4], t[5]);
+            half2_to_f(w.w, t[6], t[7]);
+        }
+#pragma unroll
+        for (int u = 0; u < DMAX; u++) x[u] = t[u];
+    } else {
+        const CT *row = C1s + c * d + g.off[k];
+#pragma unroll
+        for (int u = 0; u < DMAX; u++) x[u] = (D1 > 0 || u < g.len[k]) ? to_f(row[u]) : 0.f;
+    }
+}
 
 // ||y'^j - C1_j[c]||^2 in the fixed order of the sub-space's coordinates.
 template <int M1, int D1, typename CT>
 __device__ __forceinline__ float part_dist(const CT *C1s, int d, int c, const LaneGeo<M1, D1> &g, int k)
 {
-    const CT *row = C1s + c * d + g.off[k];
+    float x[LaneGeo<M1, D1>::DMAX];
+    load_row<M1, D1, CT>(C1s, d, c, g, k, x);
     float s = 0.f;
     if (D1 > 0) {
 #pragma unroll
         for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) {
-            float df = g.y[k][u] - to_f(row[u]);
+            float df = g.y[k][u] - x[u];
             s = fmaf(df, df, s);
         }
     } else {
 #pragma unroll
         for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++)
             if (u < g.len[k]) {
-                float df = g.y[k][u] - to_f(row[u]);
+                float df = g.y[k][u] - x[u];
                 s = fmaf(df, df, s);
             }
     }
@@ -247,13 +308,14 @@ template <int M1, int D1, typename CT>
 __device__ __forceinline__ void pair_dist(const CT *C1s, int d, int c0, int c1, const LaneGeo<M1, D1> &g,
                                           int k, float &s0, float &s1)
 {
-    const CT *r0 = C1s + c0 * d + g.off[k];
-    const CT *r1 = C1s + c1 * d + g.off[k];
+    float x0[LaneGeo<M1, D1>::DMAX], x1[LaneGeo<M1, D1>::DMAX];
+    load_row<M1, D1, CT>(C1s, d, c0, g, k, x0);
+    load_row<M1, D1, CT>(C1s, d, c1, g, k, x1);
     unsigned long long acc = 0ull;                   // (+0.f, +0.f)
 #pragma unroll
     for (int u = 0; u < D1; u++) {
         const unsigned long long yy = pack2(g.y[k][u], g.y[k][u]);
-        const unsigned long long cc = pack2(to_f(r0[u]), to_f(r1[u]));
+        const unsigned long long cc = pack2(x0[u], x1[u]);
         unsigned long long df;
         asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(df) : "l"(yy), "l"(cc));
         asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(acc) : "l"(df), "l"(acc));
@@ -388,11 +450,12 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(sizeof(CT) == 4 ? a.C1 : (const void *)a.C1h);
         uint4 *dst = reinterpret_cast<uint4 *>(C1s);
-        for (int i = threadIdx.x; i < (int)(256 * d * sizeof(CT) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+        const int n16 = (int)(walk_c1_bytes(d, M1, D1, sizeof(CT)) / 16);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
     const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam);
-    unsigned char *base = smem_raw + walk_c1_bytes(d, sizeof(CT)) + (size_t)warp * L.total;
+    unsigned char *base = smem_raw + walk_c1_bytes(d, M1, D1, sizeof(CT)) + (size_t)warp * L.total;
     float *yq = reinterpret_cast<float *>(base + L.yq);
     uint8_t *stage = base + L.stage;
     uint64_t *wkey = reinterpret_cast<uint64_t *>(base + L.wkey);
@@ -436,6 +499,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
 #pragma unroll
         for (int k = 0; k < LaneGeo<M1, D1>::NSUB; k++) {
             const int j = M1 == 16 ? (lane & 15) : lane + 32 * k;
+            g.j[k] = j;
             g.off[k] = a.s1.off[j];
             g.len[k] = a.s1.len[j];
 #pragma unroll
@@ -893,11 +957,27 @@ lc_status upload(lc_index *ix)
         std::memcpy(c2b.data() + i * M2P, ix->codes2.data() + i * M2, M2);
         for (int m = 0; m < nb; m++) c2b[i * M2P + M2P - nb + m] = ix->beta[i * bM + m];
     }
-    std::vector<__half> c1h(ix->C1.size());
-    for (size_t i = 0; i < c1h.size(); i++) c1h[i] = __float2half_rn(ix->C1[i]);   // round to nearest even
+    // the walk's level-1 codebook, FP32 and FP16 (rounded to nearest even), in its layout
+    const int M1 = ix->p.M1, D1 = walk_variant_d1(walk_variant(M1, d));
+    std::vector<int> so, sl;
+    splits(d, M1, so, sl);
+    auto walk_layout = [&](int es, auto put) {
+        if (!walk_il(D1, es)) {
+            for (size_t i = 0; i < ix->C1.size(); i++) put(i, ix->C1[i]);
+            return;
+        }
+        const int P = walk_pad(D1);
+        for (int c = 0; c < 256; c++)
+            for (int j = 0; j < M1; j++)
+                for (int u = 0; u < sl[j]; u++) put(((size_t)c * M1 + j) * P + u, ix->C1[(size_t)c * d + so[j] + u]);
+    };
+    std::vector<float> c1w(walk_c1_bytes(d, M1, D1, 4) / 4, 0.f);
+    walk_layout(4, [&](size_t i, float v) { c1w[i] = v; });
+    std::vector<__half> c1h(walk_c1_bytes(d, M1, D1, 2) / 2, __float2half_rn(0.f));
+    walk_layout(2, [&](size_t i, float v) { c1h[i] = __float2half_rn(v); });
     __half *c1h_dev = static_cast<__half *>(dv->C1h);
     bool ok = dupload(dv->Rt, Rt) && dupload(dv->C1, ix->C1) && dupload(dv->C2, ix->C2) &&
-              dupload(c1h_dev, c1h) &&
+              dupload(dv->C1w, c1w) && dupload(c1h_dev, c1h) &&
               dupload(dv->B, ix->B) && dupload(dv->codes1, ix->codes1) &&
               dupload(dv->codes2b, c2b) &&
               dupload(dv->adj0, ix->adj0) && dupload(dv->upper_off, off) &&
@@ -937,7 +1017,7 @@ template <int M1, int D1, typename CT>
 static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int want, int *wpc_out,
                                int *grid_out, size_t *smem_out)
 {
-    size_t c1 = walk_c1_bytes(wa.d, sizeof(CT));
+    size_t c1 = walk_c1_bytes(wa.d, M1, D1, sizeof(CT));
     if (c1 + smem_per_warp > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
     int wpc = (int)std::min<size_t>(MAX_WALK_WARPS, (MAX_SMEM_PER_BLOCK - c1) / smem_per_warp);
     if (want > 0) wpc = std::min(wpc, want);
@@ -1044,8 +1124,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     const int efcap = (int)align_up(P.efp, 32);
     P.per_warp = walk_smem(dv->M1, dv->d, efcap, P.hash_log, P.beam).total;
     // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
-    P.variant = (dv->M1 == 16 && dv->d == 96) ? 1 : (dv->M1 == 32 && dv->d == 96) ? 2
-              : (dv->M1 == 64 && dv->d == 128) ? 3 : 0;
+    P.variant = walk_variant(dv->M1, dv->d);
     WalkArgs wa{};
     wa.nq = nq;
     wa.d = dv->d;
@@ -1054,7 +1133,8 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
                             : launch_any<float>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem);
     if (ce == cudaErrorInvalidConfiguration) {
         set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
-                  "lower efSearch or visited_log", P.per_warp, walk_c1_bytes(dv->d, P.half ? 2 : 4));
+                  "lower efSearch or visited_log", P.per_warp,
+                  walk_c1_bytes(dv->d, dv->M1, walk_variant_d1(P.variant), P.half ? 2 : 4));
         return LC_ERR_CAPACITY;
     }
     if (ce != cudaSuccess) {
@@ -1097,7 +1177,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
 {
     WalkArgs wa{};
     wa.Q = dq; wa.Q8 = dq8; wa.efq = defq; wa.k = P.k; wa.nq = nq; wa.d = dv->d;
-    wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.C1h = static_cast<const __half *>(dv->C1h); wa.codes1 = dv->codes1;
+    wa.Rt = dv->Rt; wa.C1 = dv->C1w; wa.C1h = static_cast<const __half *>(dv->C1h); wa.codes1 = dv->codes1;
     wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
     wa.ep = dv->ep; wa.max_level = dv->max_level;
     wa.efp = P.efp; wa.efcap = (int)align_up(P.efp, 32);
@@ -1366,7 +1446,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
 
     WalkArgs wa{};
     wa.Q = q; wa.nq = nq; wa.d = dv->d;
-    wa.Rt = dv->Rt; wa.C1 = dv->C1; wa.codes1 = dv->codes1;
+    wa.Rt = dv->Rt; wa.C1 = dv->C1w; wa.codes1 = dv->codes1;
     wa.adj0 = dv->adj0; wa.upper_off = dv->upper_off; wa.upper_adj = dv->upper_adj;
     wa.ep = dv->ep; wa.max_level = dv->max_level;
     wa.efp = efp; wa.efcap = (int)align_up(efp, 32); wa.k = k;
