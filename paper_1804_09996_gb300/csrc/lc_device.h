@@ -47,6 +47,8 @@ struct SearchPlan {
     int wpc = 0, grid = 0;               // walk: warps per CTA, CTAs
     size_t per_warp = 0, smem = 0;
     int rw = 0, rgrid = 0;               // refine: warps per CTA, CTAs
+    int qgrid = 0;                       // rotation: CTAs
+    size_t qsm = 0;                      // rotation: shared memory
     size_t rsm = 0;
     bool rboth = false;                  // both codebooks in shared memory
     size_t yq_elems = 0, sl_elems = 0, spill_elems = 0;
@@ -54,7 +56,7 @@ struct SearchPlan {
 
 // Device scratch of one search in flight.
 struct SearchScratch {
-    float *yq = nullptr;                 // [nq][d] (refinement only)
+    float *yq = nullptr;                 // [nq][d] rotated queries
     int32_t *shortlist = nullptr;        // [nq][R] (refinement only)
     int32_t *spill = nullptr;            // [grid * wpc][2^spill_log]
     int32_t *status = nullptr;           // 1 word

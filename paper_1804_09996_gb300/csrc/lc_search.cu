@@ -88,6 +88,7 @@ struct WalkArgs {
     int hash_log;     // shared-memory visited table: 2^hash_log entries
     int spill_log;    // global spill table per warp: 2^spill_log entries
     int32_t *spill;
+    const float *yq_in;    // non-null: y' = R y computed by rotate_kernel (read, not recomputed)
     float *yq_out;
     int32_t *short_out;
     int32_t *ids_out;
@@ -108,18 +109,26 @@ struct WalkSmem {
     size_t yq, stage, wkey, wflag, cand, cunsorted, slot, rowbuf, hash, total;
 };
 
-// Layout of the walk's level-1 codebook.  With a uniform split (D1 > 0) in FP16, and with
-// D1 = 2 in FP32, it is interleaved by sub-space: the P values (D1 rounded up to 2, 4 or 8)
-// of centroid c in sub-space j sit at (c * M1 + j) * P, so a lane's sub-space term takes one
-// vector load and the lanes of one shared-memory phase hit distinct banks.  Otherwise row c
-// holds centroid c of every sub-space in its own coordinates ([256][d]); with D1 = 3 in FP32
-// (3 j + u mod 32 is a permutation of the lanes) that is already conflict-free.
-__host__ __device__ constexpr bool walk_il(int D1, int es) { return D1 > 0 && (es == 2 || D1 == 2); }
+// Layout of the walk's level-1 codebook in shared memory, chosen so that a lane's sub-space
+// term takes few loads and the lanes of one shared-memory phase hit distinct banks:
+//  0 (row-major): row c holds centroid c of every sub-space in its own coordinates ([256][d]).
+//    Used in FP32 with 3 or 6 dimensions per sub-space (3 j + u mod 32 permutes the lanes)
+//    and for non-uniform splits.
+//  1 (interleaved): the P values (D1 rounded up to 2 or 8) of centroid c in sub-space j sit
+//    at (c * M1 + j) * P: one vector load.  FP32 and FP16 with 2 dimensions, FP16 with 6.
+//  2 (split, FP16 with 3 dimensions): the first two values as a half2 array [256][M1], the
+//    third as a half array [256][M1] behind it: two loads, no padding.
+__host__ __device__ constexpr int walk_layout(int D1, int es)
+{
+    return D1 == 0 ? 0 : D1 == 2 ? 1 : es == 4 ? 0 : D1 == 3 ? 2 : 1;
+}
 __host__ __device__ constexpr int walk_pad(int D1) { return D1 <= 2 ? 2 : (D1 <= 4 ? 4 : 8); }
 // bytes of the level-1 codebook in shared memory (es = 4: FP32, es = 2: FP16)
 __host__ __device__ inline size_t walk_c1_bytes(int d, int M1, int D1, size_t es)
 {
-    return align_up(walk_il(D1, (int)es) ? (size_t)256 * M1 * walk_pad(D1) * es : (size_t)256 * d * es, 128);
+    const int L = walk_layout(D1, (int)es);
+    const size_t n = L == 1 ? (size_t)256 * M1 * walk_pad(D1) : (size_t)256 * d;
+    return align_up(n * es, 128);
 }
 // compile-time sub-space width of the uniform splits 96/16, 96/32 and 128/64 (0: other)
 __host__ __device__ constexpr int walk_variant_d1(int variant) { return variant == 1 ? 6 : variant == 2 ? 3 : variant == 3 ? 2 : 0; }
@@ -131,18 +140,21 @@ inline int walk_variant(int M1, int d)
 __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
 
-__host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log, int beam)
+// own_rot: the walk rotates the query itself (y' in shared memory); otherwise y' is read from
+// the rotation kernel's output.  The adjacency rows of a step are only read before the
+// candidates are collected, so they share the unsorted-candidate area.
+__host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log, int beam, bool own_rot)
 {
     WalkSmem s;
     size_t o = 0;
-    s.yq = o;        o += align_up((size_t)d * 4, 16);
+    s.yq = o;        o += own_rot ? align_up((size_t)d * 4, 16) : 0;
     s.stage = o;     o += (size_t)32 * M1;
     s.wkey = o;      o += (size_t)2 * efcap * 8;
     s.wflag = o;     o += align_up((size_t)2 * efcap, 16);
     s.cand = o;      o += (size_t)32 * beam * 8;
     s.cunsorted = o; o += (size_t)32 * beam * 8;
+    s.rowbuf = s.cunsorted;
     s.slot = o;      o += (size_t)32 * beam * 4;
-    s.rowbuf = o;    o += (size_t)32 * beam * 4;
     s.hash = o;      o += ((size_t)1 << hash_log) * 4;
     s.total = align_up(o, 128);
     return s;
@@ -235,7 +247,12 @@ __device__ __forceinline__ void load_row(const CT *C1s, int d, int c, const Lane
                                          float (&x)[LaneGeo<M1, D1>::DMAX])
 {
     constexpr int DMAX = LaneGeo<M1, D1>::DMAX;
-    if constexpr (walk_il(D1, (int)sizeof(CT))) {
+    constexpr int LAYOUT = walk_layout(D1, (int)sizeof(CT));
+    if constexpr (LAYOUT == 2) {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(C1s + ((size_t)c * M1 + g.j[k]) * 2);
+        half2_to_f(w, x[0], x[1]);
+        x[2] = to_f(C1s[(size_t)256 * M1 * 2 + (size_t)c * M1 + g.j[k]]);
+    } else if constexpr (LAYOUT == 1) {
         constexpr int P = walk_pad(D1);
         const CT *p = C1s + ((size_t)c * M1 + g.j[k]) * P;
         float t[P];
@@ -245,10 +262,6 @@ __device__ __forceinline__ void load_row(const CT *C1s, int d, int c, const Lane
             t[1] = f.y;
         } else if constexpr (P == 2) {
             half2_to_f(*reinterpret_cast<const uint32_t *>(p), t[0], t[1]);
-        } else if constexpr (P == 4) {
-            const uint2 w = *reinterpret_cast<const uint2 *>(p);
-            half2_to_f(w.x, t[0], t[1]);
-            half2_to_f(w.y, t[2], t[3]);
         } else {
             const uint4 w = *reinterpret_cast<const uint4 *>(p);
             half2_to_f(w.x, t[0], t[1]);
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
     }
     __syncthreads();
-    const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam);
+    const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam, a.yq_in == nullptr);
     unsigned char *base = smem_raw + walk_c1_bytes(d, M1, D1, sizeof(CT)) + (size_t)warp * L.total;
     float *yq = reinterpret_cast<float *>(base + L.yq);
     uint8_t *stage = base + L.stage;
@@ -478,7 +491,10 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         // this query's ef' = max(ef, k)
         const int efp = a.efq ? max(min(max(__ldg(a.efq + q), 1), a.efp), a.k) : a.efp;
         // rotation y' = R y (fixed order u = 0..d-1); uint8 queries convert exactly to FP32
-        if (a.Q8) {
+        const float *yrot = a.yq_in ? a.yq_in + q * d : yq;
+        if (a.yq_in) {
+            // computed by rotate_kernel
+        } else if (a.Q8) {
             const uint8_t *y = a.Q8 + q * d;
             for (int t = lane; t < d; t += 32) {
                 float s = 0.f;
@@ -503,7 +519,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             g.off[k] = a.s1.off[j];
             g.len[k] = a.s1.len[j];
 #pragma unroll
-            for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) g.y[k][u] = u < g.len[k] ? yq[g.off[k] + u] : 0.f;
+            for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) g.y[k][u] = u < g.len[k] ? yrot[g.off[k] + u] : 0.f;
         }
         int my_slot;
 
@@ -580,7 +596,43 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             __syncwarp();
             // visited test row by row (row order, then slot order); fresh nodes are appended
             int ns = 0;
-            for (int r = 0; r < nb; r++) {
+            if (!spilled && hcount + 32 * nb <= H / 2) {
+                // every row fits in the shared table without a switch to the spill table: the
+                // first probes of up to 4 rows are issued together, then each row is resolved
+                // in row order (a node in two rows probes the same bucket first, so it is
+                // fresh in the earlier row)
+                const uint32_t Hm = (uint32_t)H - 1;
+                for (int r0 = 0; r0 < nb; r0 += 4) {
+                    int32_t ev[4], ov[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        ev[u] = r0 + u < nb ? rowbuf[(r0 + u) * DEG + lane] : -1;
+                        ov[u] = ev[u] >= 0 ? atomicCAS(hash + (hash32(ev[u]) & Hm), -1, ev[u]) : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        if (r0 + u >= nb) break;
+                        const int32_t e = ev[u];
+                        bool fresh = e >= 0 && ov[u] == -1;
+                        if (e >= 0 && ov[u] != -1 && ov[u] != e) {
+                            // collision: continue the linear probe
+                            uint32_t h = hash32(e) & Hm;
+                            for (uint32_t p = 1; p <= Hm; p++) {
+                                h = (h + 1) & Hm;
+                                const int32_t old = atomicCAS(hash + h, -1, e);
+                                if (old == -1) { fresh = true; break; }
+                                if (old == e) break;
+                            }
+                        }
+                        const unsigned fm = __ballot_sync(FULL, fresh);
+                        if (fresh) slot[ns + __popc(fm & lt_mask)] = e;
+                        const int nf = __popc(fm);
+                        ns += nf;
+                        n_dist += nf;
+                        hcount += nf;
+                    }
+                }
+            } else for (int r = 0; r < nb; r++) {
                 // switch to the global table before the shared one passes half full
                 if (!spilled && hcount + 32 > H / 2) {
                     spilled = true;
@@ -666,7 +718,8 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         // outputs
         const uint64_t *W = wkey + buf * a.efcap;
         if (a.refine) {
-            for (int t = lane; t < d; t += 32) a.yq_out[q * d + t] = yq[t];
+            if (!a.yq_in)
+                for (int t = lane; t < d; t += 32) a.yq_out[q * d + t] = yq[t];
             for (int i = lane; i < a.R; i += 32)
                 a.short_out[q * a.R + i] = (!failed && i < wn) ? key_id(W[i]) : -1;
         } else {
@@ -703,6 +756,47 @@ struct RefineArgs {
     uint8_t sub1[256], sub2[256];   // sub-space of each dimension, per level
     uint8_t subb[256];              // regression block of each dimension
 };
+
+// ------------------------------------------------------------------------------------------
+// Query rotation y' = R y (Section 3.3 / 5.1: OPQ rotates vectors and queries alike) for a
+// whole batch ahead of the walk.  Every output coordinate is the fixed-order sum over
+// u = 0..d-1 of R[t][u] y[u] (fmaf chain), the arithmetic of the walk's own rotation, so the
+// walk gives bit-identical results either way.  R^T sits in shared memory when it fits
+// (d <= 200); uint8 queries convert exactly to FP32.
+constexpr int ROT_Q = 8;            // queries per block step
+constexpr int ROT_THREADS = 256;
+__host__ __device__ inline bool rotate_rt_shared(int d) { return (size_t)d * d * 4 <= 160 * 1024; }
+__host__ __device__ inline size_t rotate_smem(int d)
+{
+    return ((rotate_rt_shared(d) ? (size_t)d * d : 0) + (size_t)ROT_Q * d) * 4;
+}
+
+__global__ void __launch_bounds__(ROT_THREADS) rotate_kernel(const float *Q, const uint8_t *Q8, int64_t nq, int d,
+                                                             const float *Rt, float *yq)
+{
+    extern __shared__ __align__(16) float rsm[];
+    const bool shared_rt = rotate_rt_shared(d);
+    float *ys = rsm + (shared_rt ? d * d : 0);
+    const float *R = Rt;
+    if (shared_rt) {
+        for (int i = threadIdx.x; i < d * d; i += blockDim.x) rsm[i] = __ldg(Rt + i);
+        R = rsm;
+    }
+    for (int64_t q0 = (int64_t)blockIdx.x * ROT_Q; q0 < nq; q0 += (int64_t)gridDim.x * ROT_Q) {
+        const int nb = nq - q0 < ROT_Q ? (int)(nq - q0) : ROT_Q;
+        __syncthreads();                               // Rt loaded / previous step's ys consumed
+        for (int i = threadIdx.x; i < nb * d; i += blockDim.x)
+            ys[i] = Q8 ? (float)__ldg(Q8 + q0 * d + i) : __ldg(Q + q0 * d + i);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nb * d; i += blockDim.x) {
+            const int qq = i / d, t = i - qq * d;
+            const float *y = ys + qq * d;
+            float s = 0.f;
+            for (int u = 0; u < d; u++) s = fmaf(R[u * d + t], y[u], s);
+            yq[(q0 + qq) * d + t] = s;
+        }
+    }
+}
 
 constexpr int REF_CH = 8;            // candidates staged at a time
 
@@ -961,20 +1055,21 @@ lc_status upload(lc_index *ix)
     const int M1 = ix->p.M1, D1 = walk_variant_d1(walk_variant(M1, d));
     std::vector<int> so, sl;
     splits(d, M1, so, sl);
-    auto walk_layout = [&](int es, auto put) {
-        if (!walk_il(D1, es)) {
-            for (size_t i = 0; i < ix->C1.size(); i++) put(i, ix->C1[i]);
-            return;
-        }
-        const int P = walk_pad(D1);
+    auto put_layout = [&](int es, auto put) {
+        const int L = walk_layout(D1, es), P = walk_pad(D1);
         for (int c = 0; c < 256; c++)
             for (int j = 0; j < M1; j++)
-                for (int u = 0; u < sl[j]; u++) put(((size_t)c * M1 + j) * P + u, ix->C1[(size_t)c * d + so[j] + u]);
+                for (int u = 0; u < sl[j]; u++) {
+                    const float v = ix->C1[(size_t)c * d + so[j] + u];
+                    if (L == 0) put((size_t)c * d + so[j] + u, v);
+                    else if (L == 1) put(((size_t)c * M1 + j) * P + u, v);
+                    else put(u < 2 ? ((size_t)c * M1 + j) * 2 + u : (size_t)256 * M1 * 2 + (size_t)c * M1 + j, v);
+                }
     };
     std::vector<float> c1w(walk_c1_bytes(d, M1, D1, 4) / 4, 0.f);
-    walk_layout(4, [&](size_t i, float v) { c1w[i] = v; });
+    put_layout(4, [&](size_t i, float v) { c1w[i] = v; });
     std::vector<__half> c1h(walk_c1_bytes(d, M1, D1, 2) / 2, __float2half_rn(0.f));
-    walk_layout(2, [&](size_t i, float v) { c1h[i] = __float2half_rn(v); });
+    put_layout(2, [&](size_t i, float v) { c1h[i] = __float2half_rn(v); });
     __half *c1h_dev = static_cast<__half *>(dv->C1h);
     bool ok = dupload(dv->Rt, Rt) && dupload(dv->C1, ix->C1) && dupload(dv->C2, ix->C2) &&
               dupload(dv->C1w, c1w) && dupload(c1h_dev, c1h) &&
@@ -1122,7 +1217,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     P.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)P.efp * 32)));
     P.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)P.efp * 64)));
     const int efcap = (int)align_up(P.efp, 32);
-    P.per_warp = walk_smem(dv->M1, dv->d, efcap, P.hash_log, P.beam).total;
+    P.per_warp = walk_smem(dv->M1, dv->d, efcap, P.hash_log, P.beam, false).total;
     // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
     P.variant = walk_variant(dv->M1, dv->d);
     WalkArgs wa{};
@@ -1143,8 +1238,19 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
         return LC_ERR_CUDA;
     }
     P.spill_elems = ((size_t)P.grid * P.wpc) << P.spill_log;
+    P.yq_elems = (size_t)nq * dv->d;
+    {
+        const size_t rsm = rotate_smem(dv->d);
+        if (cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM_PER_BLOCK) != cudaSuccess) {
+            set_error("rotation kernel configuration failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return LC_ERR_CUDA;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rotate_kernel, ROT_THREADS, rsm);
+        P.qsm = rsm;
+        P.qgrid = (int)std::min<int64_t>((nq + ROT_Q - 1) / ROT_Q, (int64_t)std::max(per_sm, 1) * dv->num_sms);
+    }
     if (P.refine) {
-        P.yq_elems = (size_t)nq * dv->d;
         P.sl_elems = (size_t)nq * P.R;
         const size_t per = refine_smem(dv->M1, dv->M2P, P.R, dv->bM);
         const size_t cbytes = (size_t)256 * dv->d * 4;
@@ -1190,6 +1296,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
     wa.status = sc.status;
     wa.counter = sc.counter;
     wa.stats_out = dstats;
+    wa.yq_in = sc.yq;
     if (P.refine) {
         wa.yq_out = sc.yq;
         wa.short_out = sc.shortlist;
@@ -1210,8 +1317,14 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(dv->ev[0], st);
     }
-    cudaError_t ce = P.half ? run_any<__half>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st)
-                            : run_any<float>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st);
+    rotate_kernel<<<std::max(P.qgrid, 1), ROT_THREADS, P.qsm, st>>>(dq, dq8, nq, dv->d, dv->Rt, sc.yq);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        set_error("rotation kernel launch failed: %s", cudaGetErrorString(ce));
+        return LC_ERR_CUDA;
+    }
+    ce = P.half ? run_any<__half>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st)
+                : run_any<float>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st);
     if (profile) cudaEventRecord(dv->ev[1], st);
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
@@ -1329,8 +1442,8 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
         if (stats) cudaMemcpy(stats, hs.data(), hs.size() * 4, kk);
         return LC_OK;
     }
-    if (!grow(dv->spill, dv->spill_cap, P.spill_elems) ||
-        (P.refine && (!grow(dv->yq, dv->yq_cap, P.yq_elems) || !grow(dv->shortlist, dv->sl_cap, P.sl_elems)))) {
+    if (!grow(dv->spill, dv->spill_cap, P.spill_elems) || !grow(dv->yq, dv->yq_cap, P.yq_elems) ||
+        (P.refine && !grow(dv->shortlist, dv->sl_cap, P.sl_elems))) {
         set_error("cudaMalloc failed for search scratch");
         return LC_ERR_OOM;
     }
@@ -1461,7 +1574,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     std::vector<int> off, len;
     splits(dv->d, dv->M1, off, len);
     for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
-    const size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log, wa.beam).total;
+    const size_t per_warp = walk_smem(dv->M1, dv->d, wa.efcap, wa.hash_log, wa.beam, true).total;
     const int variant = (dv->M1 == 16 && dv->d == 96) ? 1 : (dv->M1 == 32 && dv->d == 96) ? 2
                       : (dv->M1 == 64 && dv->d == 128) ? 3 : 0;
     int grid = 0, wpc = 1;
@@ -1641,7 +1754,7 @@ lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, 
               alloc(pl->ids, (size_t)nq_max * k * 4) && alloc(pl->dists, (size_t)nq_max * k * 4) &&
               alloc(pl->stats, (size_t)nq_max * 12) && alloc(pl->sc.spill, P.spill_elems * 4) &&
               alloc(pl->sc.status, 4) && alloc(pl->sc.counter, 8) &&
-              (!P.refine || (alloc(pl->sc.yq, P.yq_elems * 4) && alloc(pl->sc.shortlist, P.sl_elems * 4)));
+              alloc(pl->sc.yq, P.yq_elems * 4) && (!P.refine || alloc(pl->sc.shortlist, P.sl_elems * 4));
     if (!ok) {
         plan_free(pl);
         set_error("cudaMalloc failed for the plan's buffers");
