@@ -522,152 +522,170 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) g.y[k][u] = u < g.len[k] ? yrot[g.off[k] + u] : 0.f;
         }
         int my_slot;
-
-        // greedy descent of the upper levels (Section 2)
+        // One loop runs the greedy descent of the upper levels (Section 2) and then the level-0
+        // best-first search.  Each iteration gathers the nodes to score in slot[] and scores
+        // them at a single call site, so the kernel holds one copy of the scoring code.
         int32_t n_up = 0, n_dist = 0, n_expand = 0;
         int32_t cur = a.ep;
-        if (lane == 0) slot[0] = cur;
-        __syncwarp();
-        float dcur = score_nodes<M1, D1, CT>(C1s, stage, a.codes1, slot, 1, d, g, lane, &my_slot);
-        dcur = __shfl_sync(FULL, dcur, 0);                                    // lane 0 holds slot 0
-        if (a.max_level >= 1) n_up = 1;
-        for (int l = a.max_level; l >= 1; l--) {
-            for (;;) {
-                int32_t e = a.upper_adj[((int64_t)a.upper_off[cur] + l - 1) * DEG + lane];
-                unsigned vm = __ballot_sync(FULL, e >= 0);
-                int nv = __popc(vm);
-                if (nv == 0) break;
-                if (e >= 0) slot[__popc(vm & lt_mask)] = e;
-                __syncwarp();
-                n_up += nv;
-                float de = score_nodes<M1, D1, CT>(C1s, stage, a.codes1, slot, nv, d, g, lane, &my_slot);
-                uint64_t k = my_slot < nv ? make_key(de, slot[my_slot]) : ~0ull;
-                uint64_t best = warp_min64(k);
-                __syncwarp();
-                if (best < make_key(dcur, cur)) {
-                    cur = key_id(best);
-                    dcur = key_dist(best);
-                } else {
-                    break;
-                }
-            }
-        }
-
-        // level 0: best-first search with result list W (sorted keys + expanded flags)
+        float dcur = 0.f;
+        int lvl = a.max_level;             // upper level being descended
+        int phase = 0;                     // 0: entry point, 1: upper levels, 2: level 0
         int buf = 0, wn = 1;
         bool spilled = false, failed = false;
-        if (lane == 0) {
-            wkey[0] = make_key(dcur, cur);
-            wflag[0] = 0;
-            hash[hash32(cur) & (H - 1)] = cur;
-        }
-        n_dist = 1;
         int32_t hcount = 1, scount = 0;
-        __syncwarp();
         int scan_from = 0;
-        const int B = a.beam;                // expansions per step; 1 = the plain walk
+        const int B = a.beam;              // level-0 expansions per step; 1 = the plain walk
         for (;;) {
-            if (a.tcap > 0 && n_dist >= a.tcap) break;     // search-time cap T (Section 3.1)
             uint64_t *W = wkey + buf * a.efcap;
             uint8_t *F = wflag + buf * a.efcap;
-            // the B best unexpanded members of W: lane i < nb holds the i-th one's position
-            int nb = 0, my_pos = -1;
-            for (int b0 = scan_from; b0 < wn && nb < B; b0 += 32) {
-                const int p = b0 + lane;
-                unsigned m = __ballot_sync(FULL, p < wn && !F[p]);
-                while (m && nb < B) {
-                    if (lane == nb) my_pos = b0 + __ffs(m) - 1;
-                    nb++;
-                    m &= m - 1;
-                }
-            }
-            if (nb == 0) break;
-            const int pos0 = __shfl_sync(FULL, my_pos, 0);
-            const uint64_t ckey0 = W[pos0];
-            const int32_t my_c = lane < nb ? key_id(W[my_pos]) : -1;
-            __syncwarp();
-            if (lane < nb) F[my_pos] = 1;
-            n_expand += nb;
-            // their adjacency rows, all loads in flight together
-            for (int r = 0; r < nb; r++) {
-                const int32_t cr = __shfl_sync(FULL, my_c, r);
-                rowbuf[r * DEG + lane] = a.adj0[(int64_t)cr * DEG + lane];
-            }
-            __syncwarp();
-            // visited test row by row (row order, then slot order); fresh nodes are appended
-            int ns = 0;
-            if (!spilled && hcount + 32 * nb <= H / 2) {
-                // every row fits in the shared table without a switch to the spill table: the
-                // first probes of up to 4 rows are issued together, then each row is resolved
-                // in row order (a node in two rows probes the same bucket first, so it is
-                // fresh in the earlier row)
-                const uint32_t Hm = (uint32_t)H - 1;
-                for (int r0 = 0; r0 < nb; r0 += 4) {
-                    int32_t ev[4], ov[4];
-#pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        ev[u] = r0 + u < nb ? rowbuf[(r0 + u) * DEG + lane] : -1;
-                        ov[u] = ev[u] >= 0 ? atomicCAS(hash + (hash32(ev[u]) & Hm), -1, ev[u]) : 0;
+            int ns = 0, pos0 = 0;
+            uint64_t ckey0 = 0;
+            if (phase == 0) {
+                if (lane == 0) slot[0] = cur;
+                ns = 1;
+            } else if (phase == 1) {
+                // the current node's row at this level
+                const int32_t e = a.upper_adj[((int64_t)a.upper_off[cur] + lvl - 1) * DEG + lane];
+                const unsigned vm = __ballot_sync(FULL, e >= 0);
+                ns = __popc(vm);
+                if (e >= 0) slot[__popc(vm & lt_mask)] = e;
+                n_up += ns;
+            } else {
+                if (a.tcap > 0 && n_dist >= a.tcap) break;     // search-time cap T (Section 3.1)
+                // the B best unexpanded members of W: lane i < nb holds the i-th one's position
+                int nb = 0, my_pos = -1;
+                for (int b0 = scan_from; b0 < wn && nb < B; b0 += 32) {
+                    const int p = b0 + lane;
+                    unsigned m = __ballot_sync(FULL, p < wn && !F[p]);
+                    while (m && nb < B) {
+                        if (lane == nb) my_pos = b0 + __ffs(m) - 1;
+                        nb++;
+                        m &= m - 1;
                     }
+                }
+                if (nb == 0) break;
+                pos0 = __shfl_sync(FULL, my_pos, 0);
+                ckey0 = W[pos0];
+                const int32_t my_c = lane < nb ? key_id(W[my_pos]) : -1;
+                __syncwarp();
+                if (lane < nb) F[my_pos] = 1;
+                n_expand += nb;
+                // their adjacency rows, all loads in flight together
+                for (int r = 0; r < nb; r++) {
+                    const int32_t cr = __shfl_sync(FULL, my_c, r);
+                    rowbuf[r * DEG + lane] = a.adj0[(int64_t)cr * DEG + lane];
+                }
+                __syncwarp();
+                // visited test row by row (row order, then slot order); fresh nodes are appended
+                if (!spilled && hcount + 32 * nb <= H / 2) {
+                    // every row fits in the shared table without a switch to the spill table: the
+                    // first probes of up to 4 rows are issued together, then each row is resolved
+                    // in row order (a node in two rows probes the same bucket first, so it is
+                    // fresh in the earlier row)
+                    const uint32_t Hm = (uint32_t)H - 1;
+                    for (int r0 = 0; r0 < nb; r0 += 4) {
+                        int32_t ev[4], ov[4];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        if (r0 + u >= nb) break;
-                        const int32_t e = ev[u];
-                        bool fresh = e >= 0 && ov[u] == -1;
-                        if (e >= 0 && ov[u] != -1 && ov[u] != e) {
-                            // collision: continue the linear probe
-                            uint32_t h = hash32(e) & Hm;
-                            for (uint32_t p = 1; p <= Hm; p++) {
-                                h = (h + 1) & Hm;
-                                const int32_t old = atomicCAS(hash + h, -1, e);
-                                if (old == -1) { fresh = true; break; }
-                                if (old == e) break;
-                            }
+                        for (int u = 0; u < 4; u++) {
+                            ev[u] = r0 + u < nb ? rowbuf[(r0 + u) * DEG + lane] : -1;
+                            ov[u] = ev[u] >= 0 ? atomicCAS(hash + (hash32(ev[u]) & Hm), -1, ev[u]) : 0;
                         }
-                        const unsigned fm = __ballot_sync(FULL, fresh);
-                        if (fresh) slot[ns + __popc(fm & lt_mask)] = e;
-                        const int nf = __popc(fm);
-                        ns += nf;
-                        n_dist += nf;
-                        hcount += nf;
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            if (r0 + u >= nb) break;
+                            const int32_t e = ev[u];
+                            bool fresh = e >= 0 && ov[u] == -1;
+                            if (e >= 0 && ov[u] != -1 && ov[u] != e) {
+                                // collision: continue the linear probe
+                                uint32_t h = hash32(e) & Hm;
+                                for (uint32_t p = 1; p <= Hm; p++) {
+                                    h = (h + 1) & Hm;
+                                    const int32_t old = atomicCAS(hash + h, -1, e);
+                                    if (old == -1) { fresh = true; break; }
+                                    if (old == e) break;
+                                }
+                            }
+                            const unsigned fm = __ballot_sync(FULL, fresh);
+                            if (fresh) slot[ns + __popc(fm & lt_mask)] = e;
+                            const int nf = __popc(fm);
+                            ns += nf;
+                            n_dist += nf;
+                            hcount += nf;
+                        }
                     }
+                } else for (int r = 0; r < nb; r++) {
+                    // switch to the global table before the shared one passes half full
+                    if (!spilled && hcount + 32 > H / 2) {
+                        spilled = true;
+                        for (int i = lane; i < (1 << a.spill_log); i += 32) spill[i] = -1;
+                        __syncwarp();
+                    }
+                    if (spilled && scount + 32 > (1 << a.spill_log) / 2) {
+                        failed = true;
+                        break;
+                    }
+                    const int32_t e = rowbuf[r * DEG + lane];
+                    const bool fresh = e >= 0 && visit(e, hash, a.hash_log, spilled, spill, a.spill_log);
+                    const unsigned fm = __ballot_sync(FULL, fresh);
+                    if (fresh) slot[ns + __popc(fm & lt_mask)] = e;
+                    const int nf = __popc(fm);
+                    ns += nf;
+                    n_dist += nf;
+                    if (spilled) scount += nf; else hcount += nf;
                 }
-            } else for (int r = 0; r < nb; r++) {
-                // switch to the global table before the shared one passes half full
-                if (!spilled && hcount + 32 > H / 2) {
-                    spilled = true;
-                    for (int i = lane; i < (1 << a.spill_log); i += 32) spill[i] = -1;
-                    __syncwarp();
-                }
-                if (spilled && scount + 32 > (1 << a.spill_log) / 2) {
-                    failed = true;
-                    break;
-                }
-                const int32_t e = rowbuf[r * DEG + lane];
-                const bool fresh = e >= 0 && visit(e, hash, a.hash_log, spilled, spill, a.spill_log);
-                const unsigned fm = __ballot_sync(FULL, fresh);
-                if (fresh) slot[ns + __popc(fm & lt_mask)] = e;
-                const int nf = __popc(fm);
-                ns += nf;
-                n_dist += nf;
-                if (spilled) scount += nf; else hcount += nf;
+                if (failed) break;
+                __syncwarp();
+                if (ns == 0) { scan_from = pos0; continue; }
             }
-            if (failed) break;
             __syncwarp();
-            if (ns == 0) { scan_from = pos0; continue; }
-            // score the fresh nodes 32 at a time; keep those that can enter W
-            const uint64_t wmax = wn == efp ? W[wn - 1] : ~0ull;
+            // score the gathered nodes 32 at a time: the upper levels keep the best, level 0
+            // keeps those that can enter W
+            const uint64_t wmax = (phase == 2 && wn == efp) ? W[wn - 1] : ~0ull;
+            uint64_t best = ~0ull;
             int nc = 0;
             for (int ch = 0; ch < ns; ch += 32) {
                 const int nf = min(32, ns - ch);
                 const float de = score_nodes<M1, D1, CT>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot);
                 uint64_t k = my_slot < nf ? make_key(de, slot[ch + my_slot]) : ~0ull;
-                if (k >= wmax) k = ~0ull;
-                const unsigned km = __ballot_sync(FULL, k != ~0ull);
-                if (k != ~0ull) cuns[nc + __popc(km & lt_mask)] = k;
-                nc += __popc(km);
+                if (phase < 2) {
+                    best = warp_min64(k);                   // at most 32 nodes here
+                } else {
+                    if (k >= wmax) k = ~0ull;
+                    const unsigned km = __ballot_sync(FULL, k != ~0ull);
+                    if (k != ~0ull) cuns[nc + __popc(km & lt_mask)] = k;
+                    nc += __popc(km);
+                }
             }
             __syncwarp();
+            if (phase < 2) {
+                bool enter0 = false;
+                if (phase == 0) {
+                    dcur = key_dist(best);
+                    if (lvl >= 1) {
+                        n_up = 1;                           // the entry point's evaluation
+                        phase = 1;
+                    } else {
+                        enter0 = true;
+                    }
+                } else if (ns > 0 && best < make_key(dcur, cur)) {
+                    cur = key_id(best);                     // greedy move at this level
+                    dcur = key_dist(best);
+                } else if (--lvl == 0) {
+                    enter0 = true;
+                }
+                if (enter0) {
+                    // level 0: best-first search with result list W (sorted keys + expanded flags)
+                    phase = 2;
+                    if (lane == 0) {
+                        wkey[0] = make_key(dcur, cur);
+                        wflag[0] = 0;
+                        hash[hash32(cur) & (H - 1)] = cur;
+                    }
+                    n_dist = 1;
+                    __syncwarp();
+                }
+                continue;
+            }
             if (nc == 0) { scan_from = pos0; continue; }
             // order the candidates by rank (keys are distinct)
             for (int m0 = lane; m0 < nc; m0 += 32) {
