@@ -781,14 +781,16 @@ struct RefineArgs {
 // u = 0..d-1 of R[t][u] y[u] (fmaf chain), the arithmetic of the walk's own rotation, so the
 // walk gives bit-identical results either way.  R^T sits in shared memory when it fits
 // (d <= 200); uint8 queries convert exactly to FP32.
-constexpr int ROT_Q = 8;            // queries per block step
-constexpr int ROT_THREADS = 256;
+constexpr int ROT_Q = 16;           // queries per block step (independent FMA chains per thread)
+constexpr int ROT_THREADS = 128;
 __host__ __device__ inline bool rotate_rt_shared(int d) { return (size_t)d * d * 4 <= 160 * 1024; }
 __host__ __device__ inline size_t rotate_smem(int d)
 {
     return ((rotate_rt_shared(d) ? (size_t)d * d : 0) + (size_t)ROT_Q * d) * 4;
 }
 
+// A thread owns output coordinate t of ROT_Q queries at a time: ROT_Q independent chains,
+// with the queries' values read four at a time from ys [d][ROT_Q] (broadcast).
 __global__ void __launch_bounds__(ROT_THREADS) rotate_kernel(const float *Q, const uint8_t *Q8, int64_t nq, int d,
                                                              const float *Rt, float *yq)
 {
@@ -803,15 +805,30 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_kernel(const float *Q, con
     for (int64_t q0 = (int64_t)blockIdx.x * ROT_Q; q0 < nq; q0 += (int64_t)gridDim.x * ROT_Q) {
         const int nb = nq - q0 < ROT_Q ? (int)(nq - q0) : ROT_Q;
         __syncthreads();                               // Rt loaded / previous step's ys consumed
-        for (int i = threadIdx.x; i < nb * d; i += blockDim.x)
-            ys[i] = Q8 ? (float)__ldg(Q8 + q0 * d + i) : __ldg(Q + q0 * d + i);
+        for (int i = threadIdx.x; i < ROT_Q * d; i += blockDim.x) {
+            const int qq = i / d, u = i - qq * d;
+            ys[u * ROT_Q + qq] = qq >= nb ? 0.f : Q8 ? (float)__ldg(Q8 + (q0 + qq) * d + u) : __ldg(Q + (q0 + qq) * d + u);
+        }
         __syncthreads();
-        for (int i = threadIdx.x; i < nb * d; i += blockDim.x) {
-            const int qq = i / d, t = i - qq * d;
-            const float *y = ys + qq * d;
-            float s = 0.f;
-            for (int u = 0; u < d; u++) s = fmaf(R[u * d + t], y[u], s);
-            yq[(q0 + qq) * d + t] = s;
+        for (int t = threadIdx.x; t < d; t += blockDim.x) {
+            float acc[ROT_Q];
+#pragma unroll
+            for (int qq = 0; qq < ROT_Q; qq++) acc[qq] = 0.f;
+            for (int u = 0; u < d; u++) {
+                const float r = R[u * d + t];
+                const float4 *y4 = reinterpret_cast<const float4 *>(ys + u * ROT_Q);
+#pragma unroll
+                for (int v = 0; v < ROT_Q / 4; v++) {
+                    const float4 y = y4[v];
+                    acc[4 * v + 0] = fmaf(r, y.x, acc[4 * v + 0]);
+                    acc[4 * v + 1] = fmaf(r, y.y, acc[4 * v + 1]);
+                    acc[4 * v + 2] = fmaf(r, y.z, acc[4 * v + 2]);
+                    acc[4 * v + 3] = fmaf(r, y.w, acc[4 * v + 3]);
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < ROT_Q; qq++)
+                if (qq < nb) yq[(q0 + qq) * d + t] = acc[qq];
         }
     }
 }
@@ -1266,14 +1283,15 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rotate_kernel, ROT_THREADS, rsm);
         P.qsm = rsm;
-        P.qgrid = (int)std::min<int64_t>((nq + ROT_Q - 1) / ROT_Q, (int64_t)std::max(per_sm, 1) * dv->num_sms);
+        // a few blocks per SM: each loads R^T once and rotates many queries
+        P.qgrid = (int)std::min<int64_t>((nq + ROT_Q - 1) / ROT_Q, (int64_t)std::min(std::max(per_sm, 1), 2) * dv->num_sms);
     }
     if (P.refine) {
         P.sl_elems = (size_t)nq * P.R;
         const size_t per = refine_smem(dv->M1, dv->M2P, P.R, dv->bM);
         const size_t cbytes = (size_t)256 * dv->d * 4;
-        // both codebooks in shared memory when that leaves room for at least 4 warps
-        P.rboth = 2 * cbytes + 4 * per <= MAX_SMEM_PER_BLOCK;
+        // both codebooks in shared memory when that leaves room for at least 8 warps
+        P.rboth = 2 * cbytes + 8 * per <= MAX_SMEM_PER_BLOCK;
         const size_t cb = (P.rboth ? 2 : 1) * cbytes;
         if (cb + per > MAX_SMEM_PER_BLOCK) {
             set_error("refinement does not fit in shared memory (d = %d)", dv->d);
