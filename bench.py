@@ -570,7 +570,9 @@ def main():
     achieved = b_walk / walk_s / 1e9
     # DRAM traffic from the committed ncu summary of the same kernel build and form, if any
     bsp = best_form[0]
-    form_key = None if (bsp.warps or bsp.visited_log or (bsp.mode and bsp.beam != args.beam)) else (
+    efp_b = max(bsp.ef, bsp.k)
+    auto_vlog = min(12, max(10, int(np.ceil(np.log2(32 * efp_b)))))      # the library's automatic table size
+    form_key = None if (bsp.warps or bsp.visited_log not in (0, auto_vlog) or (bsp.mode and bsp.beam != args.beam)) else (
         ("batched" if bsp.mode else "plain") + ("_fp16" if bsp.lut_prec else "") + f"_ef{bsp.ef}")
     traffic = profiled_traffic(args.workload, form_key) if form_key else None
 

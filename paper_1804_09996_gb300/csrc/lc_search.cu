@@ -799,12 +799,18 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_kernel(const float *Q, con
     float *ys = rsm + (shared_rt ? d * d : 0);
     const float *R = Rt;
     if (shared_rt) {
-        for (int i = threadIdx.x; i < d * d; i += blockDim.x) rsm[i] = __ldg(Rt + i);
+        // 16-byte loads, several in flight per thread (R^T is cudaMalloc-aligned)
+        const int n4 = d * d / 4;
+#pragma unroll 6
+        for (int i = threadIdx.x; i < n4; i += blockDim.x)
+            reinterpret_cast<float4 *>(rsm)[i] = __ldg(reinterpret_cast<const float4 *>(Rt) + i);
+        for (int i = 4 * n4 + threadIdx.x; i < d * d; i += blockDim.x) rsm[i] = __ldg(Rt + i);
         R = rsm;
     }
     for (int64_t q0 = (int64_t)blockIdx.x * ROT_Q; q0 < nq; q0 += (int64_t)gridDim.x * ROT_Q) {
         const int nb = nq - q0 < ROT_Q ? (int)(nq - q0) : ROT_Q;
         __syncthreads();                               // Rt loaded / previous step's ys consumed
+#pragma unroll 4
         for (int i = threadIdx.x; i < ROT_Q * d; i += blockDim.x) {
             const int qq = i / d, u = i - qq * d;
             ys[u * ROT_Q + qq] = qq >= nb ? 0.f : Q8 ? (float)__ldg(Q8 + (q0 + qq) * d + u) : __ldg(Q + (q0 + qq) * d + u);
@@ -814,6 +820,7 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_kernel(const float *Q, con
             float acc[ROT_Q];
 #pragma unroll
             for (int qq = 0; qq < ROT_Q; qq++) acc[qq] = 0.f;
+#pragma unroll 4
             for (int u = 0; u < d; u++) {
                 const float r = R[u * d + t];
                 const float4 *y4 = reinterpret_cast<const float4 *>(ys + u * ROT_Q);
@@ -1283,8 +1290,8 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rotate_kernel, ROT_THREADS, rsm);
         P.qsm = rsm;
-        // a few blocks per SM: each loads R^T once and rotates many queries
-        P.qgrid = (int)std::min<int64_t>((nq + ROT_Q - 1) / ROT_Q, (int64_t)std::min(std::max(per_sm, 1), 2) * dv->num_sms);
+        // as many blocks as fit at once: the batch is rotated in about one step per block
+        P.qgrid = (int)std::min<int64_t>((nq + ROT_Q - 1) / ROT_Q, (int64_t)std::max(per_sm, 1) * dv->num_sms);
     }
     if (P.refine) {
         P.sl_elems = (size_t)nq * P.R;
