@@ -14,7 +14,9 @@
  *   orc_search      Section 4.1 (two-stage search) over the HNSW structure of Section 2
  *                   (beam >= 2: the batched form, several expansions per step; tcap > 0:
  *                   stop after T level-0 distance computations, Section 3.1; C1w: the
- *                   codebook the walk's ADC terms use, NULL = C1):
+ *                   codebook the walk's ADC terms use, NULL = C1; walk_full: the walk scores
+ *                   the full two-level decode q(x) = c1 + c2 instead of the level-1 code,
+ *                   with C2w standing for C2 as C1w for C1):
  *                   rotation, ADC tables, greedy descent of the upper levels, best-first
  *                   search of level 0, shortlist, refinement with the regression codebook
  *                   (Section 4.3, reconstruction beta^T G(x)), exact L2 and top-k.
@@ -61,6 +63,8 @@ typedef struct {
     double gap;                 /* smallest relative gap seen so far */
     const uint8_t *codes1;      /* to recognise exact ties between identical code rows */
     int M1;
+    const uint8_t *codes2;      /* non-NULL when the walk scores the full decode */
+    int M2;
 } gap_rec;
 
 static void note_gap(gap_rec *g, double a, int32_t ia, double b, int32_t ib, int walk)
@@ -70,7 +74,9 @@ static void note_gap(gap_rec *g, double a, int32_t ia, double b, int32_t ib, int
         /* Identical code rows give identical sums on any hardware; that tie is decided
            by id on both sides.  Any other exact tie is treated as unresolved. */
         if (walk && memcmp(g->codes1 + (int64_t)ia * g->M1, g->codes1 + (int64_t)ib * g->M1,
-                           (size_t)g->M1) == 0)
+                           (size_t)g->M1) == 0 &&
+            (!g->codes2 || memcmp(g->codes2 + (int64_t)ia * g->M2, g->codes2 + (int64_t)ib * g->M2,
+                                  (size_t)g->M2) == 0))
             return;
         g->gap = 0.0;
         return;
@@ -109,6 +115,35 @@ static double adc(const orc_index *ix, const double *lut, int32_t e)
     return s;
 }
 
+/* What the walk scores a node by.  Level-1 walk (the default reading): the ADC sum above.
+   Full walk: the squared distance to the node's full decode q(x) = c1(x) + c2(x), each
+   coordinate t taking the level-1 centroid of its level-1 sub-space and the level-2 centroid
+   of its level-2 sub-space (Section 4.1 describes the graph as searched with the codec's
+   approximation; this is that approximation taken in full). */
+typedef struct {
+    const orc_index *ix;
+    const double *lut;          /* ADC tables (level-1 walk) */
+    int full;
+    const double *yr;           /* rotated query (full walk) */
+    const float *C1w, *C2w;     /* codebooks the full walk decodes with */
+    const int *sub1, *sub2;     /* sub-space of each coordinate at level 1 and level 2 */
+} walk_ctx;
+
+static double wdist(const walk_ctx *w, int32_t e)
+{
+    if (!w->full) return adc(w->ix, w->lut, e);
+    const orc_index *ix = w->ix;
+    const uint8_t *a = ix->codes1 + (int64_t)e * ix->M1;
+    const uint8_t *b = ix->codes2 + (int64_t)e * ix->M2;
+    double s = 0.0;
+    for (int t = 0; t < ix->d; t++) {
+        double x = (double)w->C1w[(int64_t)a[w->sub1[t]] * ix->d + t] + (double)w->C2w[(int64_t)b[w->sub2[t]] * ix->d + t];
+        double diff = w->yr[t] - x;
+        s += diff * diff;
+    }
+    return s;
+}
+
 /* Decoded vector q(x) = c1(x) + c2(x - c1(x)) of the two-level codec (Section 3.3 / 4.1),
    in the rotated space. */
 static void decode2(const orc_index *ix, const int *off1, const int *len1, const int *off2,
@@ -128,7 +163,7 @@ static void decode2(const orc_index *ix, const int *off1, const int *len1, const
    W together, scores all their unvisited neighbours (a node shared by two rows is scored and
    counted once), and keeps the ef' best of W and the new nodes.  With beam = 1 this expands
    the same nodes in the same order as the best-first search of orc_search. */
-static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, int efp, int beam,
+static int walk_batched(const orc_index *ix, const walk_ctx *wc, int32_t seed, int efp, int beam,
                         int tcap, char *visited, int32_t *touched, int *ntouch, double *wd,
                         int32_t *wi, int32_t *n_dist, int32_t *n_expand, gap_rec *g)
 {
@@ -139,7 +174,7 @@ static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, in
     char *wf = calloc((size_t)efp + 1, 1);
     int32_t *U = malloc(sizeof(int32_t) * (beam > 0 ? beam : 1));
     int wn = 1;
-    wd[0] = adc(ix, lut, seed);
+    wd[0] = wdist(wc, seed);
     wi[0] = seed;
     visited[seed] = 1;
     touched[(*ntouch)++] = seed;
@@ -171,7 +206,7 @@ static int walk_batched(const orc_index *ix, const double *lut, int32_t seed, in
                 visited[e] = 1;
                 touched[(*ntouch)++] = e;
                 (*n_dist)++;
-                ad[an] = adc(ix, lut, e); ai[an] = e; af[an] = 0; an++;
+                ad[an] = wdist(wc, e); ai[an] = e; af[an] = 0; an++;
             }
         }
         /* order W and the new nodes by key (insertion sort) and keep the ef' best */
@@ -201,7 +236,8 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                const uint8_t *beta, const float *B, int bM, int bK, int deg, const int32_t *adj0, int deg_up,
                const int32_t *upper_off, const int32_t *upper_adj, int32_t ep, int max_level,
                int64_t nq, const float *Q, int k, int ef, int shortlist, int beam, int tcap,
-               const float *C1w, int32_t *ids, double *dists, int32_t *stats, double *min_gap,
+               const float *C1w, int walk_full, const float *C2w, int32_t *ids, double *dists,
+               int32_t *stats, double *min_gap,
                int32_t *w_ids, double *w_dists, int32_t *w_size)
 {
     orc_index ix = {N, d, M1, M2, deg, deg_up, max_level, ep, R, C1, C2, B, bM, bK,
@@ -210,11 +246,15 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
     /* the walk's codebook: C1 itself, or a variant of it (e.g. rounded to FP16); the
        refinement always decodes with C1 */
     if (!C1w) C1w = C1;
+    if (!C2w) C2w = C2;
     int off1[256], len1[256], off2[256], len2[256], offb[256], lenb[256];
     if (M1 > 256 || M2 > 256 || bM < 1 || bM > 256 || bM > d || bK < 1 || bK > 256 || k < 1) return -1;
     split_offsets(d, M1, off1, len1);
     split_offsets(d, M2, off2, len2);
     split_offsets(d, bM, offb, lenb);       /* regression blocks (Section 4.3, product codebook) */
+    int *sub1 = malloc(sizeof(int) * d), *sub2 = malloc(sizeof(int) * d);
+    for (int j = 0; j < M1; j++) for (int t = off1[j]; t < off1[j] + len1[j]; t++) sub1[t] = j;
+    for (int j = 0; j < M2; j++) for (int t = off2[j]; t < off2[j] + len2[j]; t++) sub2[t] = j;
 
     double *yr = malloc(sizeof(double) * d);
     double *lut = malloc(sizeof(double) * 256 * M1);
@@ -232,7 +272,8 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
 
     for (int64_t q = 0; q < nq; q++) {
         const float *y = Q + q * d;
-        gap_rec g = {INFINITY, codes1, M1};
+        gap_rec g = {INFINITY, codes1, M1, walk_full ? codes2 : NULL, M2};
+        walk_ctx wc = {&ix, lut, walk_full, yr, C1w, C2w, sub1, sub2};
         int32_t n_dist = 0, n_expand = 0, n_up = 0;
         int wn = 0, ntouch = 0;
 
@@ -243,7 +284,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
             yr[t] = s;
         }
         /* ADC tables LUT[j][c] = || y'^j - C1_j[c] ||^2, in difference form. */
-        for (int j = 0; j < M1; j++)
+        for (int j = 0; j < M1 && !walk_full; j++)
             for (int c = 0; c < 256; c++) {
                 double s = 0.0;
                 for (int t = off1[j]; t < off1[j] + len1[j]; t++) {
@@ -256,7 +297,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
         if (N > 0) {
             /* Greedy descent through levels max_level..1 (Section 2). */
             int32_t cur = ep;
-            double dcur = adc(&ix, lut, cur);
+            double dcur = wdist(&wc, cur);
             if (max_level >= 1) n_up++;
             for (int l = max_level; l >= 1; l--) {
                 for (;;) {
@@ -266,7 +307,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                     for (int s = 0; s < deg_up; s++) {
                         int32_t e = row[s];
                         if (e < 0) continue;
-                        double de = adc(&ix, lut, e);
+                        double de = wdist(&wc, e);
                         n_up++;
                         if (best < 0 || key_less(de, e, dbest, best)) {
                             second = best; dsecond = dbest;
@@ -288,12 +329,12 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
             }
 
             if (beam >= 2) {
-                wn = walk_batched(&ix, lut, cur, efp, beam, tcap, visited, touched, &ntouch, wd, wi,
+                wn = walk_batched(&ix, &wc, cur, efp, beam, tcap, visited, touched, &ntouch, wd, wi,
                                   &n_dist, &n_expand, &g);
             } else {
                 /* Best-first search of level 0 from the seed, result set of size ef'. */
                 int64_t cn = 0;
-                double d0 = adc(&ix, lut, cur);
+                double d0 = wdist(&wc, cur);
                 n_dist = 1;
                 visited[cur] = 1;
                 touched[ntouch++] = cur;
@@ -338,7 +379,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                         if (e < 0 || visited[e]) continue;
                         visited[e] = 1;
                         touched[ntouch++] = e;
-                        double de = adc(&ix, lut, e);
+                        double de = wdist(&wc, e);
                         n_dist++;
                         bf = 0;
                         for (int u = 1; u < wn; u++)
@@ -458,7 +499,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
         }
         if (min_gap) min_gap[q] = g.gap;
     }
-    free(yr); free(lut); free(visited); free(touched); free(cd); free(ci);
+    free(yr); free(lut); free(sub1); free(sub2); free(visited); free(touched); free(cd); free(ci);
     free(wd); free(wi); free(xh); free(yh); free(rd); free(ri);
     return 0;
 }

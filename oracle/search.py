@@ -17,14 +17,18 @@ from ._clib import lib, ptr
 
 
 def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: bool = False,
-           beam: int = 1, tcap: int = 0, c1_walk: np.ndarray | None = None):
+           beam: int = 1, tcap: int = 0, c1_walk: np.ndarray | None = None, walk_full: bool = False,
+           c2_walk: np.ndarray | None = None):
     """Returns dict(ids [nq][k] int32, dists [nq][k] float64, stats [nq][3] int32 =
     (n_dist, n_expand, n_dist_upper), gap [nq] = smallest relative gap of a deciding
     comparison, and with ``return_w`` the final result set W sorted by (dist, id)).  ``beam``
     >= 2 selects the batched form of the level-0 search (that many expansions per step);
     ``tcap`` > 0 stops the level-0 search once that many distances were computed (Section 3.1's
     search-time parameter T, checked before each expansion).  ``c1_walk`` replaces the level-1
-    codebook in the walk's ADC terms only (e.g. C1 rounded to FP16); the re-rank uses ix.C1."""
+    codebook in the walk's ADC terms only (e.g. C1 rounded to FP16); the re-rank uses ix.C1.
+    ``walk_full`` makes the walk score the full two-level decode q = c1 + c2 (Section 4.1's
+    approximation taken in full) instead of the level-1 code; ``c2_walk`` then replaces C2 in
+    the walk as ``c1_walk`` replaces C1."""
     Q = np.ascontiguousarray(Q, np.float32)
     nq = Q.shape[0]
     efp = max(ef, k)
@@ -43,7 +47,9 @@ def search(ix, Q: np.ndarray, k: int, ef: int, shortlist: int = 0, return_w: boo
         ix.upper_adj.shape[1], ptr(ix.upper_off),
         ptr(ix.upper_adj) if ix.upper_adj.shape[0] > 0 else None, ix.ep, ix.max_level,
         nq, ptr(Q), k, ef, shortlist, beam, tcap,
-        ptr(np.ascontiguousarray(c1_walk, np.float32)) if c1_walk is not None else None, ptr(ids), ptr(dists), ptr(stats), ptr(gap),
+        ptr(np.ascontiguousarray(c1_walk, np.float32)) if c1_walk is not None else None, int(walk_full),
+        ptr(np.ascontiguousarray(c2_walk, np.float32)) if c2_walk is not None else None,
+        ptr(ids), ptr(dists), ptr(stats), ptr(gap),
         ptr(w_ids), ptr(w_d), ptr(w_n))
     if rc != 0:
         raise RuntimeError(f"orc_search failed ({rc})")

@@ -404,3 +404,70 @@ def test_exhaustive_rerank_product_codebook(opq3k, bM, bK):
         order = np.lexsort((np.arange(N), d))[:k]
         np.testing.assert_allclose(r["dists"][q], d[order], rtol=1e-11)
         assert np.array_equal(r["ids"][q], order)
+
+
+# ---- walk on the full two-level decode q = c1 + c2 (Section 4.1, the approximation taken in full) ----
+
+def test_exhaustive_full_walk_is_bruteforce_on_full_decode(opq3k):
+    # ef' >= N: W is the brute-force order of || y' - (c1 + c2) ||^2 over every node, the two
+    # levels decoded here with their own (uneven) sub-space splits
+    ix, xb, xq = opq3k
+    N = ix.N
+    r = oracle.search(ix, xq[:5], k=N, ef=N, shortlist=-1, walk_full=True)
+    q = codec.pq_decode(ix.codes1, ix.C1.astype(np.float64), ix.M1) + \
+        codec.pq_decode(ix.codes2, ix.C2.astype(np.float64), ix.M2)
+    yr = xq[:5].astype(np.float64) @ ix.R.astype(np.float64).T
+    assert len(reachable(ix.adj0, 0)) == N
+    for i in range(5):
+        d = ((yr[i][None] - q) ** 2).sum(1)
+        order = np.lexsort((np.arange(N), d))
+        assert r["stats"][i, 0] == N
+        np.testing.assert_allclose(r["dists"][i], d[order], rtol=1e-12, atol=1e-15)
+        gaps = np.diff(d[order]) / d[order][1:]
+        ok = np.concatenate([[True], gaps > 1e-12]) & np.concatenate([gaps > 1e-12, [True]])
+        assert np.array_equal(r["ids"][i][ok], order[ok])
+
+
+@pytest.mark.parametrize("beam", [1, 4])
+def test_full_walk_with_zero_residual_codebook_is_the_level1_walk(mix3k, beam):
+    # with C2 = 0 the full decode is c1 itself: the full walk must expand the same nodes
+    ix, xb, xq = mix3k
+    import dataclasses
+    ix0 = dataclasses.replace(ix, C2=np.zeros_like(ix.C2))
+    a = oracle.search(ix0, xq[:60], 10, 48, shortlist=-1, beam=beam)
+    b = oracle.search(ix0, xq[:60], 10, 48, shortlist=-1, beam=beam, walk_full=True)
+    assert np.array_equal(a["stats"], b["stats"])
+    assert np.array_equal(a["ids"], b["ids"])
+    np.testing.assert_allclose(a["dists"], b["dists"], rtol=1e-12)
+
+
+def test_full_walk_hand_case():
+    # 3 nodes on a path 0 - 1 - 2, d = 2, one sub-space per level.  Level-1 codes put node 1
+    # and node 2 at the same centroid (0, 0); the residual level moves node 2 to (1, 0) and
+    # node 1 to (3, 0).  Query (1, 0): the level-1 walk sees nodes 1 and 2 tie at 1 (decided
+    # by id), the full walk ranks node 2 (distance 0) before node 1 (distance 4).
+    d, N = 2, 3
+    C1 = np.zeros((256, d), np.float32)
+    C1[1] = (5.0, 5.0)
+    C2 = np.zeros((256, d), np.float32)
+    C2[1] = (3.0, 0.0)
+    C2[2] = (1.0, 0.0)
+    codes1 = np.array([[1], [0], [0]], np.uint8)
+    codes2 = np.array([[0], [1], [2]], np.uint8)
+    adj0 = np.full((N, 32), -1, np.int32)
+    adj0[0, 0] = 1
+    adj0[1, :2] = (0, 2)
+    adj0[2, 0] = 1
+    B = np.tile(refine.e0().astype(np.float32), (256, 1))
+    ix = OracleIndex(d=d, M1=1, M2=1, R=np.eye(d, dtype=np.float32), C1=C1, C2=C2, codes1=codes1,
+                     codes2=codes2, beta=np.zeros(N, np.uint8), B=B, adj0=adj0,
+                     upper_off=np.full(N, -1, np.int32), upper_adj=np.zeros((0, 32), np.int32), ep=0,
+                     max_level=0, levels=np.zeros(N, np.int32))
+    q = np.array([[1.0, 0.0]], np.float32)
+    lvl1 = oracle.search(ix, q, k=3, ef=3, shortlist=-1)
+    full = oracle.search(ix, q, k=3, ef=3, shortlist=-1, walk_full=True)
+    assert lvl1["ids"][0].tolist() == [1, 2, 0]
+    np.testing.assert_allclose(lvl1["dists"][0], [1.0, 1.0, 41.0])
+    assert full["ids"][0].tolist() == [2, 1, 0]
+    np.testing.assert_allclose(full["dists"][0], [0.0, 4.0, 41.0])
+    assert full["stats"][0].tolist() == [3, 3, 0]
