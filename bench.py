@@ -419,6 +419,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="target duration of each open-loop point")
     ap.add_argument("--visited-log", type=int, default=0,
                     help="visited table size 2^v of the single form run by --mode plain / batched (0: automatic)")
+    ap.add_argument("--walk-full", type=int, default=0, help="single form: 1 = walk on the full two-level decode")
     ap.add_argument("--lut", default="fp32", choices=["fp32", "fp16"],
                     help="level-1 codebook precision of the single form run by --mode plain / batched")
     ap.add_argument("--mode", default="both", choices=["both", "plain", "batched"],
@@ -455,13 +456,13 @@ def main():
     stream = torch.cuda.Stream()
     lc.lc_profile(h, True)
 
-    def params(level, mode, prec=lc.LC_LUT_FP32, vlog=0):
+    def params(level, mode, prec=lc.LC_LUT_FP32, vlog=0, full=0):
         """Search parameters at one sweep level: efSearch, or (uneven workloads) the factor
         every query's own efSearch is scaled by; returns (sp, host efq or None)."""
         efq = uneven_ef(w, nq, level)
         ef = int(efq.max()) if uneven else int(level)
         sp = lc.lc_default_search_params(k, ef, mode=mode, beam=args.beam if mode == lc.LC_MODE_BATCHED else 1,
-                                         lut_prec=prec, visited_log=vlog)
+                                         lut_prec=prec, visited_log=vlog, walk_full=full)
         return sp, efq
 
     def measure(form, steps):
@@ -502,13 +503,14 @@ def main():
     batched = None
     lut1 = lc.LC_LUT_FP16 if args.lut == "fp16" else lc.LC_LUT_FP32
     if args.mode == "batched":
-        f_b = params(base_level, lc.LC_MODE_BATCHED, lut1, args.visited_log)
+        f_b = params(base_level, lc.LC_MODE_BATCHED, lut1, args.visited_log, args.walk_full)
         batched = measure(f_b, args.steps)
         batched.update(ef=base_level, sweep=[])
         plain, target = None, batched["recall"]
         best, best_form, best_name = batched, f_b, f"batched(beam={args.beam}){', fp16 codebook' if lut1 else ''}"
     else:
-        f_p = params(base_level, lc.LC_MODE_PLAIN, *((lut1, args.visited_log) if args.mode == "plain" else ()))
+        f_p = params(base_level, lc.LC_MODE_PLAIN,
+                     *((lut1, args.visited_log, args.walk_full) if args.mode == "plain" else ()))
         plain = measure(f_p, args.steps)
         plain.update(ef=base_level)
         target = plain["recall"]
@@ -516,21 +518,23 @@ def main():
     forms = {}
     if args.mode == "both" and args.beam > 1:
         # the cheapest level at which each faster form reaches the plain form's recall
-        for name, prec in (("batched", lc.LC_LUT_FP32), ("batched_fp16", lc.LC_LUT_FP16)):
+        for name, prec, full in (("batched", lc.LC_LUT_FP32, 0), ("batched_fp16", lc.LC_LUT_FP16, 0),
+                                 ("batched_full_fp16", lc.LC_LUT_FP16, 1)):
             sweep = []
             for lv in levels:
-                r = measure(params(lv, lc.LC_MODE_BATCHED, prec), max(10, args.steps // 5))
+                r = measure(params(lv, lc.LC_MODE_BATCHED, prec, full=full), max(10, args.steps // 5))
                 sweep.append((lv, r["recall"], r["qps"]))
                 if r["recall"] >= target:
                     break
             lv = sweep[-1][0]
-            f_b = params(lv, lc.LC_MODE_BATCHED, prec)
+            f_b = params(lv, lc.LC_MODE_BATCHED, prec, full=full)
             r = measure(f_b, args.steps)
             r.update(ef=lv, sweep=sweep)
             forms[name] = r
             if r["recall"] >= target and r["qps"] > best["qps"]:
                 best, best_form = r, f_b
-                best_name = f"batched(beam={args.beam}){', fp16 codebook' if prec else ''}"
+                best_name = (f"batched(beam={args.beam}){', fp16 codebook' if prec else ''}"
+                             f"{', full-decode walk' if full else ''}")
         batched = forms.get("batched")
         if not uneven:
             # the library's autotuner on a disjoint sample with its exact neighbours
@@ -562,9 +566,10 @@ def main():
     # walk kernel: algorithmic bytes per launch, from its own counters
     st = best["stats"]
     M1 = w["M1"]
+    row = M1 + ((w["M2"] + 1 + 15) // 16 * 16 if best_form[0].walk_full else 0)   # code bytes per scored node
     R = max(10, k)
     qbytes = d * (1 if u8 else 4) + (4 if uneven else 0)
-    b_walk = int((st[:, 1] * 128 + (st[:, 0] + st[:, 2]) * M1).sum() + nq * (qbytes + 4 * d + 4 * R))
+    b_walk = int((st[:, 1] * 128 + (st[:, 0] + st[:, 2]) * row).sum() + nq * (qbytes + 4 * d + 4 * R))
     walk_s = best["walk_ms"] / 1e3
     peak, peak_src = peaks()
     achieved = b_walk / walk_s / 1e9
@@ -573,7 +578,8 @@ def main():
     efp_b = max(bsp.ef, bsp.k)
     auto_vlog = min(12, max(10, int(np.ceil(np.log2(32 * efp_b)))))      # the library's automatic table size
     form_key = None if (bsp.warps or bsp.visited_log not in (0, auto_vlog) or (bsp.mode and bsp.beam != args.beam)) else (
-        ("batched" if bsp.mode else "plain") + ("_fp16" if bsp.lut_prec else "") + f"_ef{bsp.ef}")
+        ("batched" if bsp.mode else "plain") + ("_full" if bsp.walk_full else "") + ("_fp16" if bsp.lut_prec else "")
+        + f"_ef{bsp.ef}")
     traffic = profiled_traffic(args.workload, form_key) if form_key else None
 
     # e2e through the same C ABI call with pinned host buffers
@@ -679,6 +685,10 @@ def main():
                    "tuned": None if "tuned" not in forms else summary(forms["tuned"], forms["tuned"]["ef"],
                                                                       {"autotune": forms["tuned"]["tune"]}),
                    "small_batches": small,
+                   "batched_full_fp16": None if "batched_full_fp16" not in forms else summary(
+                       forms["batched_full_fp16"], forms["batched_full_fp16"]["ef"],
+                       {"beam": args.beam, "sweep": forms["batched_full_fp16"]["sweep"],
+                        "walk": "full two-level decode q = c1 + c2, codebooks rounded to FP16"}),
                    "served": served,
                    "l2": "flushed before every step (256 MB read, outside the timed span)",
                    "index_build_s": round(build_s, 1), "parallelism": f"replicas x{ws}"},

@@ -106,6 +106,11 @@ typedef struct {
     int warps;       /* walk queries in flight per thread block: 0 = as many as fit in shared
                         memory (at most 16); 1..16 = at most that many.  Results do not depend
                         on it (a launch-shape knob for the autotuner) */
+    int walk_full;   /* 0: the walk scores the level-1 code by ADC (the default reading of
+                        Section 4.1); 1: it scores the full two-level decode q = c1 + c2 (each
+                        coordinate's level-1 plus level-2 centroid; reads M1 + M2P code bytes
+                        per node).  1 needs a uniform level-1 split (M1 = 16 or 32 at d = 96,
+                        M1 = 64 at d = 128); with LC_LUT_FP16 both codebooks are rounded */
 } lc_search_params;
 
 void lc_default_search_params(lc_search_params *p, int k, int ef);

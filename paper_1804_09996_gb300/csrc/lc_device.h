@@ -17,6 +17,7 @@ struct DeviceIndex {
     float *C1 = nullptr, *C2 = nullptr, *B = nullptr;
     float *C1w = nullptr;         // C1 in the walk's shared-memory layout (FP32)
     void *C1h = nullptr;          // the same rounded to FP16 (device __half), for the FP16 mode
+    void *C2h = nullptr;          // C2 rounded to FP16 [256][d] (full-decode walk in FP16)
     uint8_t *codes1 = nullptr, *codes2b = nullptr;   // codes2b: residual codes padded to M2P bytes, codeword id last
     int M2P = 0;
     int bM = 1, bK = 256;         // regression blocks and codewords per block (B: [bM][bK][9])
@@ -44,6 +45,7 @@ struct SearchPlan {
     int k = 0, efp = 0, R = 0, beam = 1, tcap = 0, hash_log = 0, spill_log = 0, variant = 0;
     bool refine = false;
     bool half = false;                   // FP16 level-1 codebook in the walk
+    bool full = false;                   // the walk scores the full two-level decode
     int wpc = 0, grid = 0;               // walk: warps per CTA, CTAs
     size_t per_warp = 0, smem = 0;
     int rw = 0, rgrid = 0;               // refine: warps per CTA, CTAs

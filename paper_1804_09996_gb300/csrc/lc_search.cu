@@ -49,7 +49,7 @@ void device_free(DeviceIndex *dv)
     int cur = -1;
     cudaGetDevice(&cur);
     if (dv->device >= 0) cudaSetDevice(dv->device);
-    cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B); cfree(dv->C1h); cfree(dv->C1w);
+    cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B); cfree(dv->C1h); cfree(dv->C1w); cfree(dv->C2h);
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
@@ -97,6 +97,12 @@ struct WalkArgs {
     int32_t *status;
     unsigned long long *counter;   // next query to take (reset to 0 before each launch)
     SplitTab s1;
+    // walk on the full two-level decode (kernels instantiated with FQ = true)
+    const float *C2;       // [256][d] FP32, read through the cache
+    const __half *C2h;     // [256][d] FP16, copied into shared memory
+    const uint8_t *codes2b;
+    int M2P;
+    uint8_t sub2[256];     // level-2 sub-space of each coordinate
 };
 
 constexpr int MAX_WALK_WARPS = 16;       // warps (queries in flight) per CTA
@@ -130,6 +136,12 @@ __host__ __device__ inline size_t walk_c1_bytes(int d, int M1, int D1, size_t es
     const size_t n = L == 1 ? (size_t)256 * M1 * walk_pad(D1) : (size_t)256 * d;
     return align_up(n * es, 128);
 }
+// shared memory before the per-warp regions: the walk's level-1 codebook and, for the full
+// walk in FP16, C2 [256][d] behind it
+__host__ __device__ inline size_t walk_cb_bytes(int d, int M1, int D1, size_t es, bool fq)
+{
+    return walk_c1_bytes(d, M1, D1, es) + (fq && es == 2 ? align_up((size_t)256 * d * 2, 128) : 0);
+}
 // compile-time sub-space width of the uniform splits 96/16, 96/32 and 128/64 (0: other)
 __host__ __device__ constexpr int walk_variant_d1(int variant) { return variant == 1 ? 6 : variant == 2 ? 3 : variant == 3 ? 2 : 0; }
 inline int walk_variant(int M1, int d)
@@ -143,12 +155,13 @@ __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
 // own_rot: the walk rotates the query itself (y' in shared memory); otherwise y' is read from
 // the rotation kernel's output.  The adjacency rows of a step are only read before the
 // candidates are collected, so they share the unsorted-candidate area.
-__host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log, int beam, bool own_rot)
+__host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log, int beam, bool own_rot,
+                                             int m2p = 0)
 {
     WalkSmem s;
     size_t o = 0;
     s.yq = o;        o += own_rot ? align_up((size_t)d * 4, 16) : 0;
-    s.stage = o;     o += (size_t)32 * M1;
+    s.stage = o;     o += (size_t)32 * (M1 + m2p);     // level-1 rows, then (full walk) residual rows
     s.wkey = o;      o += (size_t)2 * efcap * 8;
     s.wflag = o;     o += align_up((size_t)2 * efcap, 16);
     s.cand = o;      o += (size_t)32 * beam * 8;
@@ -232,6 +245,7 @@ struct LaneGeo {
     static constexpr int DMAX = D1 > 0 ? D1 : (M1 == 16 ? 16 : (M1 == 32 ? 8 : 4));   // d <= 256
     int off[NSUB], len[NSUB], j[NSUB];
     float y[NSUB][DMAX];
+    int m2[NSUB][DMAX];          // full walk: level-2 sub-space of each of the lane's coordinates
 };
 
 __device__ __forceinline__ void half2_to_f(uint32_t w, float &a, float &b)
@@ -336,13 +350,61 @@ __device__ __forceinline__ void pair_dist(const CT *C1s, int d, int c0, int c1, 
     unpack2(acc, s0, s1);
 }
 
+// C2 value for the full walk: FP32 codebooks are read through the cache, FP16 ones from
+// shared memory.
+__device__ __forceinline__ float c2_at(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float c2_at(const __half *p) { return __half2float(*p); }
+
+// Full walk: sum over this lane's coordinates t of (y'_t - (C1[c1][t] + C2[c2_m(t)][t]))^2,
+// where row2 is the node's staged residual row and m(t) the level-2 sub-space of t.
+template <int M1, int D1, typename CT>
+__device__ __forceinline__ float part_full(const CT *C1s, const CT *C2, int d, int c, const uint8_t *row2,
+                                           const LaneGeo<M1, D1> &g, int k)
+{
+    float x[LaneGeo<M1, D1>::DMAX];
+    load_row<M1, D1, CT>(C1s, d, c, g, k, x);
+    float s = 0.f;
+#pragma unroll
+    for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) {
+        if (D1 == 0 && u >= g.len[k]) continue;
+        const float v = x[u] + c2_at(C2 + (int)row2[g.m2[k][u]] * d + g.off[k] + u);
+        const float df = g.y[k][u] - v;
+        s = fmaf(df, df, s);
+    }
+    return s;
+}
+
 // Sub-space terms of S slots (S = 16 or 32) for this lane, summed by reduce_slots<S>.
-template <int M1, int D1, int S, typename CT>
+template <int M1, int D1, int S, typename CT, bool FQ>
 __device__ __forceinline__ float score_slots(const CT *C1s, const uint8_t *stage, int nf, int d,
-                                             const LaneGeo<M1, D1> &g, int lane)
+                                             const LaneGeo<M1, D1> &g, int lane, const CT *C2, int M2P)
 {
     float v[S];
-    if (M1 == 16) {
+    if constexpr (FQ) {
+        // full walk: one slot per step; the residual rows follow the 32 level-1 rows
+        const uint8_t *stage2 = stage + 32 * M1;
+        if (M1 == 16) {
+            const int h = lane >> 4, j = lane & 15;
+#pragma unroll
+            for (int i = 0; i < S / 2; i++) {
+                const int sl = 2 * i + h;
+                float t = 0.f;
+                if (2 * i < nf && sl < nf) t = part_full<M1, D1, CT>(C1s, C2, d, stage[sl * 16 + j], stage2 + sl * M2P, g, 0);
+                v[2 * i] = h ? 0.f : t;
+                v[2 * i + 1] = h ? t : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < S; i++) {
+                float t = 0.f;
+                if (i < nf) {
+                    t = part_full<M1, D1, CT>(C1s, C2, d, stage[i * M1 + lane], stage2 + i * M2P, g, 0);
+                    if (M1 == 64) t += part_full<M1, D1, CT>(C1s, C2, d, stage[i * M1 + 32 + lane], stage2 + i * M2P, g, 1);
+                }
+                v[i] = t;
+            }
+        }
+    } else if (M1 == 16) {
         const int h = lane >> 4, j = lane & 15;
 #pragma unroll
         for (int i = 0; i < S / 2; i++) {
@@ -388,24 +450,30 @@ __device__ __forceinline__ float score_slots(const CT *C1s, const uint8_t *stage
 // Walk distances of the nf nodes in slot[0..nf) (1 <= nf <= 32): their code rows are staged
 // in shared memory, each lane computes its sub-space terms, and the totals are formed with
 // 16 or 32 slots.  Returns lane's total; *my_slot = the slot it holds (>= 32: none).
-template <int M1, int D1, typename CT>
+template <int M1, int D1, typename CT, bool FQ>
 __device__ __forceinline__ float score_nodes(const CT *C1s, uint8_t *stage, const uint8_t *codes1,
                                              const int32_t *slot, int nf, int d,
-                                             const LaneGeo<M1, D1> &g, int lane, int *my_slot)
+                                             const LaneGeo<M1, D1> &g, int lane, int *my_slot,
+                                             const CT *C2, const uint8_t *codes2b, int M2P)
 {
     if (lane < nf) {
         const uint4 *src = reinterpret_cast<const uint4 *>(codes1 + (int64_t)slot[lane] * M1);
         uint4 *dst = reinterpret_cast<uint4 *>(stage + lane * M1);
 #pragma unroll
         for (int u = 0; u < M1 / 16; u++) dst[u] = __ldg(src + u);
+        if constexpr (FQ) {
+            const uint4 *s2 = reinterpret_cast<const uint4 *>(codes2b + (int64_t)slot[lane] * M2P);
+            uint4 *d2 = reinterpret_cast<uint4 *>(stage + 32 * M1 + lane * M2P);
+            for (int u = 0; u < M2P / 16; u++) d2[u] = __ldg(s2 + u);
+        }
     }
     __syncwarp();
     float r;
     if (nf <= 16) {
-        r = score_slots<M1, D1, 16, CT>(C1s, stage, nf, d, g, lane);
+        r = score_slots<M1, D1, 16, CT, FQ>(C1s, stage, nf, d, g, lane, C2, M2P);
         *my_slot = lane < 16 ? lane : 32;           // lanes l and l + 16 hold slot l
     } else {
-        r = score_slots<M1, D1, 32, CT>(C1s, stage, nf, d, g, lane);
+        r = score_slots<M1, D1, 32, CT, FQ>(C1s, stage, nf, d, g, lane, C2, M2P);
         *my_slot = slot_of_lane(lane, 5);
     }
     __syncwarp();
@@ -452,7 +520,7 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
     return false;       // unreachable: the spill table is kept at most half full
 }
 
-template <int M1, int D1, typename CT>
+template <int M1, int D1, typename CT, bool FQ>
 __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -466,9 +534,21 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         const int n16 = (int)(walk_c1_bytes(d, M1, D1, sizeof(CT)) / 16);
         for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
     }
+    // full walk: C2 in shared memory (FP16) or read through the cache (FP32)
+    const CT *C2 = nullptr;
+    if constexpr (FQ) {
+        if constexpr (sizeof(CT) == 2) {
+            CT *C2s = reinterpret_cast<CT *>(smem_raw + walk_c1_bytes(d, M1, D1, sizeof(CT)));
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.C2h);
+            for (int i = threadIdx.x; i < 256 * d * 2 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(C2s)[i] = __ldg(src + i);
+            C2 = C2s;
+        } else {
+            C2 = reinterpret_cast<const CT *>(a.C2);
+        }
+    }
     __syncthreads();
-    const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam, a.yq_in == nullptr);
-    unsigned char *base = smem_raw + walk_c1_bytes(d, M1, D1, sizeof(CT)) + (size_t)warp * L.total;
+    const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam, a.yq_in == nullptr, FQ ? a.M2P : 0);
+    unsigned char *base = smem_raw + walk_cb_bytes(d, M1, D1, sizeof(CT), FQ) + (size_t)warp * L.total;
     float *yq = reinterpret_cast<float *>(base + L.yq);
     uint8_t *stage = base + L.stage;
     uint64_t *wkey = reinterpret_cast<uint64_t *>(base + L.wkey);
@@ -519,7 +599,10 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             g.off[k] = a.s1.off[j];
             g.len[k] = a.s1.len[j];
 #pragma unroll
-            for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) g.y[k][u] = u < g.len[k] ? yrot[g.off[k] + u] : 0.f;
+            for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) {
+                g.y[k][u] = u < g.len[k] ? yrot[g.off[k] + u] : 0.f;
+                g.m2[k][u] = FQ && u < g.len[k] ? a.sub2[g.off[k] + u] : 0;
+            }
         }
         int my_slot;
         // One loop runs the greedy descent of the upper levels (Section 2) and then the level-0
@@ -645,7 +728,8 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             int nc = 0;
             for (int ch = 0; ch < ns; ch += 32) {
                 const int nf = min(32, ns - ch);
-                const float de = score_nodes<M1, D1, CT>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot);
+                const float de = score_nodes<M1, D1, CT, FQ>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot,
+                                                             C2, a.codes2b, a.M2P);
                 uint64_t k = my_slot < nf ? make_key(de, slot[ch + my_slot]) : ~0ull;
                 if (phase < 2) {
                     best = warp_min64(k);                   // at most 32 nodes here
@@ -794,7 +878,7 @@ __host__ __device__ inline size_t rotate_smem(int d)
 __global__ void __launch_bounds__(ROT_THREADS) rotate_kernel(const float *Q, const uint8_t *Q8, int64_t nq, int d,
                                                              const float *Rt, float *yq)
 {
-    extern __shared__ __align__(16) float rsm[];
+    extern __shared__ __align__(128) float rsm[];
     const bool shared_rt = rotate_rt_shared(d);
     float *ys = rsm + (shared_rt ? d * d : 0);
     const float *R = Rt;
@@ -1112,14 +1196,18 @@ lc_status upload(lc_index *ix)
     put_layout(4, [&](size_t i, float v) { c1w[i] = v; });
     std::vector<__half> c1h(walk_c1_bytes(d, M1, D1, 2) / 2, __float2half_rn(0.f));
     put_layout(2, [&](size_t i, float v) { c1h[i] = __float2half_rn(v); });
+    std::vector<__half> c2h(ix->C2.size());
+    for (size_t i = 0; i < c2h.size(); i++) c2h[i] = __float2half_rn(ix->C2[i]);   // round to nearest even
+    __half *c2h_dev = static_cast<__half *>(dv->C2h);
     __half *c1h_dev = static_cast<__half *>(dv->C1h);
     bool ok = dupload(dv->Rt, Rt) && dupload(dv->C1, ix->C1) && dupload(dv->C2, ix->C2) &&
-              dupload(dv->C1w, c1w) && dupload(c1h_dev, c1h) &&
+              dupload(dv->C1w, c1w) && dupload(c1h_dev, c1h) && dupload(c2h_dev, c2h) &&
               dupload(dv->B, ix->B) && dupload(dv->codes1, ix->codes1) &&
               dupload(dv->codes2b, c2b) &&
               dupload(dv->adj0, ix->adj0) && dupload(dv->upper_off, off) &&
               dupload(dv->upper_adj, ix->upper_adj);
     dv->C1h = c1h_dev;
+    dv->C2h = c2h_dev;
     if (!ok) {
         set_error("device upload of the index failed: %s", cudaGetErrorString(cudaGetLastError()));
         return LC_ERR_OOM;
@@ -1150,22 +1238,22 @@ constexpr size_t MAX_SMEM_PER_BLOCK = 227 * 1024;
 
 // Warps per CTA: as many as fit next to the codebook (at most MAX_WALK_WARPS, and at most
 // want if want > 0).
-template <int M1, int D1, typename CT>
+template <int M1, int D1, typename CT, bool FQ>
 static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int want, int *wpc_out,
                                int *grid_out, size_t *smem_out)
 {
-    size_t c1 = walk_c1_bytes(wa.d, M1, D1, sizeof(CT));
+    size_t c1 = walk_cb_bytes(wa.d, M1, D1, sizeof(CT), FQ);
     if (c1 + smem_per_warp > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
     int wpc = (int)std::min<size_t>(MAX_WALK_WARPS, (MAX_SMEM_PER_BLOCK - c1) / smem_per_warp);
     if (want > 0) wpc = std::min(wpc, want);
     size_t smem = c1 + smem_per_warp * wpc;
     // the attribute is an upper bound: set to the maximum, so plans made in any order (the
     // server plans at submission and launches later) all remain launchable
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1, CT, FQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)MAX_SMEM_PER_BLOCK);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1, CT>, wpc * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1, CT, FQ>, wpc * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t need = (wa.nq + wpc - 1) / wpc;
@@ -1175,10 +1263,10 @@ static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num
     return cudaSuccess;
 }
 
-template <int M1, int D1, typename CT>
+template <int M1, int D1, typename CT, bool FQ>
 static cudaError_t run_walk(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
 {
-    walk_kernel<M1, D1, CT><<<grid, wpc * 32, smem, st>>>(wa);
+    walk_kernel<M1, D1, CT, FQ><<<grid, wpc * 32, smem, st>>>(wa);
     return cudaGetLastError();
 }
 
@@ -1198,48 +1286,74 @@ static RefineFn refine_kernel_for(bool both, int d, bool prod)
     return both ? refine_kernel<true, 8, false> : refine_kernel<false, 8, false>;
 }
 
-// Dispatch on (sub-space width variant, codebook element type).
+// Dispatch on (sub-space width variant, codebook element type, full walk).  The full walk
+// exists for the uniform splits only (variants 1-3).
 template <typename CT>
-static cudaError_t launch_any(int variant, int M1, const WalkArgs &wa, size_t per_warp, int sms, int want,
+static cudaError_t launch_any(int variant, int M1, bool fq, const WalkArgs &wa, size_t per_warp, int sms, int want,
                               int *wpc, int *grid, size_t *smem)
 {
+    if (fq) {
+        switch (variant) {
+        case 1: return launch_walk<16, 6, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
+        case 2: return launch_walk<32, 3, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
+        case 3: return launch_walk<64, 2, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (variant) {
-    case 1: return launch_walk<16, 6, CT>(wa, per_warp, sms, want, wpc, grid, smem);
-    case 2: return launch_walk<32, 3, CT>(wa, per_warp, sms, want, wpc, grid, smem);
-    case 3: return launch_walk<64, 2, CT>(wa, per_warp, sms, want, wpc, grid, smem);
+    case 1: return launch_walk<16, 6, CT, false>(wa, per_warp, sms, want, wpc, grid, smem);
+    case 2: return launch_walk<32, 3, CT, false>(wa, per_warp, sms, want, wpc, grid, smem);
+    case 3: return launch_walk<64, 2, CT, false>(wa, per_warp, sms, want, wpc, grid, smem);
     default:
-        if (M1 == 16) return launch_walk<16, 0, CT>(wa, per_warp, sms, want, wpc, grid, smem);
-        if (M1 == 32) return launch_walk<32, 0, CT>(wa, per_warp, sms, want, wpc, grid, smem);
-        return launch_walk<64, 0, CT>(wa, per_warp, sms, want, wpc, grid, smem);
+        if (M1 == 16) return launch_walk<16, 0, CT, false>(wa, per_warp, sms, want, wpc, grid, smem);
+        if (M1 == 32) return launch_walk<32, 0, CT, false>(wa, per_warp, sms, want, wpc, grid, smem);
+        return launch_walk<64, 0, CT, false>(wa, per_warp, sms, want, wpc, grid, smem);
     }
 }
 
 // The walk instantiation a plan launches (for finding its node in a captured graph).
 template <typename CT>
-static const void *walk_fn(int variant, int M1)
+static const void *walk_fn(int variant, int M1, bool fq)
 {
+    if (fq) {
+        switch (variant) {
+        case 1: return (const void *)walk_kernel<16, 6, CT, true>;
+        case 2: return (const void *)walk_kernel<32, 3, CT, true>;
+        case 3: return (const void *)walk_kernel<64, 2, CT, true>;
+        default: return nullptr;
+        }
+    }
     switch (variant) {
-    case 1: return (const void *)walk_kernel<16, 6, CT>;
-    case 2: return (const void *)walk_kernel<32, 3, CT>;
-    case 3: return (const void *)walk_kernel<64, 2, CT>;
+    case 1: return (const void *)walk_kernel<16, 6, CT, false>;
+    case 2: return (const void *)walk_kernel<32, 3, CT, false>;
+    case 3: return (const void *)walk_kernel<64, 2, CT, false>;
     default:
-        if (M1 == 16) return (const void *)walk_kernel<16, 0, CT>;
-        if (M1 == 32) return (const void *)walk_kernel<32, 0, CT>;
-        return (const void *)walk_kernel<64, 0, CT>;
+        if (M1 == 16) return (const void *)walk_kernel<16, 0, CT, false>;
+        if (M1 == 32) return (const void *)walk_kernel<32, 0, CT, false>;
+        return (const void *)walk_kernel<64, 0, CT, false>;
     }
 }
 
 template <typename CT>
-static cudaError_t run_any(int variant, int M1, const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
+static cudaError_t run_any(int variant, int M1, bool fq, const WalkArgs &wa, size_t smem, int wpc, int grid,
+                           cudaStream_t st)
 {
+    if (fq) {
+        switch (variant) {
+        case 1: return run_walk<16, 6, CT, true>(wa, smem, wpc, grid, st);
+        case 2: return run_walk<32, 3, CT, true>(wa, smem, wpc, grid, st);
+        case 3: return run_walk<64, 2, CT, true>(wa, smem, wpc, grid, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (variant) {
-    case 1: return run_walk<16, 6, CT>(wa, smem, wpc, grid, st);
-    case 2: return run_walk<32, 3, CT>(wa, smem, wpc, grid, st);
-    case 3: return run_walk<64, 2, CT>(wa, smem, wpc, grid, st);
+    case 1: return run_walk<16, 6, CT, false>(wa, smem, wpc, grid, st);
+    case 2: return run_walk<32, 3, CT, false>(wa, smem, wpc, grid, st);
+    case 3: return run_walk<64, 2, CT, false>(wa, smem, wpc, grid, st);
     default:
-        if (M1 == 16) return run_walk<16, 0, CT>(wa, smem, wpc, grid, st);
-        if (M1 == 32) return run_walk<32, 0, CT>(wa, smem, wpc, grid, st);
-        return run_walk<64, 0, CT>(wa, smem, wpc, grid, st);
+        if (M1 == 16) return run_walk<16, 0, CT, false>(wa, smem, wpc, grid, st);
+        if (M1 == 32) return run_walk<32, 0, CT, false>(wa, smem, wpc, grid, st);
+        return run_walk<64, 0, CT, false>(wa, smem, wpc, grid, st);
     }
 }
 
@@ -1259,19 +1373,24 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     P.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)P.efp * 32)));
     P.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)P.efp * 64)));
     const int efcap = (int)align_up(P.efp, 32);
-    P.per_warp = walk_smem(dv->M1, dv->d, efcap, P.hash_log, P.beam, false).total;
     // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
     P.variant = walk_variant(dv->M1, dv->d);
+    P.full = sp->walk_full != 0;
+    if (P.full && P.variant == 0) {
+        set_error("the full-decode walk needs a uniform level-1 split (M1 = 16 or 32 at d = 96, M1 = 64 at d = 128)");
+        return LC_ERR_ARG;
+    }
+    P.per_warp = walk_smem(dv->M1, dv->d, efcap, P.hash_log, P.beam, false, P.full ? dv->M2P : 0).total;
     WalkArgs wa{};
     wa.nq = nq;
     wa.d = dv->d;
     P.half = sp->lut_prec == LC_LUT_FP16;
-    cudaError_t ce = P.half ? launch_any<__half>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem)
-                            : launch_any<float>(P.variant, dv->M1, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem);
+    cudaError_t ce = P.half ? launch_any<__half>(P.variant, dv->M1, P.full, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem)
+                            : launch_any<float>(P.variant, dv->M1, P.full, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem);
     if (ce == cudaErrorInvalidConfiguration) {
         set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
                   "lower efSearch or visited_log", P.per_warp,
-                  walk_c1_bytes(dv->d, dv->M1, walk_variant_d1(P.variant), P.half ? 2 : 4));
+                  walk_cb_bytes(dv->d, dv->M1, walk_variant_d1(P.variant), P.half ? 2 : 4, P.full));
         return LC_ERR_CAPACITY;
     }
     if (ce != cudaSuccess) {
@@ -1350,6 +1469,15 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
     std::vector<int> off, len;
     splits(dv->d, dv->M1, off, len);
     for (int j = 0; j < dv->M1; j++) { wa.s1.off[j] = (uint16_t)off[j]; wa.s1.len[j] = (uint8_t)len[j]; }
+    if (P.full) {
+        wa.C2 = dv->C2;
+        wa.C2h = static_cast<const __half *>(dv->C2h);
+        wa.codes2b = dv->codes2b;
+        wa.M2P = dv->M2P;
+        std::vector<int> o2, l2;
+        splits(dv->d, dv->M2, o2, l2);
+        for (int j = 0; j < dv->M2; j++) for (int t = o2[j]; t < o2[j] + l2[j]; t++) wa.sub2[t] = (uint8_t)j;
+    }
     if (cudaMemsetAsync(sc.status, 0, sizeof(int32_t), st) != cudaSuccess ||
         cudaMemsetAsync(sc.counter, 0, sizeof(unsigned long long), st) != cudaSuccess) {
         set_error("status reset failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1366,8 +1494,8 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         set_error("rotation kernel launch failed: %s", cudaGetErrorString(ce));
         return LC_ERR_CUDA;
     }
-    ce = P.half ? run_any<__half>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st)
-                : run_any<float>(P.variant, dv->M1, wa, P.smem, P.wpc, P.grid, st);
+    ce = P.half ? run_any<__half>(P.variant, dv->M1, P.full, wa, P.smem, P.wpc, P.grid, st)
+                : run_any<float>(P.variant, dv->M1, P.full, wa, P.smem, P.wpc, P.grid, st);
     if (profile) cudaEventRecord(dv->ev[1], st);
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
@@ -1623,7 +1751,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     int grid = 0, wpc = 1;
     size_t smem = 0;
     cudaError_t ce;
-    ce = launch_any<float>(variant, dv->M1, wa, per_warp, dv->num_sms, 0, &wpc, &grid, &smem);
+    ce = launch_any<float>(variant, dv->M1, false, wa, per_warp, dv->num_sms, 0, &wpc, &grid, &smem);
     if (ce != cudaSuccess) {
         set_error("walk kernel configuration failed: %s", cudaGetErrorString(ce));
         return ce == cudaErrorInvalidConfiguration ? LC_ERR_CAPACITY : LC_ERR_CUDA;
@@ -1636,7 +1764,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
         set_error("reset of the no-allocation scratch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return LC_ERR_CUDA;
     }
-    ce = run_any<float>(variant, dv->M1, wa, smem, wpc, grid, st);
+    ce = run_any<float>(variant, dv->M1, false, wa, smem, wpc, grid, st);
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
         return LC_ERR_CUDA;
@@ -1830,7 +1958,7 @@ lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, 
         return rs == LC_OK ? LC_ERR_CUDA : rs;
     }
     // find the two kernel nodes whose batch size a smaller call updates
-    const void *wf = P.half ? walk_fn<__half>(P.variant, dv->M1) : walk_fn<float>(P.variant, dv->M1);
+    const void *wf = P.half ? walk_fn<__half>(P.variant, dv->M1, P.full) : walk_fn<float>(P.variant, dv->M1, P.full);
     const void *rf = P.refine ? (const void *)refine_kernel_for(P.rboth, d, dv->bM > 1) : nullptr;
     size_t nn = 0;
     cudaGraphGetNodes(pl->graph, nullptr, &nn);

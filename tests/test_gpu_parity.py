@@ -38,11 +38,11 @@ def handle(name, ix):
     return _handles[name]
 
 
-def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1, tcap=0, lut_prec=0):
+def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1, tcap=0, lut_prec=0, walk_full=0):
     import torch
     nq = len(xq)
     sp = lc.lc_default_search_params(k, ef, shortlist=shortlist, visited_log=visited_log, max_dist=tcap,
-                                     lut_prec=lut_prec)
+                                     lut_prec=lut_prec, walk_full=walk_full)
     if beam > 1:
         sp.mode, sp.beam = lc.LC_MODE_BATCHED, beam
     if device:
