@@ -309,7 +309,7 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
             sizes = np.exp(rng.uniform(0, np.log(512), size=n)).astype(int)
             ks = rng.choice([1, 10, 100], size=n)
             efs = np.exp(rng.uniform(np.log(16), np.log(512), size=n)).astype(int)
-            lat, cbs2, arr_of = [], [], {}
+            lat, cbs2, arr_of, shape_of = [], [], {}, {}
             fin = {}
 
             def cb_lat(rid, st, i, d):
@@ -326,13 +326,17 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
                     cbs2.append(cb)
                     rid = lc.lc_serve_submit(srv, xq[s0:s0 + sizes[j]], sp, cb)
                     arr_of[rid] = tb + arrive[j]
+                    shape_of[rid] = (int(sizes[j]), int(ks[j]), int(efs[j]))
                     j += 1
                 lc.lc_serve_poll(srv, 0)
-            lat = np.array([(fin[r][0] - arr_of[r]) * 1e3 for r in arr_of])
+            rids = list(arr_of)
+            lat = np.array([(fin[r][0] - arr_of[r]) * 1e3 for r in rids])
+            slow = [dict(zip(("queries", "k", "efSearch"), shape_of[rids[i]]), latency_ms=round(float(lat[i]), 2))
+                    for i in np.argsort(-lat)[:5]]
             span = max(v[0] for v in fin.values()) - tb
             points.append({"offered_qps": lam, "requests": n, "achieved_qps": float(sizes.sum() / span),
                            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                           "all_ok": all(v[1] == 0 for v in fin.values())})
+                           "all_ok": all(v[1] == 0 for v in fin.values()), "slowest": slow})
         out["open_loop"] = points
         out["open_loop_mix"] = ("request sizes log-uniform in [1, 512] queries, k uniform in {1, 10, 100}, "
                                 "efSearch log-uniform in [16, 512], plain mode, Poisson arrivals")
@@ -499,7 +503,7 @@ def main():
     base_level = 1.0 if uneven else args.ef
     # sweep levels of the batched forms: efSearch values, or scale factors of the per-query ones
     levels = ((0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 1.0, 1.25, 1.5, 2.0) if uneven else
-              sorted({e for e in (16, 24, 32, 40, 48, 56, 64, 80, 96, 128) if e <= max(2 * args.ef, 16)}))
+              sorted({e for e in (16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 128) if e <= max(2 * args.ef, 16)}))
     batched = None
     lut1 = lc.LC_LUT_FP16 if args.lut == "fp16" else lc.LC_LUT_FP32
     if args.mode == "batched":
