@@ -173,9 +173,9 @@ def extra_queries(w, start, n):
     return dg.gaussian_mixture(n, w["d"], w["centres"], stream=dg.STREAM_QUERY, start=start)
 
 
-def build_index(w, xt, xb):
+def build_index(w, xt, xb, build_gpu=0):
     from paper_1804_09996_gb300 import lc
-    p = lc.lc_default_params(w["d"], w["M1"], w["M2"], use_opq=w["opq"])
+    p = lc.lc_default_params(w["d"], w["M1"], w["M2"], use_opq=w["opq"], build_gpu=build_gpu)
     h = lc.lc_create(p)
     t0 = time.time()
     lc.lc_train(h, xt.astype(np.float32))
@@ -423,6 +423,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="target duration of each open-loop point")
     ap.add_argument("--visited-log", type=int, default=0,
                     help="visited table size 2^v of the single form run by --mode plain / batched (0: automatic)")
+    ap.add_argument("--gpu-build", type=int, default=0,
+                    help="1: the index build runs its level-0 insertion searches on the GPU")
     ap.add_argument("--walk-full", type=int, default=0, help="single form: 1 = walk on the full two-level decode")
     ap.add_argument("--lut", default="fp32", choices=["fp32", "fp16"],
                     help="level-1 codebook precision of the single form run by --mode plain / batched")
@@ -444,7 +446,7 @@ def main():
     dev = local
     torch.cuda.set_device(dev)
     xt, xb, xq = make_data(w)
-    h, build_s = build_index(w, xt, xb)
+    h, build_s = build_index(w, xt, xb, args.gpu_build)
     del xt
     n_gt = min(len(xq), w.get("gt_sample", len(xq)))
     gt, gt_d = exact_nn(xb, xq[:n_gt], f"cuda:{dev}")
@@ -695,7 +697,7 @@ def main():
                         "walk": "full two-level decode q = c1 + c2, codebooks rounded to FP16"}),
                    "served": served,
                    "l2": "flushed before every step (256 MB read, outside the timed span)",
-                   "index_build_s": round(build_s, 1), "parallelism": f"replicas x{ws}"},
+                   "index_build_s": round(build_s, 1), "index_build": "GPU-assisted" if args.gpu_build else "host", "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "walk_kernel",
                      "peak_source": peak_src, "algorithmic_bytes_per_launch": b_walk},

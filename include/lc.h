@@ -70,6 +70,12 @@ typedef struct {
                               block is e0 and beta_M bytes are stored per vector; 1: the 0-byte
                               refinement of Section 4.2 (one least-squares weight vector per
                               block, shared by all vectors, nothing stored per vector) */
+    int build_gpu;         /* 1: lc_add runs the level-0 insertion searches of each batch on the
+                              current GPU (the batch searches the graph as it stood at the batch
+                              start, Section 5.1, all its level-0 members at once, with the
+                              exact-to-decoded distance of the full-decode walk); neighbour
+                              selection, links and the few nodes of higher level stay on the
+                              host.  0 (default): everything on the host */
 } lc_params;
 
 /* Fills *p with the defaults above for dimension d and code sizes M1, M2. */
@@ -109,8 +115,8 @@ typedef struct {
     int walk_full;   /* 0: the walk scores the level-1 code by ADC (the default reading of
                         Section 4.1); 1: it scores the full two-level decode q = c1 + c2 (each
                         coordinate's level-1 plus level-2 centroid; reads M1 + M2P code bytes
-                        per node).  1 needs a uniform level-1 split (M1 = 16 or 32 at d = 96,
-                        M1 = 64 at d = 128); with LC_LUT_FP16 both codebooks are rounded */
+                        per node).  With LC_LUT_FP16 both codebooks are rounded, which needs a
+                        uniform level-1 split (M1 = 16 or 32 at d = 96, M1 = 64 at d = 128) */
 } lc_search_params;
 
 void lc_default_search_params(lc_search_params *p, int k, int ef);

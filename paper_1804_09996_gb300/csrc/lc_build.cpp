@@ -572,11 +572,20 @@ static void add_link(Graph &g, int l, int32_t owner, int32_t x)
 
 }  // namespace
 
-static void insert_range(lc_index *ix, const float *xr, int64_t first, int64_t count, int nt)
+static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int64_t count, int nt)
 {
     const lc_params &p = ix->p;
     Graph g{ix, p.d, ix->xh.data()};
     std::vector<SearchState> states(nt);
+    const bool gpu = p.build_gpu != 0;
+    if (gpu) {
+        lc_status rs = build_gpu_begin(ix);
+        if (rs != LC_OK) return rs;
+    }
+    const int efc = p.ef_construction;
+    std::vector<int64_t> gmem;                  // batch members searched on the device
+    std::vector<int32_t> gslot, gids;           // member -> row of the device results
+    std::vector<float> gxr, gd;
     int64_t done = 0;
     while (done < count) {
         int64_t ncur = first + done;
@@ -589,6 +598,21 @@ static void insert_range(lc_index *ix, const float *xr, int64_t first, int64_t c
         int32_t ep0 = ix->ep;
         // selections per batch member and level: sel[u][l] (up to DEG ids)
         std::vector<std::vector<int32_t>> sel(b);
+        // level-0 members: their level-0 insertion searches run together on the device
+        gmem.clear();
+        gslot.assign(b, -1);
+        if (gpu && ep0 >= 0) {
+            for (int64_t u = 0; u < b; u++)
+                if (ix->levels[ncur + u] == 0) { gslot[u] = (int32_t)gmem.size(); gmem.push_back(u); }
+            const int64_t m = (int64_t)gmem.size();
+            gxr.resize((size_t)m * p.d);
+            for (int64_t i = 0; i < m; i++)
+                std::memcpy(gxr.data() + i * p.d, xr + (ncur + gmem[i] - first) * p.d, sizeof(float) * p.d);
+            gids.resize((size_t)m * efc);
+            gd.resize((size_t)m * efc);
+            lc_status rs = build_gpu_search(ix, gxr.data(), m, efc, ep0, ml0, gids.data(), gd.data());
+            if (rs != LC_OK) { build_gpu_end(ix); return rs; }
+        }
         parallel_for(b, nt, 8, [&](int64_t a, int64_t e, int t) {
             SearchState &st = states[t];
             for (int64_t u = a; u < e; u++) {
@@ -598,6 +622,16 @@ static void insert_range(lc_index *ix, const float *xr, int64_t first, int64_t c
                 int top = std::min(Lx, ml0);
                 sel[u].assign((size_t)(top + 1) * (DEG + 1), -1);
                 if (ep0 < 0) continue;
+                if (gslot[u] >= 0) {
+                    // level 0 searched on the device: its result list, sorted by (distance, id)
+                    const int32_t *gi = gids.data() + (size_t)gslot[u] * efc;
+                    const float *gv = gd.data() + (size_t)gslot[u] * efc;
+                    st.W.clear();
+                    for (int i = 0; i < efc && gi[i] >= 0; i++) st.W.push_back(Key{gv[i], gi[i]});
+                    int32_t *out = sel[u].data();
+                    out[DEG] = heuristic(g, st.W.data(), (int)st.W.size(), DEG, out);
+                    continue;
+                }
                 int32_t cur = ep0;
                 float dcur = l2f(xv, g.xh + (int64_t)cur * p.d, p.d);
                 for (int l = ml0; l > Lx; l--) {
@@ -661,12 +695,31 @@ static void insert_range(lc_index *ix, const float *xr, int64_t first, int64_t c
                 for (size_t i = starts[gi]; i < starts[gi + 1]; i++)
                     add_link(g, links[i].level, links[i].target, links[i].src);
         });
+        if (gpu) {
+            // re-send every row the batch wrote: the members' own rows and the link targets'
+            std::vector<int32_t> rows0;
+            std::vector<int64_t> rowsu;
+            for (int64_t u = 0; u < b; u++) {
+                int64_t x = ncur + u;
+                rows0.push_back((int32_t)x);
+                for (int l = 1; l <= std::min((int)ix->levels[x], ml0); l++) rowsu.push_back(ix->upper_off[x] + l - 1);
+            }
+            for (size_t gi = 0; gi + 1 < starts.size(); gi++) {
+                const Link &lk = links[starts[gi]];
+                if (lk.level == 0) rows0.push_back(lk.target);
+                else rowsu.push_back(ix->upper_off[lk.target] + lk.level - 1);
+            }
+            lc_status rs = build_gpu_rows(ix, rows0.data(), (int64_t)rows0.size(), rowsu.data(), (int64_t)rowsu.size());
+            if (rs != LC_OK) { build_gpu_end(ix); return rs; }
+        }
         for (int64_t u = 0; u < b; u++) {
             int64_t x = ncur + u;
             if (ix->levels[x] > ix->max_level) { ix->max_level = ix->levels[x]; ix->ep = (int32_t)x; }
         }
         done += b;
     }
+    if (gpu) build_gpu_end(ix);
+    return LC_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -911,7 +964,8 @@ lc_status build_add(lc_index *ix, const float *x, int64_t n)
     ix->adj0.resize((size_t)total * DEG, -1);
     ix->adj0_d.resize((size_t)total * DEG, 0.f);
     ix->n = total;
-    insert_range(ix, xr.data(), first, n, nt);
+    lc_status rs = insert_range(ix, xr.data(), first, n, nt);
+    if (rs != LC_OK) return rs;
     if (!ix->has_codebook) train_codebook(ix, xr.data(), first, n, nt);
     assign_codewords(ix, xr.data(), first, n, nt);
     ix->dev_dirty = true;

@@ -41,6 +41,7 @@ static lc_status check_params(const lc_params *p)
         return LC_ERR_ARG;
     }
     if (p->beta_K < 1 || p->beta_K > NBETA) { set_error("beta_K = %d outside 1..%d", p->beta_K, NBETA); return LC_ERR_ARG; }
+    if (p->build_gpu != 0 && p->build_gpu != 1) { set_error("build_gpu = %d is neither 0 nor 1", p->build_gpu); return LC_ERR_ARG; }
     return LC_OK;
 }
 
@@ -342,10 +343,10 @@ lc_status lc_export(const lc_index *ix, float *R, float *C1, float *C2, uint8_t 
     return LC_OK;
 }
 
-// File format (little-endian, native layouts): "LCIDX002", lc_params, int64 n, int64 upper
+// File format (little-endian, native layouts): "LCIDX003", lc_params, int64 n, int64 upper
 // rows, int32 ep, int32 max_level, int32 trained, int32 has_codebook, then R, C1, C2,
 // B [beta_M][beta_K][9], codes1, codes2, beta [n][beta_M], adj0, levels, upper_adj.
-static const char MAGIC[8] = {'L', 'C', 'I', 'D', 'X', '0', '0', '2'};
+static const char MAGIC[8] = {'L', 'C', 'I', 'D', 'X', '0', '0', '3'};
 
 lc_status lc_save(const lc_index *ix, const char *path)
 {

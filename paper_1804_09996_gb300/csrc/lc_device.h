@@ -38,6 +38,12 @@ struct DeviceIndex {
     bool ev_valid = false, has_refine = false;
     int num_sms = 0;
     uint64_t gen = 0;             // changes with every upload (plans check it)
+    // GPU-assisted build: batch vectors, results and re-sent rows
+    float *b_yq = nullptr; size_t b_yq_cap = 0;
+    int32_t *b_ids = nullptr; size_t b_ids_cap = 0;
+    float *b_d = nullptr; size_t b_d_cap = 0;
+    int32_t *b_rows = nullptr; size_t b_rows_cap = 0;
+    int64_t *b_idx = nullptr; size_t b_idx_cap = 0;
 };
 
 // Launch configuration of one search and the scratch it needs.
@@ -70,9 +76,9 @@ lc_status upload(lc_index *ix);
 lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl);
 // Queues the walk (and refinement) on `st`; q, ids, dists, stats are device pointers.
 // q8 (uint8 queries [nq][d], replacing q) and efq (per-query efSearch [nq]) are optional
-// device pointers.
+// device pointers; rotated: sc.yq already holds y' (no rotation launch, q unused).
 lc_status run_search(DeviceIndex *dv, const SearchPlan &pl, const float *q, int64_t nq, int32_t *ids,
                      float *dists, int32_t *stats, const SearchScratch &sc, cudaStream_t st, bool profile,
-                     const uint8_t *q8 = nullptr, const int32_t *efq = nullptr);
+                     const uint8_t *q8 = nullptr, const int32_t *efq = nullptr, bool rotated = false);
 
 }  // namespace lc

@@ -74,6 +74,16 @@ lc_status profile_read(lc_index *ix, float *walk_ms, float *refine_ms);
 // Autotuner (lc_tune.cpp).
 lc_status autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, const lc_tune_params *tp,
                    lc_tune_result *out);
+// GPU-assisted build (lc_search.cu): the device copy of the index under construction serves
+// the level-0 insertion searches of each batch; rows changed by a batch are re-sent.
+lc_status build_gpu_begin(lc_index *ix);
+// m rotated vectors xr [m][d] (host) search level 0 from ep after a greedy descent of levels
+// max_level..1, keeping efc: ids/dists [m][efc] (host, sorted by (distance, id), -1 padded).
+lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, int32_t ep, int max_level,
+                           int32_t *ids, float *dists);
+// Re-sends level-0 rows of nodes0 [n0] and upper rows (indexes into upper_adj) rows_up [nu].
+lc_status build_gpu_rows(lc_index *ix, const int32_t *nodes0, int64_t n0, const int64_t *rows_up, int64_t nu);
+void build_gpu_end(lc_index *ix);
 // Captured searches (lc_plan_*), lc_search.cu.
 lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype, int per_query_ef,
                       lc_plan **out);

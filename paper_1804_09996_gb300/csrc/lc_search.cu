@@ -53,6 +53,7 @@ void device_free(DeviceIndex *dv)
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
+    cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx);
     cfree(dv->q_st); cfree(dv->ef_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
     for (auto &e : dv->ev) if (e) cudaEventDestroy(e);
     if (cur >= 0) cudaSetDevice(cur);
@@ -1287,7 +1288,7 @@ static RefineFn refine_kernel_for(bool both, int d, bool prod)
 }
 
 // Dispatch on (sub-space width variant, codebook element type, full walk).  The full walk
-// exists for the uniform splits only (variants 1-3).
+// exists for the uniform splits (variants 1-3) and, in FP32, for any split.
 template <typename CT>
 static cudaError_t launch_any(int variant, int M1, bool fq, const WalkArgs &wa, size_t per_warp, int sms, int want,
                               int *wpc, int *grid, size_t *smem)
@@ -1297,7 +1298,13 @@ static cudaError_t launch_any(int variant, int M1, bool fq, const WalkArgs &wa, 
         case 1: return launch_walk<16, 6, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
         case 2: return launch_walk<32, 3, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
         case 3: return launch_walk<64, 2, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
-        default: return cudaErrorInvalidValue;
+        default:
+            if constexpr (sizeof(CT) == 4) {
+                if (M1 == 16) return launch_walk<16, 0, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
+                if (M1 == 32) return launch_walk<32, 0, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
+                return launch_walk<64, 0, CT, true>(wa, per_warp, sms, want, wpc, grid, smem);
+            }
+            return cudaErrorInvalidValue;
         }
     }
     switch (variant) {
@@ -1320,7 +1327,13 @@ static const void *walk_fn(int variant, int M1, bool fq)
         case 1: return (const void *)walk_kernel<16, 6, CT, true>;
         case 2: return (const void *)walk_kernel<32, 3, CT, true>;
         case 3: return (const void *)walk_kernel<64, 2, CT, true>;
-        default: return nullptr;
+        default:
+            if constexpr (sizeof(CT) == 4) {
+                if (M1 == 16) return (const void *)walk_kernel<16, 0, CT, true>;
+                if (M1 == 32) return (const void *)walk_kernel<32, 0, CT, true>;
+                return (const void *)walk_kernel<64, 0, CT, true>;
+            }
+            return nullptr;
         }
     }
     switch (variant) {
@@ -1343,7 +1356,13 @@ static cudaError_t run_any(int variant, int M1, bool fq, const WalkArgs &wa, siz
         case 1: return run_walk<16, 6, CT, true>(wa, smem, wpc, grid, st);
         case 2: return run_walk<32, 3, CT, true>(wa, smem, wpc, grid, st);
         case 3: return run_walk<64, 2, CT, true>(wa, smem, wpc, grid, st);
-        default: return cudaErrorInvalidValue;
+        default:
+            if constexpr (sizeof(CT) == 4) {
+                if (M1 == 16) return run_walk<16, 0, CT, true>(wa, smem, wpc, grid, st);
+                if (M1 == 32) return run_walk<32, 0, CT, true>(wa, smem, wpc, grid, st);
+                return run_walk<64, 0, CT, true>(wa, smem, wpc, grid, st);
+            }
+            return cudaErrorInvalidValue;
         }
     }
     switch (variant) {
@@ -1376,8 +1395,9 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
     P.variant = walk_variant(dv->M1, dv->d);
     P.full = sp->walk_full != 0;
-    if (P.full && P.variant == 0) {
-        set_error("the full-decode walk needs a uniform level-1 split (M1 = 16 or 32 at d = 96, M1 = 64 at d = 128)");
+    if (P.full && P.variant == 0 && sp->lut_prec == LC_LUT_FP16) {
+        set_error("the full-decode walk in FP16 needs a uniform level-1 split (M1 = 16 or 32 at d = 96, "
+                  "M1 = 64 at d = 128); use FP32");
         return LC_ERR_ARG;
     }
     P.per_warp = walk_smem(dv->M1, dv->d, efcap, P.hash_log, P.beam, false, P.full ? dv->M2P : 0).total;
@@ -1441,7 +1461,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
 
 lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int64_t nq, int32_t *dids,
                      float *ddists, int32_t *dstats, const SearchScratch &sc, cudaStream_t st, bool profile,
-                     const uint8_t *dq8, const int32_t *defq)
+                     const uint8_t *dq8, const int32_t *defq, bool rotated)
 {
     WalkArgs wa{};
     wa.Q = dq; wa.Q8 = dq8; wa.efq = defq; wa.k = P.k; wa.nq = nq; wa.d = dv->d;
@@ -1488,7 +1508,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
             if (!e) cudaEventCreate(&e);
         cudaEventRecord(dv->ev[0], st);
     }
-    rotate_kernel<<<std::max(P.qgrid, 1), ROT_THREADS, P.qsm, st>>>(dq, dq8, nq, dv->d, dv->Rt, sc.yq);
+    if (!rotated) rotate_kernel<<<std::max(P.qgrid, 1), ROT_THREADS, P.qsm, st>>>(dq, dq8, nq, dv->d, dv->Rt, sc.yq);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         set_error("rotation kernel launch failed: %s", cudaGetErrorString(ce));
@@ -2048,6 +2068,114 @@ lc_status plan_run(lc_plan *pl, int64_t nq, void *stream)
         return LC_ERR_CUDA;
     }
     return LC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// GPU-assisted build.  lc_add inserts by batches, each searching the graph as it stood at the
+// batch start (Section 5.1); the level-0 insertion searches of a batch are independent, so
+// they run as one launch of the walk on the device copy of the index, with the exact-to-
+// decoded distance of the full-decode walk (FP32).  The host keeps neighbour selection,
+// linking and the nodes of higher level, and re-sends the rows a batch changed.
+
+__global__ void scatter_rows_kernel(int32_t *dst, const int64_t *idx, const int32_t *rows, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * DEG; i += (int64_t)gridDim.x * blockDim.x)
+        dst[idx[i / DEG] * DEG + (i % DEG)] = rows[i];
+}
+
+lc_status build_gpu_begin(lc_index *ix)
+{
+    ix->dev_dirty = true;                       // upload the index as it stands (codes of all nodes)
+    return upload(ix);
+}
+
+lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, int32_t ep, int max_level,
+                           int32_t *ids, float *dists)
+{
+    DeviceIndex *dv = ix->dev;
+    if (!dv || m <= 0) return LC_OK;
+    lc_search_params sp;
+    lc_default_search_params(&sp, efc, efc);
+    sp.shortlist = -1;                          // the walk's own result list, sorted
+    sp.walk_full = 1;
+    SearchPlan P;
+    lc_status rs = plan_search(dv, m, &sp, &P);
+    if (rs != LC_OK) return rs;
+    if (!grow(dv->b_yq, dv->b_yq_cap, (size_t)m * dv->d) || !grow(dv->b_ids, dv->b_ids_cap, (size_t)m * efc) ||
+        !grow(dv->b_d, dv->b_d_cap, (size_t)m * efc) || !grow(dv->spill, dv->spill_cap, P.spill_elems)) {
+        set_error("cudaMalloc failed for the build's search buffers");
+        return LC_ERR_OOM;
+    }
+    if (cudaMemcpy(dv->b_yq, xr, sizeof(float) * m * dv->d, cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("build batch upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return LC_ERR_CUDA;
+    }
+    dv->ep = ep;
+    dv->max_level = max_level < 0 ? 0 : max_level;
+    SearchScratch sc;
+    sc.yq = dv->b_yq;
+    sc.spill = dv->spill;
+    sc.status = dv->status;
+    sc.counter = dv->counter;
+    rs = run_search(dv, P, nullptr, m, dv->b_ids, dv->b_d, nullptr, sc, 0, false, nullptr, nullptr, true);
+    if (rs != LC_OK) return rs;
+    int32_t status = 0;
+    if (cudaMemcpy(ids, dv->b_ids, sizeof(int32_t) * m * efc, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(dists, dv->b_d, sizeof(float) * m * efc, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&status, dv->status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("build search failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return LC_ERR_CUDA;
+    }
+    if (status) {
+        set_error("an insertion search overflowed its visited table");
+        return LC_ERR_CAPACITY;
+    }
+    return LC_OK;
+}
+
+static lc_status scatter_rows(DeviceIndex *dv, int32_t *dst, const int32_t *src_rows, const int64_t *idx, int64_t n)
+{
+    if (n <= 0) return LC_OK;
+    std::vector<int32_t> rows((size_t)n * DEG);
+    for (int64_t r = 0; r < n; r++) std::memcpy(rows.data() + r * DEG, src_rows + idx[r] * DEG, DEG * 4);
+    if (!grow(dv->b_rows, dv->b_rows_cap, rows.size()) || !grow(dv->b_idx, dv->b_idx_cap, (size_t)n)) {
+        set_error("cudaMalloc failed for the build's row updates");
+        return LC_ERR_OOM;
+    }
+    if (cudaMemcpy(dv->b_rows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dv->b_idx, idx, (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("row update upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return LC_ERR_CUDA;
+    }
+    const int grid = (int)std::min<int64_t>((n * DEG + 255) / 256, (int64_t)dv->num_sms * 8);
+    scatter_rows_kernel<<<grid, 256>>>(dst, dv->b_idx, dv->b_rows, n);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_error("row update launch failed");
+        return LC_ERR_CUDA;
+    }
+    return LC_OK;
+}
+
+lc_status build_gpu_rows(lc_index *ix, const int32_t *nodes0, int64_t n0, const int64_t *rows_up, int64_t nu)
+{
+    DeviceIndex *dv = ix->dev;
+    if (!dv) return LC_OK;
+    std::vector<int64_t> i0(nodes0, nodes0 + n0);
+    lc_status rs = scatter_rows(dv, dv->adj0, ix->adj0.data(), i0.data(), n0);
+    if (rs != LC_OK) return rs;
+    return scatter_rows(dv, dv->upper_adj, ix->upper_adj.data(), rows_up, nu);
+}
+
+void build_gpu_end(lc_index *ix)
+{
+    DeviceIndex *dv = ix->dev;
+    if (dv) {
+        cudaDeviceSynchronize();
+        cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx);
+        dv->b_yq = nullptr; dv->b_ids = nullptr; dv->b_d = nullptr; dv->b_rows = nullptr; dv->b_idx = nullptr;
+        dv->b_yq_cap = dv->b_ids_cap = dv->b_d_cap = dv->b_rows_cap = dv->b_idx_cap = 0;
+    }
+    ix->dev_dirty = true;                       // codewords are assigned after the graph
 }
 
 lc_status profile_enable(lc_index *ix, int on)

@@ -46,7 +46,7 @@ class lc_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "d", "M1", "M2", "use_opq", "deg", "deg_upper", "level_ratio", "ef_construction",
         "beta_train_n", "beta_iters", "kmeans_iters", "opq_iters", "batch_max", "n_threads")] + [
-        ("seed", ctypes.c_uint64), ("beta_M", ctypes.c_int), ("beta_K", ctypes.c_int)]
+        ("seed", ctypes.c_uint64), ("beta_M", ctypes.c_int), ("beta_K", ctypes.c_int), ("build_gpu", ctypes.c_int)]
 
 
 class lc_search_params(ctypes.Structure):

@@ -30,6 +30,18 @@ def test_parity_full_walk(request, name, beam, prec):
         compare(ref, *got, max_exempt=0.1)
 
 
+@pytest.mark.parametrize("beam", [1, 4])
+def test_parity_full_walk_uneven_split(odd2k, beam):
+    # FP32 full walk with non-uniform level-1 and level-2 splits (d = 40, M1 = 16, M2 = 10)
+    ix, xb, xq = odd2k
+    h = handle("odd2k", ix)
+    for shortlist in (0, -1):
+        ref = oracle.search(ix, xq, 10, 48, shortlist=shortlist, beam=beam, walk_full=True)
+        compare(ref, *gpu_search(h, xq, 10, 48, shortlist, beam=beam, walk_full=1), max_exempt=0.1)
+        ref = oracle.search(ix, xq, 10, 48, shortlist=shortlist, beam=beam)
+        compare(ref, *gpu_search(h, xq, 10, 48, shortlist, beam=beam), max_exempt=0.1)
+
+
 def test_full_walk_differs_from_level1_walk(opq3k):
     # the two walks score different things: their visit counts differ on most queries
     ix, xb, xq = opq3k
@@ -39,7 +51,7 @@ def test_full_walk_differs_from_level1_walk(opq3k):
     assert (a[2][:, 0] != b[2][:, 0]).mean() > 0.5
 
 
-def test_full_walk_needs_uniform_split():
+def test_full_walk_fp16_needs_uniform_split():
     d, M1, M2, n = 40, 16, 8, 300
     rng = np.random.default_rng(3)
     h = lc.lc_create(lc.lc_default_params(d, M1, M2, use_opq=0, kmeans_iters=3, beta_iters=1))
@@ -50,8 +62,9 @@ def test_full_walk_needs_uniform_split():
         ids = np.empty((4, 10), np.int32)
         ds = np.empty((4, 10), np.float32)
         lc.lc_search(h, q, 4, lc.lc_default_search_params(10, 32), ids, ds)
+        lc.lc_search(h, q, 4, lc.lc_default_search_params(10, 32, walk_full=1), ids, ds)
         with pytest.raises(lc.LcError) as e:
-            lc.lc_search(h, q, 4, lc.lc_default_search_params(10, 32, walk_full=1), ids, ds)
+            lc.lc_search(h, q, 4, lc.lc_default_search_params(10, 32, walk_full=1, lut_prec=lc.LC_LUT_FP16), ids, ds)
         assert e.value.status == lc.LC_ERR_ARG and "uniform" in e.value.message
     finally:
         lc.lc_free(h)
