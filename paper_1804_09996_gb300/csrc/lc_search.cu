@@ -697,6 +697,53 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                             hcount += nf;
                         }
                     }
+                } else if (spilled && scount + 32 * nb <= (1 << a.spill_log) / 2) {
+                    // spilled, and every row fits in the global table: the shared table is only
+                    // read; the first global probes of up to 4 rows are issued together, then
+                    // each row is resolved in row order (as above)
+                    const uint32_t Hm = (uint32_t)H - 1, Sm = (1u << a.spill_log) - 1;
+                    for (int r0 = 0; r0 < nb; r0 += 4) {
+                        int32_t ev[4], ov[4];
+                        bool seen[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            ev[u] = r0 + u < nb ? rowbuf[(r0 + u) * DEG + lane] : -1;
+                            seen[u] = false;
+                            if (ev[u] >= 0) {
+                                uint32_t h = hash32(ev[u]) & Hm;
+                                for (uint32_t p = 0; p <= Hm; p++) {
+                                    const int32_t v = hash[h];
+                                    if (v == ev[u]) { seen[u] = true; break; }
+                                    if (v == -1) break;
+                                    h = (h + 1) & Hm;
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++)
+                            ov[u] = ev[u] >= 0 && !seen[u] ? atomicCAS(spill + ((hash32(ev[u]) >> 3) & Sm), -1, ev[u]) : 0;
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            if (r0 + u >= nb) break;
+                            const int32_t e = ev[u];
+                            bool fresh = e >= 0 && !seen[u] && ov[u] == -1;
+                            if (e >= 0 && !seen[u] && ov[u] != -1 && ov[u] != e) {
+                                uint32_t h = (hash32(e) >> 3) & Sm;
+                                for (uint32_t p = 1; p <= Sm; p++) {
+                                    h = (h + 1) & Sm;
+                                    const int32_t old = atomicCAS(spill + h, -1, e);
+                                    if (old == -1) { fresh = true; break; }
+                                    if (old == e) break;
+                                }
+                            }
+                            const unsigned fm = __ballot_sync(FULL, fresh);
+                            if (fresh) slot[ns + __popc(fm & lt_mask)] = e;
+                            const int nf = __popc(fm);
+                            ns += nf;
+                            n_dist += nf;
+                            scount += nf;
+                        }
+                    }
                 } else for (int r = 0; r < nb; r++) {
                     // switch to the global table before the shared one passes half full
                     if (!spilled && hcount + 32 > H / 2) {
