@@ -987,6 +987,7 @@ __host__ __device__ inline size_t refine_smem(int M1, int M2P, int R, int BM)
     size_t o = 0;
     o += (size_t)REF_CH * 9 * 4;            // vertex ids
     o += (size_t)REF_CH * 9 * 4 * BM;       // weights, per regression block
+    o = align_up(o, 16);                    // code rows are written 16 bytes at a time
     o += (size_t)REF_CH * 9 * M1;           // level-1 code rows
     o += (size_t)REF_CH * 9 * M2P;          // level-2 code rows (+ codeword id)
     o += (size_t)pow2_at_least(R) * 8;      // keys
@@ -1021,7 +1022,7 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
     const int RP = pow2_at_least(a.R);
     int32_t *vid = reinterpret_cast<int32_t *>(base);
     float *wt = reinterpret_cast<float *>(base + REF_CH * 9 * 4);       // [REF_CH][BM][9]
-    uint8_t *st1 = base + REF_CH * 9 * 4 * (1 + BM);
+    uint8_t *st1 = base + align_up((size_t)REF_CH * 9 * 4 * (1 + BM), 16);
     uint8_t *st2 = st1 + REF_CH * 9 * M1;
     uint64_t *keys = reinterpret_cast<uint64_t *>(st2 + REF_CH * 9 * M2P);
     const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
