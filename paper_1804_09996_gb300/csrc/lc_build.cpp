@@ -26,6 +26,8 @@
 #include <thread>
 #include <utility>
 
+#include <cuda_runtime.h>
+
 #include "lc_internal.h"
 
 namespace lc {
@@ -930,6 +932,15 @@ lc_status build_add(lc_index *ix, const float *x, int64_t n)
 {
     const lc_params &p = ix->p;
     int d = p.d, nt = n_threads(p);
+    if (p.build_gpu) {
+        // checked before the index is touched: a failed add leaves it as it was
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            set_error("build_gpu = 1 needs a CUDA device");
+            return LC_ERR_CUDA;
+        }
+    }
     ensure_build_state(ix);
     int64_t first = ix->n, total = first + n;
     std::vector<float> xr((size_t)n * d);

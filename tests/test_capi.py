@@ -209,3 +209,19 @@ def test_autotune_argument_errors_without_gpu(mix3k):
             assert e.value.status == lc.LC_ERR_ARG
     finally:
         lc.lc_free(h)
+
+
+def test_gpu_build_without_gpu_leaves_index_untouched():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = lc.lc_create(lc.lc_default_params(16, 16, 8, use_opq=0, kmeans_iters=2, build_gpu=1))
+    try:
+        rng = np.random.default_rng(0)
+        lc.lc_train(h, rng.standard_normal((400, 16)).astype(np.float32))
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_add(h, rng.standard_normal((50, 16)).astype(np.float32))
+        assert e.value.status == lc.LC_ERR_CUDA and "CUDA device" in e.value.message
+        assert lc.lc_size(h) == 0
+    finally:
+        lc.lc_free(h)
