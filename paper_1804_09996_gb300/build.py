@@ -52,7 +52,10 @@ def build(verbose: bool = False, force: bool = False) -> str:
                    "-c", src, "-o", obj]
         else:
             cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
-            cmd = ["g++", "-std=c++17", "-O3", "-fPIC", "-pthread", "-Wall", "-I", cuda_inc, "-c", src, "-o", obj]
+            # no multiply-add contraction: the host build gives the same bits on x86 and Arm, and
+            # the device codeword assignment reproduces it exactly
+            cmd = ["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fPIC", "-pthread", "-Wall", "-I", cuda_inc,
+                   "-c", src, "-o", obj]
         jobs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
     failed = []
     for cmd, pr in jobs:

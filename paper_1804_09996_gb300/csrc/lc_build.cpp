@@ -978,7 +978,12 @@ lc_status build_add(lc_index *ix, const float *x, int64_t n)
     lc_status rs = insert_range(ix, xr.data(), first, n, nt);
     if (rs != LC_OK) return rs;
     if (!ix->has_codebook) train_codebook(ix, xr.data(), first, n, nt);
-    assign_codewords(ix, xr.data(), first, n, nt);
+    if (p.build_gpu) {
+        rs = build_gpu_assign(ix, xr.data(), first, n);
+        if (rs != LC_OK) return rs;
+    } else {
+        assign_codewords(ix, xr.data(), first, n, nt);
+    }
     ix->dev_dirty = true;
     return LC_OK;
 }

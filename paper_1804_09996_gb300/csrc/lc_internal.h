@@ -84,6 +84,9 @@ lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, in
 // Re-sends level-0 rows of nodes0 [n0] and upper rows (indexes into upper_adj) rows_up [nu].
 lc_status build_gpu_rows(lc_index *ix, const int32_t *nodes0, int64_t n0, const int64_t *rows_up, int64_t nu);
 void build_gpu_end(lc_index *ix);
+// Codeword assignment of vectors [first, first + n) (rotated xr [n][d], host) on the device,
+// after the graph is final; writes ix->beta exactly as the host assignment would.
+lc_status build_gpu_assign(lc_index *ix, const float *xr, int64_t first, int64_t n);
 // Captured searches (lc_plan_*), lc_search.cu.
 lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype, int per_query_ef,
                       lc_plan **out);

@@ -2214,6 +2214,139 @@ lc_status build_gpu_rows(lc_index *ix, const int32_t *nodes0, int64_t n0, const 
     return scatter_rows(dv, dv->upper_adj, ix->upper_adj.data(), rows_up, nu);
 }
 
+// Codeword assignment on the device (Section 4.3): one thread per vector computes the normal
+// equations of each regression block over its coordinates in the host build's order (sums
+// over t ascending, double, multiply and add rounded separately as the host compiles them) and
+// takes the argmin over the block's codewords (first minimum), so the choice is the host's.
+struct AssignArgs {
+    const float *xr;                  // rotated vectors of this chunk [n][d]
+    int64_t first, n;                 // global id of row 0, rows
+    int d, M1, M2P, bM, bK;
+    const float *C1, *C2, *B;         // [256][d], [256][d], [bM][bK][9]
+    const uint8_t *codes1, *codes2b;
+    const int32_t *adj0;
+    uint8_t *beta_out;                // [n][bM]
+    uint8_t sub1[256], sub2[256];     // level-1 / level-2 sub-space of each coordinate
+    uint16_t boff[33];                // regression block m covers [boff[m], boff[m + 1])
+};
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+
+__global__ void __launch_bounds__(128) assign_kernel(const AssignArgs a)
+{
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.n) return;
+    const int64_t i = a.first + v;
+    int32_t vid[9];
+    vid[0] = (int32_t)i;
+    for (int j = 1; j <= 8; j++) vid[j] = __ldg(a.adj0 + i * DEG + j - 1);
+    const float *x = a.xr + v * a.d;
+    for (int m = 0; m < a.bM; m++) {
+        double A[45], b[9], xx = 0.0;
+        for (int u = 0; u < 45; u++) A[u] = 0.0;
+        for (int u = 0; u < 9; u++) b[u] = 0.0;
+        for (int t = a.boff[m]; t < a.boff[m + 1]; t++) {
+            // q(v) at coordinate t: level-1 plus level-2 centroid, added in FP32 as the host decodes
+            float g[9];
+#pragma unroll
+            for (int j = 0; j < 9; j++)
+                g[j] = vid[j] < 0 ? 0.f
+                       : __ldg(a.C1 + (int)__ldg(a.codes1 + (int64_t)vid[j] * a.M1 + a.sub1[t]) * a.d + t) +
+                             __ldg(a.C2 + (int)__ldg(a.codes2b + (int64_t)vid[j] * a.M2P + a.sub2[t]) * a.d + t);
+            const double xt = (double)__ldg(x + t);
+            int u = 0;
+#pragma unroll
+            for (int p = 0; p < 9; p++) {
+                if (vid[p] >= 0) b[p] = dadd(b[p], dmul((double)g[p], xt));
+#pragma unroll
+                for (int c = p; c < 9; c++, u++)
+                    if (vid[p] >= 0 && vid[c] >= 0) A[u] = dadd(A[u], dmul((double)g[p], (double)g[c]));
+            }
+            xx = dadd(xx, dmul(xt, xt));
+        }
+        int best = 0;
+        if (a.bK > 1) {
+            double bl = __longlong_as_double(0x7ff0000000000000ll);        // +inf
+            for (int cw = 0; cw < a.bK; cw++) {
+                const float *bw = a.B + ((int64_t)m * a.bK + cw) * 9;
+                double be[9];
+#pragma unroll
+                for (int p = 0; p < 9; p++) be[p] = (double)__ldg(bw + p);
+                // ||x - beta^T G||^2 = ||x||^2 - 2 beta.b + beta^T A beta, in the host's order
+                double sl = xx;
+                int u = 0;
+#pragma unroll
+                for (int p = 0; p < 9; p++) {
+                    sl = dsub(sl, dmul(dmul(2.0, be[p]), b[p]));
+                    sl = dadd(sl, dmul(dmul(be[p], be[p]), A[u]));
+                    u++;
+#pragma unroll
+                    for (int c = p + 1; c < 9; c++, u++) sl = dadd(sl, dmul(dmul(dmul(2.0, be[p]), be[c]), A[u]));
+                }
+                if (sl < bl) { bl = sl; best = cw; }
+            }
+        }
+        a.beta_out[v * a.bM + m] = (uint8_t)best;
+    }
+}
+
+lc_status build_gpu_assign(lc_index *ix, const float *xr, int64_t first, int64_t n)
+{
+    lc_status rs = LC_OK;
+    if (!ix->dev) {
+        rs = upload(ix);
+        if (rs != LC_OK) return rs;
+    }
+    DeviceIndex *dv = ix->dev;
+    const int d = ix->p.d, bM = ix->p.beta_M, bK = ix->p.beta_K;
+    if (!dupload(dv->B, ix->B)) {                   // trained after the graph
+        set_error("upload of the regression codebook failed");
+        return LC_ERR_OOM;
+    }
+    AssignArgs aa{};
+    aa.d = d; aa.M1 = ix->p.M1; aa.M2P = dv->M2P; aa.bM = bM; aa.bK = bK;
+    aa.C1 = dv->C1; aa.C2 = dv->C2; aa.B = dv->B;
+    aa.codes1 = dv->codes1; aa.codes2b = dv->codes2b; aa.adj0 = dv->adj0;
+    std::vector<int> o, l;
+    splits(d, ix->p.M1, o, l);
+    for (int j = 0; j < ix->p.M1; j++) for (int t = o[j]; t < o[j] + l[j]; t++) aa.sub1[t] = (uint8_t)j;
+    splits(d, ix->p.M2, o, l);
+    for (int j = 0; j < ix->p.M2; j++) for (int t = o[j]; t < o[j] + l[j]; t++) aa.sub2[t] = (uint8_t)j;
+    splits(d, bM, o, l);
+    for (int m = 0; m < bM; m++) aa.boff[m] = (uint16_t)o[m];
+    aa.boff[bM] = (uint16_t)d;
+    const int64_t CH = 1 << 20;                      // vectors per chunk
+    uint8_t *dbeta = nullptr;
+    size_t xcap = 0;
+    float *dx = nullptr;
+    if (cudaMalloc(&dbeta, (size_t)std::min(n, CH) * bM + 16) != cudaSuccess) {
+        set_error("cudaMalloc failed for codeword assignment");
+        return LC_ERR_OOM;
+    }
+    for (int64_t c0 = 0; c0 < n && rs == LC_OK; c0 += CH) {
+        const int64_t m = std::min(CH, n - c0);
+        if (!grow(dx, xcap, (size_t)m * d) ||
+            cudaMemcpy(dx, xr + c0 * d, sizeof(float) * m * d, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("upload for codeword assignment failed");
+            rs = LC_ERR_CUDA;
+            break;
+        }
+        aa.xr = dx; aa.first = first + c0; aa.n = m; aa.beta_out = dbeta;
+        assign_kernel<<<(unsigned)((m + 127) / 128), 128>>>(aa);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(ix->beta.data() + (first + c0) * bM, dbeta, (size_t)m * bM, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error("codeword assignment on the device failed: %s", cudaGetErrorString(cudaGetLastError()));
+            rs = LC_ERR_CUDA;
+        }
+    }
+    cfree(dx);
+    cfree(dbeta);
+    ix->dev_dirty = true;
+    return rs;
+}
+
 void build_gpu_end(lc_index *ix)
 {
     DeviceIndex *dv = ix->dev;

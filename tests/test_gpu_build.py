@@ -60,6 +60,48 @@ def test_device_built_graph_is_well_formed(builds):
     assert same > 0.3
 
 
+def test_device_codeword_assignment_is_the_hosts(builds):
+    # the device assignment reproduces the host's arithmetic: wherever a vector's G(x) (its
+    # first eight neighbours) is the same in both builds, so is its codeword
+    hg, ixg, _ = builds[1]
+    hh, ixh, _ = builds[0]
+    assert np.array_equal(ixg.B, ixh.B) or not np.array_equal(ixg.adj0, ixh.adj0)
+    same_g = (ixg.adj0[:, :8] == ixh.adj0[:, :8]).all(1)
+    assert same_g.mean() > 0.3
+    if np.array_equal(ixg.B, ixh.B):
+        assert np.array_equal(ixg.beta[same_g], ixh.beta[same_g])
+
+
+@pytest.mark.parametrize("bM,bK", [(4, 16), (3, 1)])
+def test_device_assignment_product_codebook(bM, bK):
+    from oracle import refine
+    d, M1, M2, n = 48, 16, 16, 2000
+    xt = dg.gaussian_mixture(3000, d, 32, stream=dg.STREAM_TRAIN)
+    xb = dg.gaussian_mixture(n, d, 32, stream=dg.STREAM_BASE)
+    out = []
+    for g in (0, 1):
+        h = lc.lc_create(lc.lc_default_params(d, M1, M2, use_opq=0, kmeans_iters=6, beta_M=bM, beta_K=bK,
+                                              beta_iters=3, beta_train_n=n, build_gpu=g))
+        try:
+            lc.lc_train(h, xt)
+            lc.lc_add(h, xb)
+            out.append(lc.lc_export(h, d, M1, M2, bM, bK))
+        finally:
+            lc.lc_free(h)
+    same_g = (out[0]["adj0"][:, :8] == out[1]["adj0"][:, :8]).all(1)
+    if np.array_equal(out[0]["B"], out[1]["B"]):
+        assert np.array_equal(out[0]["beta"][same_g], out[1]["beta"][same_g])
+    # and every device choice is the blockwise argmin under the device build's own codebooks
+    ex = out[1]
+    xr = xb.astype(np.float64) @ ex["R"].astype(np.float64).T
+    from oracle import codec
+    xh = codec.pq_decode(ex["codes1"], ex["C1"].astype(np.float64), M1) + \
+        codec.pq_decode(ex["codes2"], ex["C2"].astype(np.float64), M2)
+    G = refine.gmatrix(xh, ex["adj0"], np.arange(n))
+    best = refine.assign_product(G, xr, ex["B"].astype(np.float64))
+    assert (best == ex["beta"]).mean() > 0.98
+
+
 def test_device_built_graph_searches_as_well(builds):
     xq = dg.gaussian_mixture(500, 96, 128, stream=dg.STREAM_QUERY)
     gt, _ = oracle.knn(builds[0][2], xq, 1)
