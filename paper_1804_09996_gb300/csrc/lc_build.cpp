@@ -586,8 +586,8 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
     }
     const int efc = p.ef_construction;
     std::vector<int64_t> gmem;                  // batch members searched on the device
-    std::vector<int32_t> gslot, gids;           // member -> row of the device results
-    std::vector<float> gxr, gd;
+    std::vector<int32_t> gslot, gsel;           // member -> row of the device selections
+    std::vector<float> gxr;
     int64_t done = 0;
     while (done < count) {
         int64_t ncur = first + done;
@@ -610,9 +610,8 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
             gxr.resize((size_t)m * p.d);
             for (int64_t i = 0; i < m; i++)
                 std::memcpy(gxr.data() + i * p.d, xr + (ncur + gmem[i] - first) * p.d, sizeof(float) * p.d);
-            gids.resize((size_t)m * efc);
-            gd.resize((size_t)m * efc);
-            lc_status rs = build_gpu_search(ix, gxr.data(), m, efc, ep0, ml0, gids.data(), gd.data());
+            gsel.resize((size_t)m * (DEG + 1));
+            lc_status rs = build_gpu_search(ix, gxr.data(), m, efc, ep0, ml0, nullptr, nullptr, gsel.data());
             if (rs != LC_OK) { build_gpu_end(ix); return rs; }
         }
         parallel_for(b, nt, 8, [&](int64_t a, int64_t e, int t) {
@@ -625,13 +624,8 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
                 sel[u].assign((size_t)(top + 1) * (DEG + 1), -1);
                 if (ep0 < 0) continue;
                 if (gslot[u] >= 0) {
-                    // level 0 searched on the device: its result list, sorted by (distance, id)
-                    const int32_t *gi = gids.data() + (size_t)gslot[u] * efc;
-                    const float *gv = gd.data() + (size_t)gslot[u] * efc;
-                    st.W.clear();
-                    for (int i = 0; i < efc && gi[i] >= 0; i++) st.W.push_back(Key{gv[i], gi[i]});
-                    int32_t *out = sel[u].data();
-                    out[DEG] = heuristic(g, st.W.data(), (int)st.W.size(), DEG, out);
+                    // level 0 searched and its neighbours selected on the device
+                    std::memcpy(sel[u].data(), gsel.data() + (size_t)gslot[u] * (DEG + 1), sizeof(int32_t) * (DEG + 1));
                     continue;
                 }
                 int32_t cur = ep0;

@@ -44,6 +44,7 @@ struct DeviceIndex {
     float *b_d = nullptr; size_t b_d_cap = 0;
     int32_t *b_rows = nullptr; size_t b_rows_cap = 0;
     int64_t *b_idx = nullptr; size_t b_idx_cap = 0;
+    int32_t *b_sel = nullptr; size_t b_sel_cap = 0;
 };
 
 // Launch configuration of one search and the scratch it needs.

@@ -78,9 +78,10 @@ lc_status autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, c
 // the level-0 insertion searches of each batch; rows changed by a batch are re-sent.
 lc_status build_gpu_begin(lc_index *ix);
 // m rotated vectors xr [m][d] (host) search level 0 from ep after a greedy descent of levels
-// max_level..1, keeping efc: ids/dists [m][efc] (host, sorted by (distance, id), -1 padded).
+// max_level..1, keeping efc: ids/dists [m][efc] (host, sorted by (distance, id), -1 padded);
+// or, with sel non-NULL, the neighbour selection of each: sel [m][DEG + 1] (ids, then count).
 lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, int32_t ep, int max_level,
-                           int32_t *ids, float *dists);
+                           int32_t *ids, float *dists, int32_t *sel = nullptr);
 // Re-sends level-0 rows of nodes0 [n0] and upper rows (indexes into upper_adj) rows_up [nu].
 lc_status build_gpu_rows(lc_index *ix, const int32_t *nodes0, int64_t n0, const int64_t *rows_up, int64_t nu);
 void build_gpu_end(lc_index *ix);

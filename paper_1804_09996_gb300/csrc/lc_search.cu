@@ -53,7 +53,7 @@ void device_free(DeviceIndex *dv)
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
-    cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx);
+    cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx); cfree(dv->b_sel);
     cfree(dv->q_st); cfree(dv->ef_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
     for (auto &e : dv->ev) if (e) cudaEventDestroy(e);
     if (cur >= 0) cudaSetDevice(cur);
@@ -2131,6 +2131,72 @@ __global__ void scatter_rows_kernel(int32_t *dst, const int64_t *idx, const int3
         dst[idx[i / DEG] * DEG + (i % DEG)] = rows[i];
 }
 
+// Neighbour selection of the GPU-assisted build: HNSW's shrinking heuristic on each member's
+// candidate list (sorted by distance to the member): a candidate is kept unless it is closer to
+// an already kept neighbour than to the member, up to DEG kept.  One warp per member; lane u
+// tests the candidate against the u-th kept neighbour.  The decoded-to-decoded distance
+// reproduces the host build's float arithmetic (eight partial sums over coordinate groups,
+// then a fixed tree; no multiply-add contraction), so the choices are the host's.
+struct SelectArgs {
+    const int32_t *cand_ids;          // [m][efc], -1 padded
+    const float *cand_d;              // [m][efc]
+    int32_t *sel;                     // [m][DEG + 1]: kept ids, then their count
+    int64_t m;
+    int efc, d, M1, M2P;
+    const float *C1, *C2;
+    const uint8_t *codes1, *codes2b;
+    uint8_t sub1[256], sub2[256];
+};
+
+__device__ __forceinline__ float decoded_at(const SelectArgs &a, int32_t v, int t)
+{
+    return __fadd_rn(__ldg(a.C1 + (int)__ldg(a.codes1 + (int64_t)v * a.M1 + a.sub1[t]) * a.d + t),
+                     __ldg(a.C2 + (int)__ldg(a.codes2b + (int64_t)v * a.M2P + a.sub2[t]) * a.d + t));
+}
+
+__device__ float decoded_l2(const SelectArgs &a, int32_t p, int32_t q)
+{
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int t = 0;
+    for (; t + 8 <= a.d; t += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const float x = __fsub_rn(decoded_at(a, p, t + u), decoded_at(a, q, t + u));
+            s[u] = __fadd_rn(s[u], __fmul_rn(x, x));
+        }
+    }
+    for (; t < a.d; t++) {
+        const float x = __fsub_rn(decoded_at(a, p, t), decoded_at(a, q, t));
+        s[0] = __fadd_rn(s[0], __fmul_rn(x, x));
+    }
+    return __fadd_rn(__fadd_rn(__fadd_rn(s[0], s[1]), __fadd_rn(s[2], s[3])),
+                     __fadd_rn(__fadd_rn(s[4], s[5]), __fadd_rn(s[6], s[7])));
+}
+
+__global__ void __launch_bounds__(256) select_kernel(const SelectArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t mi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (mi >= a.m) return;                               // whole warps leave together
+    const int32_t *ci = a.cand_ids + mi * a.efc;
+    const float *cd = a.cand_d + mi * a.efc;
+    int kept = 0;
+    int32_t kid = -1;                                    // lane u: the u-th kept neighbour
+    for (int s = 0; s < a.efc && kept < DEG; s++) {
+        const int32_t c = __ldg(ci + s);
+        if (c < 0) break;
+        const float dc = __ldg(cd + s);
+        const bool closer = lane < kept && decoded_l2(a, c, kid) < dc;
+        if (__ballot_sync(FULL, closer) == 0) {
+            if (lane == kept) kid = c;
+            kept++;
+        }
+    }
+    int32_t *out = a.sel + mi * (DEG + 1);
+    out[lane] = lane < kept ? kid : -1;
+    if (lane == 0) out[DEG] = kept;
+}
+
 lc_status build_gpu_begin(lc_index *ix)
 {
     ix->dev_dirty = true;                       // upload the index as it stands (codes of all nodes)
@@ -2138,7 +2204,7 @@ lc_status build_gpu_begin(lc_index *ix)
 }
 
 lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, int32_t ep, int max_level,
-                           int32_t *ids, float *dists)
+                           int32_t *ids, float *dists, int32_t *sel)
 {
     DeviceIndex *dv = ix->dev;
     if (!dv || m <= 0) return LC_OK;
@@ -2168,9 +2234,30 @@ lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, in
     rs = run_search(dv, P, nullptr, m, dv->b_ids, dv->b_d, nullptr, sc, 0, false, nullptr, nullptr, true);
     if (rs != LC_OK) return rs;
     int32_t status = 0;
-    if (cudaMemcpy(ids, dv->b_ids, sizeof(int32_t) * m * efc, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(dists, dv->b_d, sizeof(float) * m * efc, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(&status, dv->status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    bool ok;
+    if (sel) {
+        // neighbour selection on the device; only the selections come back
+        if (!grow(dv->b_sel, dv->b_sel_cap, (size_t)m * (DEG + 1))) {
+            set_error("cudaMalloc failed for the build's selections");
+            return LC_ERR_OOM;
+        }
+        SelectArgs sa{};
+        sa.cand_ids = dv->b_ids; sa.cand_d = dv->b_d; sa.sel = dv->b_sel; sa.m = m; sa.efc = efc;
+        sa.d = dv->d; sa.M1 = dv->M1; sa.M2P = dv->M2P; sa.C1 = dv->C1; sa.C2 = dv->C2;
+        sa.codes1 = dv->codes1; sa.codes2b = dv->codes2b;
+        std::vector<int> o, l;
+        splits(dv->d, dv->M1, o, l);
+        for (int j = 0; j < dv->M1; j++) for (int t = o[j]; t < o[j] + l[j]; t++) sa.sub1[t] = (uint8_t)j;
+        splits(dv->d, dv->M2, o, l);
+        for (int j = 0; j < dv->M2; j++) for (int t = o[j]; t < o[j] + l[j]; t++) sa.sub2[t] = (uint8_t)j;
+        select_kernel<<<(unsigned)((m * 32 + 255) / 256), 256>>>(sa);
+        ok = cudaGetLastError() == cudaSuccess &&
+             cudaMemcpy(sel, dv->b_sel, sizeof(int32_t) * m * (DEG + 1), cudaMemcpyDeviceToHost) == cudaSuccess;
+    } else {
+        ok = cudaMemcpy(ids, dv->b_ids, sizeof(int32_t) * m * efc, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             cudaMemcpy(dists, dv->b_d, sizeof(float) * m * efc, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    if (!ok || cudaMemcpy(&status, dv->status, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
         set_error("build search failed: %s", cudaGetErrorString(cudaGetLastError()));
         return LC_ERR_CUDA;
     }
@@ -2352,9 +2439,10 @@ void build_gpu_end(lc_index *ix)
     DeviceIndex *dv = ix->dev;
     if (dv) {
         cudaDeviceSynchronize();
-        cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx);
+        cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx); cfree(dv->b_sel);
         dv->b_yq = nullptr; dv->b_ids = nullptr; dv->b_d = nullptr; dv->b_rows = nullptr; dv->b_idx = nullptr;
-        dv->b_yq_cap = dv->b_ids_cap = dv->b_d_cap = dv->b_rows_cap = dv->b_idx_cap = 0;
+        dv->b_sel = nullptr;
+        dv->b_yq_cap = dv->b_ids_cap = dv->b_d_cap = dv->b_rows_cap = dv->b_idx_cap = dv->b_sel_cap = 0;
     }
     ix->dev_dirty = true;                       // codewords are assigned after the graph
 }

@@ -57,7 +57,8 @@ def test_device_built_graph_is_well_formed(builds):
     assert np.array_equal(ix.codes1, host.codes1) and np.array_equal(ix.levels, host.levels)
     same = np.mean([set(a[a >= 0]) == set(b[b >= 0]) for a, b in zip(ix.adj0, host.adj0)])
     print(f"level-0 rows identical to the host build: {same:.1%}")
-    assert same > 0.3
+    # the device searches and selections reproduce the host's choices except near-ties
+    assert same > 0.95
 
 
 def test_device_codeword_assignment_is_the_hosts(builds):
