@@ -77,8 +77,11 @@ def peaks():
 
 
 def kernel_hash():
-    src = os.path.join(ROOT, "paper_1804_09996_gb300", "csrc", "lc_search.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the device sources (the search kernels and their headers)."""
+    h = hashlib.sha256()
+    for f in ("lc_walk.cuh", "lc_walk_f32.cu", "lc_walk_f16.cu", "lc_search.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1804_09996_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic(workload: str, form: str):

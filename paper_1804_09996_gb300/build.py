@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "liblc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU = ["lc_search.cu"]
+CU = ["lc_search.cu", "lc_walk_f32.cu", "lc_walk_f16.cu"]
 CPP = ["lc_capi.cpp", "lc_build.cpp", "lc_serve.cpp", "lc_tune.cpp"]
 
 
@@ -30,7 +30,7 @@ def _nvcc() -> str:
 
 
 def _deps():
-    hdrs = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".h")]
+    hdrs = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))]
     hdrs.append(os.path.join(INCLUDE, "lc.h"))
     return max(os.path.getmtime(h) for h in hdrs)
 
