@@ -938,7 +938,19 @@ lc_status build_add(lc_index *ix, const float *x, int64_t n)
     ensure_build_state(ix);
     int64_t first = ix->n, total = first + n;
     std::vector<float> xr((size_t)n * d);
-    rotate(x, n, d, ix->R.data(), xr.data(), nt);
+    std::vector<uint8_t> nc1((size_t)n * p.M1), nc2((size_t)n * p.M2);
+    if (p.build_gpu) {
+        // rotation and both code levels on the device (the host's arithmetic, the host's codes)
+        lc_status rs = build_gpu_encode(ix, x, n, xr.data(), nc1.data(), nc2.data());
+        if (rs != LC_OK) return rs;
+    } else {
+        rotate(x, n, d, ix->R.data(), xr.data(), nt);
+        std::vector<float> xh1((size_t)n * d);
+        pq_encode(xr.data(), n, d, p.M1, ix->C1.data(), nc1.data(), nt);
+        pq_decode(nc1.data(), n, d, p.M1, ix->C1.data(), xh1.data(), false, nt);
+        for (size_t i = 0; i < xh1.size(); i++) xh1[i] = xr[i] - xh1[i];       // the residual
+        pq_encode(xh1.data(), n, d, p.M2, ix->C2.data(), nc2.data(), nt);
+    }
     ix->codes1.resize((size_t)total * p.M1);
     ix->codes2.resize((size_t)total * p.M2);
     ix->beta.resize((size_t)total * p.beta_M, 0);
@@ -946,13 +958,9 @@ lc_status build_add(lc_index *ix, const float *x, int64_t n)
     uint8_t *c1 = ix->codes1.data() + first * p.M1;
     uint8_t *c2 = ix->codes2.data() + first * p.M2;
     float *xh = ix->xh.data() + first * d;
-    pq_encode(xr.data(), n, d, p.M1, ix->C1.data(), c1, nt);
+    std::memcpy(c1, nc1.data(), nc1.size());
+    std::memcpy(c2, nc2.data(), nc2.size());
     pq_decode(c1, n, d, p.M1, ix->C1.data(), xh, false, nt);
-    {
-        std::vector<float> res((size_t)n * d);
-        for (size_t i = 0; i < res.size(); i++) res[i] = xr[i] - xh[i];
-        pq_encode(res.data(), n, d, p.M2, ix->C2.data(), c2, nt);
-    }
     pq_decode(c2, n, d, p.M2, ix->C2.data(), xh, true, nt);
     // levels and row storage
     ix->levels.resize(total);

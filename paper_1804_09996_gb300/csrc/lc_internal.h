@@ -88,6 +88,9 @@ void build_gpu_end(lc_index *ix);
 // Codeword assignment of vectors [first, first + n) (rotated xr [n][d], host) on the device,
 // after the graph is final; writes ix->beta exactly as the host assignment would.
 lc_status build_gpu_assign(lc_index *ix, const float *xr, int64_t first, int64_t n);
+// Rotation and two-level encoding of x [n][d] (host) on the device, with the host build's
+// arithmetic: xr [n][d], codes c1 [n][M1], c2 [n][M2] (host).
+lc_status build_gpu_encode(lc_index *ix, const float *x, int64_t n, float *xr, uint8_t *c1, uint8_t *c2);
 // Captured searches (lc_plan_*), lc_search.cu.
 lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, int qtype, int per_query_ef,
                       lc_plan **out);

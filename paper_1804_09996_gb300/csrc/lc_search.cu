@@ -1480,6 +1480,118 @@ lc_status build_gpu_assign(lc_index *ix, const float *xr, int64_t first, int64_t
     return rs;
 }
 
+// Encoding of the vectors being added (rotation, level-1 PQ, residual, level-2 PQ), in the host
+// build's float arithmetic (the rotation sums R[t][u] x_u over u in order; each centroid's
+// score is ||c||^2 plus (-2 x_t) c_t over t in order; the first minimum wins; no multiply-add
+// contraction), so the codes are the host's.
+__global__ void rotate_exact_kernel(const float *X, int64_t n, int d, const float *RT, float *Y)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * d; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / d;
+        const int t = (int)(e - i * d);
+        const float *x = X + i * d;
+        float y = 0.f;
+        for (int u = 0; u < d; u++) y = __fadd_rn(y, __fmul_rn(__ldg(RT + (int64_t)u * d + t), __ldg(x + u)));
+        Y[e] = y;
+    }
+}
+
+// codes[i][j] = argmin_c cn[j][c] + sum_t (-2 x_t) C[c][t] over sub-space j; with sub != nullptr
+// the encoded vector is X minus its level-1 decode (the residual)
+__global__ void pq_encode_kernel(const float *X, int64_t n, int d, int M, const uint16_t *off, const uint8_t *len,
+                                 const float *C, const float *cn, uint8_t *codes, const float *C1, int M1,
+                                 const uint8_t *codes1, const uint8_t *sub1)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * M; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / M;
+        const int j = (int)(e - i * M), o = off[j], L = len[j];
+        float m2x[16];
+        for (int t = 0; t < L; t++) {
+            float x = __ldg(X + i * d + o + t);
+            if (codes1) x = __fsub_rn(x, __ldg(C1 + (int)codes1[i * M1 + sub1[o + t]] * d + o + t));
+            m2x[t] = -2.f * x;
+        }
+        int best = 0;
+        float bv = 0.f;
+        for (int c = 0; c < 256; c++) {
+            float acc = __ldg(cn + j * 256 + c);
+            for (int t = 0; t < L; t++) acc = __fadd_rn(acc, __fmul_rn(m2x[t], __ldg(C + c * d + o + t)));
+            if (c == 0 || acc < bv) { bv = acc; best = c; }
+        }
+        codes[e] = (uint8_t)best;
+    }
+}
+
+lc_status build_gpu_encode(lc_index *ix, const float *x, int64_t n, float *xr, uint8_t *c1, uint8_t *c2)
+{
+    const int d = ix->p.d, M1 = ix->p.M1, M2 = ix->p.M2;
+    std::vector<int> o1, l1, o2, l2;
+    splits(d, M1, o1, l1);
+    splits(d, M2, o2, l2);
+    for (int j = 0; j < M2; j++)
+        if (l2[j] > 16 || (j < M1 && l1[j] > 16)) {
+            set_error("device encoding needs sub-spaces of at most 16 dimensions");
+            return LC_ERR_ARG;
+        }
+    // transposed rotation and squared centroid norms exactly as the host computes them
+    std::vector<float> RT((size_t)d * d), cn1((size_t)M1 * 256, 0.f), cn2((size_t)M2 * 256, 0.f);
+    for (int t = 0; t < d; t++)
+        for (int u = 0; u < d; u++) RT[(size_t)u * d + t] = ix->R[(size_t)t * d + u];
+    auto norms = [&](const std::vector<float> &C, int M, const std::vector<int> &o, const std::vector<int> &l,
+                     std::vector<float> &cn) {
+        for (int j = 0; j < M; j++)
+            for (int c = 0; c < 256; c++)
+                for (int t = 0; t < l[j]; t++) {
+                    const float v = C[(size_t)c * d + o[j] + t];
+                    cn[(size_t)j * 256 + c] += v * v;
+                }
+    };
+    norms(ix->C1, M1, o1, l1, cn1);
+    norms(ix->C2, M2, o2, l2, cn2);
+    std::vector<uint16_t> off1(o1.begin(), o1.end()), off2(o2.begin(), o2.end());
+    std::vector<uint8_t> len1(l1.begin(), l1.end()), len2(l2.begin(), l2.end()), sub1(d);
+    for (int j = 0; j < M1; j++) for (int t = o1[j]; t < o1[j] + l1[j]; t++) sub1[t] = (uint8_t)j;
+    float *dRT = nullptr, *dC1 = nullptr, *dC2 = nullptr, *dcn1 = nullptr, *dcn2 = nullptr, *dX = nullptr, *dY = nullptr;
+    uint16_t *doff1 = nullptr, *doff2 = nullptr;
+    uint8_t *dlen1 = nullptr, *dlen2 = nullptr, *dsub1 = nullptr, *dc1 = nullptr, *dc2 = nullptr;
+    const int64_t CH = std::min<int64_t>(n, 1 << 20);
+    bool ok = dupload(dRT, RT) && dupload(dC1, ix->C1) && dupload(dC2, ix->C2) && dupload(dcn1, cn1) &&
+              dupload(dcn2, cn2) && dupload(doff1, off1) && dupload(doff2, off2) && dupload(dlen1, len1) &&
+              dupload(dlen2, len2) && dupload(dsub1, sub1) &&
+              cudaMalloc(&dX, sizeof(float) * CH * d + 16) == cudaSuccess &&
+              cudaMalloc(&dY, sizeof(float) * CH * d + 16) == cudaSuccess &&
+              cudaMalloc(&dc1, (size_t)CH * M1 + 16) == cudaSuccess && cudaMalloc(&dc2, (size_t)CH * M2 + 16) == cudaSuccess;
+    lc_status rs = LC_OK;
+    if (!ok) {
+        set_error("device allocation for encoding failed");
+        rs = LC_ERR_OOM;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, sms) * 8;
+    for (int64_t a = 0; a < n && rs == LC_OK; a += CH) {
+        const int64_t m = std::min(CH, n - a);
+        if (cudaMemcpy(dX, x + a * d, sizeof(float) * m * d, cudaMemcpyHostToDevice) != cudaSuccess) {
+            rs = LC_ERR_CUDA;
+            break;
+        }
+        rotate_exact_kernel<<<grid, 256>>>(dX, m, d, dRT, dY);
+        pq_encode_kernel<<<grid, 256>>>(dY, m, d, M1, doff1, dlen1, dC1, dcn1, dc1, nullptr, 0, nullptr, nullptr);
+        pq_encode_kernel<<<grid, 256>>>(dY, m, d, M2, doff2, dlen2, dC2, dcn2, dc2, dC1, M1, dc1, dsub1);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(xr + a * d, dY, sizeof(float) * m * d, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(c1 + a * M1, dc1, (size_t)m * M1, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(c2 + a * M2, dc2, (size_t)m * M2, cudaMemcpyDeviceToHost) != cudaSuccess)
+            rs = LC_ERR_CUDA;
+    }
+    if (rs == LC_ERR_CUDA) set_error("encoding on the device failed: %s", cudaGetErrorString(cudaGetLastError()));
+    for (void *p : {(void *)dRT, (void *)dC1, (void *)dC2, (void *)dcn1, (void *)dcn2, (void *)dX, (void *)dY,
+                    (void *)doff1, (void *)doff2, (void *)dlen1, (void *)dlen2, (void *)dsub1, (void *)dc1, (void *)dc2})
+        cfree(p);
+    return rs;
+}
+
 void build_gpu_end(lc_index *ix)
 {
     DeviceIndex *dv = ix->dev;

@@ -1,6 +1,7 @@
-"""GPU-assisted build (lc_params.build_gpu): lc_add runs the level-0 insertion searches of each
-batch on the device (the batch searches the graph as it stood at its start, Section 5.1) and
-keeps neighbour selection and linking on the host.  The FP32 device distances may order
+"""GPU-assisted build (lc_params.build_gpu): lc_add encodes on the device, runs the level-0
+insertion searches and neighbour selections of each batch on the device (the batch searches the
+graph as it stood at its start, Section 5.1), keeps back-links on the host, and assigns the
+codewords on the device.  The FP32 device distances may order
 near-equal candidates differently from the host build, so the graphs are not bit-identical;
 the checks are the structural invariants of the host build's graph, search quality equal to
 the host build's, and search parity against the oracle on the device-built index."""
@@ -53,8 +54,9 @@ def test_device_built_graph_is_well_formed(builds):
     h, ix, xb = builds[1]
     check_structure(ix)
     host = builds[0][1]
-    # same codec and levels: only the graph may differ
-    assert np.array_equal(ix.codes1, host.codes1) and np.array_equal(ix.levels, host.levels)
+    # the device encodes with the host's arithmetic: the same codes at both levels, the same levels
+    assert np.array_equal(ix.codes1, host.codes1) and np.array_equal(ix.codes2, host.codes2)
+    assert np.array_equal(ix.levels, host.levels)
     same = np.mean([set(a[a >= 0]) == set(b[b >= 0]) for a, b in zip(ix.adj0, host.adj0)])
     print(f"level-0 rows identical to the host build: {same:.1%}")
     # the device searches and selections reproduce the host's choices except near-ties
