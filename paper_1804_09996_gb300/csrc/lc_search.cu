@@ -1,31 +1,21 @@
-// GPU search path of Link and Code (Douze, Sablayrolles, Jegou, CVPR 2018), sm_103a.
+// GPU search path of Link and Code (Douze, Sablayrolles, Jegou, CVPR 2018), sm_103a: the
+// host side of a search and the kernels other than the walk (which is in lc_walk.cuh).
 //
-// walk_kernel  (one warp per query; persistent CTAs take queries from an atomic counter)
-//   - rotation y' = R y; the walk distance is the ADC distance ||y' - c1(x)||^2 of Section
-//     4.1 ("asymmetric distance computations"): the sum over level-1 sub-spaces j of
-//     ||y'^j - C1_j[c_j]||^2, each term computed in FP32 from the codebook C1, which every
-//     CTA keeps once in shared memory (a per-query table of the same terms would cost
-//     32-64 KB of shared memory per query in flight);
-//   - greedy descent of the upper HNSW levels (Section 2);
-//   - best-first search of level 0 with result set W of size ef' (Section 2), kept as a
-//     sorted list of (distance, id) keys with an "expanded" flag: each step expands the best
-//     unexpanded member of W, scores all its unvisited neighbours at once (one per lane)
-//     and merges them into W keeping the ef' best.  This expands exactly the nodes, in
-//     exactly the order, of the two-set formulation (candidate heap C + result heap W);
-//   - exact visited set: open-addressing hash in shared memory, spilling to a per-warp
-//     table in global memory when it fills;
-//   - writes the shortlist (the R best of W, Section 4.1 two-stage search) or, without
-//     refinement, the top-k directly.
-// refine_kernel (one warp per query)
-//   - for each shortlisted x: G(x) = [q(x), q(g_1..g_8)] decoded from both code levels,
-//     y^ = beta_b^T G(x) with b the vector's codeword (Section 4.3), exact squared L2 to
-//     y', and the final top-k by (distance, id).
+// rotate_kernel  y' = R y for a batch of queries (OPQ rotation, Section 3.3 / 5.1).
+// walk           lc_walk.cuh / lc_walk_f32.cu / lc_walk_f16.cu: upper-level descent and level-0
+//                search (Section 2) scored by ADC on the level-1 code (Section 4.1).
+// refine_kernel  (one warp per query) for each shortlisted x: G(x) = [q(x), q(g_1..g_8)]
+//                decoded from both code levels, y^ = beta_b^T G(x) with b the vector's codeword
+//                (per block with a product codebook; Section 4.2, 4.3), exact squared L2 to
+//                y', and the final top-k by (distance, id).
+// merge_kernel   top-k merge of per-shard results (sharded search).
+// Host side      device copy of the index (upload), launch planning (plan_search), one search
+//                (run_search / search), captured plans (lc_plan_*), the GPU-assisted build
+//                (encoding, insertion searches and neighbour selection, row re-sends, codeword
+//                assignment), the walk without allocation, and kernel timing.
 //
-// FP32 walk distance: lane l holds the term of sub-space l (M1 = 32), of l mod 16 (M1 = 16)
-// or the sum of sub-spaces l and l + 32 (M1 = 64), each term summed over its coordinates in
-// order; the 32 lane values are added pairwise, lanes differing in bit 3 first, then bits 2,
-// 1, 0 and 4.  The order is the same for every node, so a node's distance does not depend on
-// where or with how many others it is scored.
+// Ordering everywhere is by (distance, id), smaller id first on equal distances.
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 

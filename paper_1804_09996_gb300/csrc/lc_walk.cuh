@@ -2,6 +2,31 @@
 // lc_walk_f32.cu / lc_walk_f16.cu and by lc_search.cu): kernel arguments, shared-memory
 // layouts, the scoring helpers and the walk kernel template, and the host templates that
 // configure and launch one instantiation.  Not part of the ABI.
+//
+// walk_kernel (one warp per query; persistent CTAs take queries from an atomic counter)
+//   - y' = R y from the rotation kernel (or rotated here, for the walk without allocation);
+//   - the walk distance is the ADC distance ||y' - c1(x)||^2 of Section 4.1: the sum over
+//     level-1 sub-spaces j of ||y'^j - C1_j[c_j]||^2, each term computed in FP32 from the
+//     codebook C1, which every CTA keeps once in shared memory (a per-query table of the same
+//     terms would cost 32-64 KB of shared memory per query in flight); with FQ the distance is
+//     to the full two-level decode c1 + c2;
+//   - greedy descent of the upper HNSW levels, then best-first search of level 0 with result
+//     set W of size ef' (Section 2), in one loop with a single scoring call site.  W is a
+//     sorted list of (distance, id) keys with an "expanded" flag: each step expands the best
+//     unexpanded member (or the `beam` best) of W, scores all their unvisited neighbours at
+//     once (one per lane) and merges them into W keeping the ef' best.  With one expansion
+//     per step this expands exactly the nodes, in exactly the order, of the two-set
+//     formulation (candidate heap C + result heap W);
+//   - exact visited set: open-addressing hash in shared memory, spilling to a per-warp table
+//     in global memory when it fills;
+//   - writes the shortlist (the R best of W, Section 4.1 two-stage search) or, without
+//     refinement, the top-k directly.
+//
+// FP32 walk distance: lane l holds the term of sub-space l (M1 = 32), of l mod 16 (M1 = 16)
+// or the sum of sub-spaces l and l + 32 (M1 = 64), each term summed over its coordinates in
+// order; the 32 lane values are added pairwise, lanes differing in bit 3 first, then bits 2,
+// 1, 0 and 4.  The order is the same for every node, so a node's distance does not depend on
+// where or with how many others it is scored.
 #pragma once
 
 #include <cuda_fp16.h>
