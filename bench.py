@@ -148,6 +148,11 @@ WORKLOADS = {
                    M1=32, M2=31, opq=1,
                    desc="10M x 96-d Gaussian-mixture (1024 centres), OPQ32 + residual PQ31 + 1 B codeword "
                         "= 64 B/vector, degree 32, 10k queries/step (the serving workload's index)"),
+    "mix50m": dict(kind="mixture", n_base=50_000_000, n_train=500_000, n_query=1_000_000, d=96, centres=4096,
+                   M1=32, M2=31, opq=1, gt_sample=10_000,
+                   desc="50M x 96-d Gaussian-mixture (4096 centres), OPQ32 + residual PQ31 + 1 B codeword "
+                        "= 64 B/vector (3.2 GB) + degree-32 graph (6.4 GB) resident, 1M queries/step; recall "
+                        "on the first 10k queries against exact search"),
     "mix10k": dict(kind="mixture", n_base=10_000, n_train=10_000, n_query=1_000, d=96, centres=64, M1=16,
                    M2=16, opq=0,
                    desc="10k x 96-d Gaussian-mixture (64 centres), PQ16 + residual PQ16 + 1 B codeword, "
