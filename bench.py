@@ -298,7 +298,7 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
             done[rid] = (time.perf_counter(), st, None if i is None else i[:, 0].copy())
 
         n_req = 120
-        starts = [(j * 512) % (len(xq) - 512) for j in range(n_req)]
+        starts = [(j * 512) % (min(len(xq), len(gt)) - 512) for j in range(n_req)]   # queries with exact neighbours
         t0 = time.perf_counter()
         ids = []
         for j in range(n_req):
