@@ -207,7 +207,10 @@ lc_status lc_export(const lc_index *ix, float *R, float *C1, float *C2, uint8_t 
                     int32_t *upper_adj, int32_t *ep);
 
 /* Writes the index to a file (versioned binary format) / reads one into a new handle.
- * Errors: LC_ERR_IO, LC_ERR_STATE (save of an untrained index), LC_ERR_OOM. */
+ * lc_load checks the file as lc_import checks its arguments, and also that the stored count
+ * of upper rows equals the sum of the levels and that nothing follows the last array; any
+ * failure leaves *out NULL.  Errors: LC_ERR_IO (unreadable, truncated, inconsistent or
+ * invalid file), LC_ERR_STATE (save of an untrained index), LC_ERR_OOM. */
 lc_status lc_save(const lc_index *ix, const char *path);
 lc_status lc_load(const char *path, lc_index **out);
 

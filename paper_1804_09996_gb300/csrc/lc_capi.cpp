@@ -415,7 +415,21 @@ lc_status lc_load(const char *path, lc_index **out)
         get(beta, (size_t)n * p.beta_M);
         get(adj0, (size_t)n * DEG);
         get(levels, (size_t)n);
+        // the upper rows are one per (node, level >= 1): a count that disagrees with the
+        // levels would let the import read past the rows that were loaded
+        int64_t want = 0;
+        for (int32_t l : levels) want += l > 0 ? l : 0;
+        if (ok && want != rows) {
+            std::fclose(f);
+            set_error("%s: %lld upper rows stored, the levels need %lld", path, (long long)rows, (long long)want);
+            return LC_ERR_IO;
+        }
         get(upper, (size_t)rows * DEG);
+        if (ok && std::fgetc(f) != EOF) {
+            std::fclose(f);
+            set_error("%s has data after the index", path);
+            return LC_ERR_IO;
+        }
         ix = new lc_index();
         ix->p = p;
     } catch (const std::bad_alloc &) {

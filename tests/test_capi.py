@@ -1,6 +1,7 @@
 """C ABI checks that need no GPU: the library loads and exports every entry point that
 include/lc.h declares; argument and state errors are reported as statuses; import, export
 and the file format round-trip; the host build (train + add) produces a well-formed index."""
+import ctypes
 import os
 import re
 
@@ -109,6 +110,18 @@ def test_import_export_and_file_roundtrip(mix3k, tmp_path):
     with pytest.raises(lc.LcError) as e:
         lc.lc_load(str(bad))
     assert e.value.status == lc.LC_ERR_IO
+    # a truncated file, trailing bytes, and an upper-row count that disagrees with the levels
+    good = (tmp_path / "ix.lc").read_bytes()
+    rows_at = 8 + ctypes.sizeof(lc.lc_params) + 8
+    rows = int(np.frombuffer(good[rows_at:rows_at + 8], np.int64)[0])
+    assert rows == len(ix.upper_adj) > 0
+    fewer = good[:rows_at] + np.int64(rows - 1).tobytes() + good[rows_at + 8:-ix.upper_adj.shape[1] * 4]
+    for blob, words in ((good[:-7], "truncated"), (good + b"\0", "after the index"),
+                        (fewer, "upper rows")):
+        bad.write_bytes(blob)
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_load(str(bad))
+        assert e.value.status == lc.LC_ERR_IO and words in e.value.message, e.value.message
 
 
 def test_import_rejects_bad_graphs(mix3k):
