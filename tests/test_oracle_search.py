@@ -137,13 +137,14 @@ def integer_index(rng, N=150, d=4, deg=6, levels=True):
     return tiny_index(codes1, adj, upper=upper, ep=ep, max_level=ml, d=d, M1=d, M2=1, C1=C1)
 
 
-def wlist_walk(dist, adj, seed, ef):
+def wlist_walk(dist, adj, seed, ef, tcap=0):
     """Result-list formulation: W is the ef best scored nodes, each expansion takes the best
-    unexpanded member of W and merges the batch of its new neighbours at once."""
+    unexpanded member of W and merges the batch of its new neighbours at once.  tcap > 0:
+    no expansion starts once tcap distances were computed (Section 3.1)."""
     W = [(dist(seed), seed)]
     expanded, visited = set(), {seed}
     n_dist, n_exp = 1, 0
-    while True:
+    while not (tcap and n_dist >= tcap):
         un = [w for w in sorted(W) if w[1] not in expanded]
         if not un:
             break
@@ -160,16 +161,18 @@ def wlist_walk(dist, adj, seed, ef):
     return sorted(W), n_dist, n_exp
 
 
+@pytest.mark.parametrize("tcap", [0, 30])
 @pytest.mark.parametrize("ef", [1, 3, 8, 32])
-def test_batched_result_list_equals_two_set_search(rng, ef):
-    for trial in range(6):
+def test_batched_result_list_equals_two_set_search(rng, ef, tcap):
+    # 25 graphs x 100 queries per ef: 10^4 queries over the four ef values (without a cap)
+    for trial in range(25):
         ix = integer_index(rng, levels=False)
-        Q = rng.integers(-8, 9, size=(20, 4)).astype(np.float32)
-        r = oracle.search(ix, Q, k=1, ef=ef, shortlist=-1, return_w=True)
+        Q = rng.integers(-8, 9, size=(100, 4)).astype(np.float32)
+        r = oracle.search(ix, Q, k=1, ef=ef, shortlist=-1, return_w=True, tcap=tcap)
         xh1 = ix.C1.astype(np.float64)[ix.codes1.astype(np.int64), np.arange(4)]
-        for q in range(20):
+        for q in range(100):
             dist = lambda e: float(((Q[q] - xh1[e]) ** 2).sum())
-            W, nd, ne = wlist_walk(dist, ix.adj0, ix.ep, ef)
+            W, nd, ne = wlist_walk(dist, ix.adj0, ix.ep, ef, tcap)
             n = r["w_size"][q]
             assert [w[1] for w in W] == r["w_ids"][q, :n].tolist()
             assert [w[0] for w in W] == r["w_dists"][q, :n].tolist()
@@ -304,13 +307,14 @@ def test_hand_traced_batched_walk():
     assert r["stats"][0].tolist() == [6, 5, 0]
 
 
-def batched_walk(dist, adj, seed, ef, beam):
+def batched_walk(dist, adj, seed, ef, beam, tcap=0):
     """The batched form restated: take the `beam` best unexpanded members of W, score their
-    unvisited neighbours, keep the ef best of everything scored."""
+    unvisited neighbours, keep the ef best of everything scored.  tcap > 0: no step starts
+    once tcap distances were computed."""
     W = [(dist(seed), seed)]
     expanded, visited = set(), {seed}
     n_dist, n_exp = 1, 0
-    while True:
+    while not (tcap and n_dist >= tcap):
         U = [w[1] for w in sorted(W) if w[1] not in expanded][:beam]
         if not U:
             break
@@ -327,17 +331,18 @@ def batched_walk(dist, adj, seed, ef, beam):
     return sorted(W), n_dist, n_exp
 
 
+@pytest.mark.parametrize("tcap", [0, 30])
 @pytest.mark.parametrize("beam", [2, 4, 8])
 @pytest.mark.parametrize("ef", [3, 16])
-def test_batched_form_matches_restatement(rng, beam, ef):
-    for trial in range(4):
+def test_batched_form_matches_restatement(rng, beam, ef, tcap):
+    for trial in range(10):
         ix = integer_index(rng, levels=False)
-        Q = rng.integers(-8, 9, size=(20, 4)).astype(np.float32)
-        r = oracle.search(ix, Q, k=1, ef=ef, shortlist=-1, return_w=True, beam=beam)
+        Q = rng.integers(-8, 9, size=(100, 4)).astype(np.float32)
+        r = oracle.search(ix, Q, k=1, ef=ef, shortlist=-1, return_w=True, beam=beam, tcap=tcap)
         xh1 = ix.C1.astype(np.float64)[ix.codes1.astype(np.int64), np.arange(4)]
-        for q in range(20):
+        for q in range(100):
             dist = lambda e: float(((Q[q] - xh1[e]) ** 2).sum())
-            W, nd, ne = batched_walk(dist, ix.adj0, ix.ep, ef, beam)
+            W, nd, ne = batched_walk(dist, ix.adj0, ix.ep, ef, beam, tcap)
             n = r["w_size"][q]
             assert [w[1] for w in W] == r["w_ids"][q, :n].tolist()
             assert (nd, ne) == tuple(r["stats"][q, :2])
