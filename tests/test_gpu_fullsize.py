@@ -1,9 +1,9 @@
 """GPU parity at the full size of the 1M workload, in the launch configuration the bench times:
 a 1M x 96-d Gaussian-mixture database (1,024 centres) built by the library's host build
 (OPQ32 + residual PQ31 + 1-byte codeword, degree 32), all 10,000 queries searched in one call
-(k = 10, efSearch = 64; the plain FP32 form and the batched beam-4 FP16 form), and a sample of
-1,001 of the outputs, spread over the whole batch and including its last query, checked one
-by one against the FP64 oracle run on the same exported index.  The bar is the one of the
+(the plain FP32 form and the batched beam-4 FP16 form at k = 1 and 10, efSearch 16 to 256),
+and a sample of 1,001 of the outputs, spread over the whole batch and including its last
+query, checked one by one against the FP64 oracle run on the same exported index.  The bar is the one of the
 small-index parity tests: ids and visit counts identical for every query that is not a
 near-tie, distances within 1e-5 relative.
 """
@@ -50,10 +50,15 @@ def index1m():
 SAMPLE = np.append(np.arange(0, N_QUERY, 10), N_QUERY - 1)
 
 
-@pytest.mark.parametrize("form", ["plain_fp32", "batched4_fp16"])
-def test_parity_full_size_sampled(index1m, form):
+# (form, k, efSearch, bound on the near-tie exempt share): the bench's recall-target and
+# headline forms at efSearch 64, the sweep's ends (efSearch 16 at k = 1, efSearch 256), k = 1
+CASES = [("plain_fp32", 10, 64, 0.1), ("batched4_fp16", 10, 64, 0.1), ("plain_fp32", 1, 16, 0.05),
+         ("batched4_fp16", 1, 64, 0.05), ("batched4_fp16", 10, 256, 0.15)]
+
+
+@pytest.mark.parametrize("form,k,ef,max_exempt", CASES)
+def test_parity_full_size_sampled(index1m, form, k, ef, max_exempt):
     h, ix, xq = index1m
-    k, ef = 10, 64
     if form == "plain_fp32":
         ids, ds, st = gpu_search(h, xq, k, ef)
         ref = oracle.search(ix, xq[SAMPLE], k, ef)
@@ -64,7 +69,8 @@ def test_parity_full_size_sampled(index1m, form):
     # every query of the batch got a full result
     assert (ids >= 0).all() and np.isfinite(ds).all()
     assert (st[:, 0] >= 1).all() and (st[:, 1] >= 1).all()
-    ex = compare(ref, ids[SAMPLE], ds[SAMPLE], st[SAMPLE], max_exempt=0.1)
-    # the sample includes queries whose visited set outgrew the shared-memory table
-    assert (ref["stats"][:, 0] > 1024).any()
-    print(f"{form}: {len(SAMPLE)} sampled queries, near-tie exempt {ex:.2%}")
+    ex = compare(ref, ids[SAMPLE], ds[SAMPLE], st[SAMPLE], max_exempt=max_exempt)
+    if ef >= 64:
+        # the sample includes queries whose visited set outgrew the shared-memory table
+        assert (ref["stats"][:, 0] > 1024).any()
+    print(f"{form} k={k} ef={ef}: {len(SAMPLE)} sampled queries, near-tie exempt {ex:.2%}")
