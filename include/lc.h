@@ -136,8 +136,11 @@ lc_status lc_train(lc_index *ix, const float *xt, int64_t nt);
  * 5.1; the inserted vector is compared exactly with the decoded indexed vectors, Section
  * 4.1), trains the regression codebook on the first call (Section 4.3, EM from a k-means
  * initialisation), and assigns each new vector the codeword minimising
- * ||x - beta^T G(x)||^2 (Section 4.3).  Host computation.  Errors: LC_ERR_ARG,
- * LC_ERR_STATE (not trained), LC_ERR_OOM. */
+ * ||x - beta^T G(x)||^2 (Section 4.3).  Host computation; with params.build_gpu = 1 the
+ * encoding, the level-0 insertion searches, the neighbour selection and the codeword
+ * assignment run on the current GPU (same results as the host build up to FP32 near-ties).
+ * Errors: LC_ERR_ARG, LC_ERR_STATE (not trained), LC_ERR_OOM, LC_ERR_CUDA (build_gpu = 1
+ * without a usable device, checked before the index is touched, or a device failure). */
 lc_status lc_add(lc_index *ix, const float *x, int64_t n);
 
 /* lc_add for uint8 vectors x [n][d] (integer-valued descriptors, Section 5.1), converted
