@@ -753,7 +753,7 @@ def main():
         "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": int(hq.numel() * hq.element_size()) + (
                     0 if he is None else int(he.numel() * 4)),
                 "d2h_bytes_per_step": nq * k * 8},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,       # per timed search: rotate_kernel, walk_kernel, refine_kernel
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
