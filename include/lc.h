@@ -117,7 +117,18 @@ typedef struct {
                         coordinate's level-1 plus level-2 centroid; reads M1 + M2P code bytes
                         per node).  With LC_LUT_FP16 both codebooks are rounded, which needs a
                         uniform level-1 split (M1 = 16 or 32 at d = 96, M1 = 64 at d = 128) */
+    int order;       /* order in which the walk takes the queries (lc_search / lc_search_ex only;
+                        plans and served requests always use query order).  LC_ORDER_AUTO (0):
+                        ordered once the batch has at least twice as many queries as the GPU
+                        walks at once; LC_ORDER_NEVER: query order; LC_ORDER_ALWAYS: ordered.
+                        Ordered: a first launch runs every query's upper-level descent, the
+                        queries are sorted by decreasing distance to the node where it enters
+                        level 0 (those tend to walk longest), and the level-0 searches run in
+                        that order, so the batch does not end on a few long walks.  Results do
+                        not depend on it */
 } lc_search_params;
+
+enum { LC_ORDER_AUTO = 0, LC_ORDER_NEVER = 1, LC_ORDER_ALWAYS = 2 };
 
 void lc_default_search_params(lc_search_params *p, int k, int ef);
 

@@ -60,6 +60,10 @@ lc_status check_search_params(const lc_search_params *sp)
     if (sp->max_dist < 0) { set_error("max_dist must be >= 0"); return LC_ERR_ARG; }
     if (sp->warps < 0 || sp->warps > 16) { set_error("warps = %d outside 0..16", sp->warps); return LC_ERR_ARG; }
     if (sp->walk_full != 0 && sp->walk_full != 1) { set_error("walk_full = %d is neither 0 nor 1", sp->walk_full); return LC_ERR_ARG; }
+    if (sp->order != LC_ORDER_AUTO && sp->order != LC_ORDER_NEVER && sp->order != LC_ORDER_ALWAYS) {
+        set_error("order = %d is not LC_ORDER_AUTO, LC_ORDER_NEVER or LC_ORDER_ALWAYS", sp->order);
+        return LC_ERR_ARG;
+    }
     if (sp->visited_log != 0 && (sp->visited_log < 10 || sp->visited_log > 14)) {
         set_error("visited_log = %d outside 10..14", sp->visited_log);
         return LC_ERR_ARG;

@@ -26,6 +26,7 @@ struct DeviceIndex {
     float *yq = nullptr; size_t yq_cap = 0;
     int32_t *shortlist = nullptr; size_t sl_cap = 0;
     int32_t *spill = nullptr; size_t spill_cap = 0;
+    int32_t *ord = nullptr; size_t ord_cap = 0;       // ordered search: 4 words per query
     int32_t *status = nullptr;
     unsigned long long *counter = nullptr;
     // staging for host-pointer calls
@@ -60,7 +61,8 @@ struct SearchPlan {
     size_t qsm = 0;                      // rotation: shared memory
     size_t rsm = 0;
     bool rboth = false;                  // both codebooks in shared memory
-    size_t yq_elems = 0, sl_elems = 0, spill_elems = 0;
+    bool ordered = false;                // two walk launches, level 0 in decreasing entry distance
+    size_t yq_elems = 0, sl_elems = 0, spill_elems = 0, ord_elems = 0;
 };
 
 // Device scratch of one search in flight.
@@ -68,13 +70,18 @@ struct SearchScratch {
     float *yq = nullptr;                 // [nq][d] rotated queries
     int32_t *shortlist = nullptr;        // [nq][R] (refinement only)
     int32_t *spill = nullptr;            // [grid * wpc][2^spill_log]
+    int32_t *ord = nullptr;              // ordered search: entry node, upper evaluations, queue
+                                         // order (int32) and entry distance (float), [nq] each
     int32_t *status = nullptr;           // 1 word
     unsigned long long *counter = nullptr;
 };
 
 lc_status upload(lc_index *ix);
 
-lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl);
+// allow_order: the caller provides the ordered search's scratch (lc_search / lc_search_ex do;
+// plans, served requests and the build's searches walk in query order).
+lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl,
+                      bool allow_order = false);
 // Queues the walk (and refinement) on `st`; q, ids, dists, stats are device pointers.
 // q8 (uint8 queries [nq][d], replacing q) and efq (per-query efSearch [nq]) are optional
 // device pointers; rotated: sc.yq already holds y' (no rotation launch, q unused).

@@ -40,7 +40,7 @@ void device_free(DeviceIndex *dv)
     cfree(dv->Rt); cfree(dv->C1); cfree(dv->C2); cfree(dv->B); cfree(dv->C1h); cfree(dv->C1w); cfree(dv->C2h);
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
-    cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->status); cfree(dv->counter);
+    cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->ord); cfree(dv->status); cfree(dv->counter);
     cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx); cfree(dv->b_sel);
     cfree(dv->q_st); cfree(dv->ef_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
     for (auto &e : dv->ev) if (e) cudaEventDestroy(e);
@@ -126,6 +126,65 @@ __global__ void __launch_bounds__(ROT_THREADS) rotate_kernel(const float *Q, con
             for (int qq = 0; qq < ROT_Q; qq++)
                 if (qq < nb) yq[(q0 + qq) * d + t] = acc[qq];
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Queue order of the ordered search: the queries sorted by decreasing distance to their
+// level-0 entry node (a query whose upper-level descent stopped far from it tends to walk
+// long at level 0, so those start first and the launch does not end on a few long walks).
+// One block of ORDER_THREADS threads: a histogram of the distances over ORDER_BUCKETS buckets
+// (the float's exponent and top 3 mantissa bits: distances are non-negative, so the bit
+// pattern orders like the value), exclusive sums in decreasing bucket order, then a scatter.
+// Within a bucket the order is whatever the atomics give; results do not depend on it.
+constexpr int ORDER_THREADS = 1024;
+constexpr int ORDER_BUCKETS = 2 * ORDER_THREADS;     // each thread sums two buckets
+constexpr int ORDER_MIN_ROUNDS = 2;                  // auto: queries >= 2 x warps in flight
+
+__device__ __forceinline__ int order_bucket(float x)
+{
+    return (int)((__float_as_uint(x) & 0x7fffffffu) >> 20);          // 0 .. 2047
+}
+
+__global__ void __launch_bounds__(ORDER_THREADS) order_kernel(const float *key, int64_t n, int32_t *order)
+{
+    __shared__ uint32_t pos[ORDER_BUCKETS];
+    __shared__ uint32_t wsum[ORDER_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int i = t; i < ORDER_BUCKETS; i += ORDER_THREADS) pos[i] = 0;
+    __syncthreads();
+    for (int64_t i = t; i < n; i += ORDER_THREADS) atomicAdd(&pos[order_bucket(__ldg(key + i))], 1u);
+    __syncthreads();
+    // thread t owns buckets b0 = 2047 - 2t and b0 - 1 (ranks 2t and 2t + 1 in decreasing order)
+    const int b0 = ORDER_BUCKETS - 1 - 2 * t, b1 = b0 - 1;
+    const uint32_t c0 = pos[b0], c1 = pos[b1];
+    const uint32_t own = c0 + c1;
+    uint32_t inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t v = wsum[lane];
+        uint32_t vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += u;
+        }
+        wsum[lane] = vi - v;                          // warps before this one
+    }
+    __syncthreads();
+    const uint32_t ex = wsum[w] + inc - own;          // queries in buckets above b0
+    pos[b0] = ex;                                     // only this thread reads or writes b0, b1
+    pos[b1] = ex + c0;
+    __syncthreads();
+    for (int64_t i = t; i < n; i += ORDER_THREADS) {
+        const uint32_t p = atomicAdd(&pos[order_bucket(__ldg(key + i))], 1u);
+        order[p] = (int32_t)i;
     }
 }
 
@@ -457,7 +516,8 @@ static RefineFn refine_kernel_for(bool both, int d, bool prod)
     return both ? refine_kernel<true, 8, false> : refine_kernel<false, 8, false>;
 }
 
-lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl)
+lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params *sp, SearchPlan *pl,
+                      bool allow_order)
 {
     SearchPlan P;
     P.k = sp->k;
@@ -501,6 +561,11 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     }
     P.spill_elems = ((size_t)P.grid * P.wpc) << P.spill_log;
     P.yq_elems = (size_t)nq * dv->d;
+    // ordered search: worth its two extra launches once every warp takes a few queries
+    P.ordered = allow_order && nq <= INT32_MAX && dv->n > 0 &&
+                (sp->order == LC_ORDER_ALWAYS ||
+                 (sp->order == LC_ORDER_AUTO && nq >= (int64_t)ORDER_MIN_ROUNDS * P.grid * P.wpc));
+    P.ord_elems = P.ordered ? (size_t)nq * 4 : 0;
     {
         const size_t rsm = rotate_smem(dv->d);
         if (cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM_PER_BLOCK) != cudaSuccess) {
@@ -595,6 +660,32 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         set_error("rotation kernel launch failed: %s", cudaGetErrorString(ce));
         return LC_ERR_CUDA;
     }
+    if (P.ordered) {
+        // ordered search: the upper-level descents, the queue order, then the level-0 walks
+        int32_t *seed = sc.ord, *seed_up = sc.ord + nq, *order = sc.ord + 2 * nq;
+        float *seed_d = reinterpret_cast<float *>(sc.ord + 3 * nq);
+        WalkArgs w1 = wa;
+        w1.mode = 1;
+        w1.seed = seed;
+        w1.seed_up = seed_up;
+        w1.seed_d = seed_d;
+        ce = walk_run(P.half, P.variant, dv->M1, P.full, w1, P.smem, P.wpc, P.grid, st);
+        if (ce == cudaSuccess && cudaMemsetAsync(sc.counter, 0, sizeof(unsigned long long), st) == cudaSuccess) {
+            order_kernel<<<1, ORDER_THREADS, 0, st>>>(seed_d, nq, order);
+            ce = cudaGetLastError();
+        } else if (ce == cudaSuccess) {
+            ce = cudaGetLastError();
+        }
+        if (ce != cudaSuccess) {
+            set_error("walk descent or queue order launch failed: %s", cudaGetErrorString(ce));
+            return LC_ERR_CUDA;
+        }
+        wa.mode = 2;
+        wa.order = order;
+        wa.seed = seed;
+        wa.seed_up = seed_up;
+        wa.seed_d = seed_d;
+    }
     ce = walk_run(P.half, P.variant, dv->M1, P.full, wa, P.smem, P.wpc, P.grid, st);
     if (profile) cudaEventRecord(dv->ev[1], st);
     if (ce != cudaSuccess) {
@@ -664,7 +755,7 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
     if (rs != LC_OK) return rs;
     DeviceIndex *dv = ix->dev;
     SearchPlan P;
-    rs = plan_search(dv, std::max<int64_t>(nq, 1), sp, &P);
+    rs = plan_search(dv, std::max<int64_t>(nq, 1), sp, &P, true);
     if (rs != LC_OK) return rs;
     if (nq == 0) return LC_OK;
     const void *dq = q;
@@ -714,7 +805,8 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
         return LC_OK;
     }
     if (!grow(dv->spill, dv->spill_cap, P.spill_elems) || !grow(dv->yq, dv->yq_cap, P.yq_elems) ||
-        (P.refine && !grow(dv->shortlist, dv->sl_cap, P.sl_elems))) {
+        (P.refine && !grow(dv->shortlist, dv->sl_cap, P.sl_elems)) ||
+        (P.ordered && !grow(dv->ord, dv->ord_cap, P.ord_elems))) {
         set_error("cudaMalloc failed for search scratch");
         return LC_ERR_OOM;
     }
@@ -722,6 +814,7 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
     sc.yq = dv->yq;
     sc.shortlist = dv->shortlist;
     sc.spill = dv->spill;
+    sc.ord = dv->ord;
     sc.status = dv->status;
     sc.counter = dv->counter;
     rs = run_search(dv, P, u8 ? nullptr : static_cast<const float *>(dq), nq, dids, ddists, dstats, sc, st,

@@ -20,7 +20,13 @@
 //   - exact visited set: open-addressing hash in shared memory, spilling to a per-warp table
 //     in global memory when it fills;
 //   - writes the shortlist (the R best of W, Section 4.1 two-stage search) or, without
-//     refinement, the top-k directly.
+//     refinement, the top-k directly;
+//   - ordered search: a first launch (mode 1) runs only the upper-level descent of every query
+//     and records where it enters level 0; a second (mode 2) runs the level-0 searches from
+//     those entry nodes in the order the host sorted them (the queries whose entry node is
+//     farthest from them first: they tend to walk longest, so the launch no longer ends with a
+//     few long walks on an otherwise idle GPU).  Each query's result is the same as in one
+//     launch (mode 0): the entry node and its distance are the ones the descent computes.
 //
 // FP32 walk distance: lane l holds the term of sub-space l (M1 = 32), of l mod 16 (M1 = 16)
 // or the sum of sub-spaces l and l + 32 (M1 = 64), each term summed over its coordinates in
@@ -85,6 +91,14 @@ struct WalkArgs {
     const uint8_t *codes2b;
     int M2P;
     uint8_t sub2[256];     // level-2 sub-space of each coordinate
+    // ordered search (see walk_kernel): 0 = the whole walk; 1 = the upper levels only, writing
+    // each query's level-0 entry node, its walk distance and the upper-level evaluations to
+    // seed / seed_d / seed_up; 2 = level 0 only, from those, queue position i taking query
+    // order[i] (order may be null: position i is query i)
+    int mode;
+    const int32_t *order;
+    int32_t *seed, *seed_up;
+    float *seed_d;
 };
 
 constexpr int MAX_WALK_WARPS = 16;       // warps (queries in flight) per CTA
@@ -546,10 +560,11 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
     const unsigned lt_mask = (1u << lane) - 1;
 
     for (;;) {
-        int64_t q = 0;
-        if (lane == 0) q = atomicAdd(a.counter, 1ull);
-        q = __shfl_sync(FULL, q, 0);
-        if (q >= a.nq) break;
+        int64_t qi = 0;
+        if (lane == 0) qi = atomicAdd(a.counter, 1ull);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= a.nq) break;
+        const int64_t q = a.order ? (int64_t)__ldg(a.order + qi) : qi;
         // this query's ef' = max(ef, k)
         const int efp = a.efq ? max(min(max(__ldg(a.efq + q), 1), a.efp), a.k) : a.efp;
         // rotation y' = R y (fixed order u = 0..d-1); uint8 queries convert exactly to FP32
@@ -571,7 +586,8 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                 yq[t] = s;
             }
         }
-        for (int i = lane; i < H; i += 32) hash[i] = -1;
+        if (a.mode != 1)
+            for (int i = lane; i < H; i += 32) hash[i] = -1;
         __syncwarp();
         LaneGeo<M1, D1> g;
 #pragma unroll
@@ -600,6 +616,20 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         int32_t hcount = 1, scount = 0;
         int scan_from = 0;
         const int B = a.beam;              // level-0 expansions per step; 1 = the plain walk
+        if (a.mode == 2) {
+            // level 0 from the entry node the descent launch recorded (as at its end below)
+            cur = __ldg(a.seed + q);
+            dcur = __ldg(a.seed_d + q);
+            n_up = __ldg(a.seed_up + q);
+            phase = 2;
+            if (lane == 0) {
+                wkey[0] = make_key(dcur, cur);
+                wflag[0] = 0;
+                hash[hash32(cur) & (H - 1)] = cur;
+            }
+            n_dist = 1;
+            __syncwarp();
+        }
         for (;;) {
             uint64_t *W = wkey + buf * a.efcap;
             uint8_t *F = wflag + buf * a.efcap;
@@ -786,6 +816,15 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                 } else if (--lvl == 0) {
                     enter0 = true;
                 }
+                if (enter0 && a.mode == 1) {
+                    // descent only: record the level-0 entry for the second launch
+                    if (lane == 0) {
+                        a.seed[q] = cur;
+                        a.seed_d[q] = dcur;
+                        a.seed_up[q] = n_up;
+                    }
+                    break;
+                }
                 if (enter0) {
                     // level 0: best-first search with result list W (sorted keys + expanded flags)
                     phase = 2;
@@ -846,6 +885,10 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             __syncwarp();
         }
 
+        if (a.mode == 1) {
+            __syncwarp();
+            continue;
+        }
         // outputs
         const uint64_t *W = wkey + buf * a.efcap;
         if (a.refine) {

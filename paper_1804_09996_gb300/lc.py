@@ -18,6 +18,7 @@ LC_ERR_TIMEOUT, LC_ERR_BUDGET, LC_ERR_IO, LC_ERR_CAPACITY = 5, 6, 7, 8
 LC_MODE_PLAIN, LC_MODE_BATCHED = 0, 1
 LC_LUT_FP32, LC_LUT_FP16 = 0, 1
 LC_QUERY_F32, LC_QUERY_U8 = 0, 1
+LC_ORDER_AUTO, LC_ORDER_NEVER, LC_ORDER_ALWAYS = 0, 1, 2
 
 EXPORTED = [
     "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_add_u8",
@@ -51,7 +52,7 @@ class lc_params(ctypes.Structure):
 
 class lc_search_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam", "max_dist", "warps",
-                                                     "walk_full")]
+                                                     "walk_full", "order")]
 
 
 class lc_tune_params(ctypes.Structure):

@@ -68,6 +68,9 @@ def test_state_errors_without_gpu():
         with pytest.raises(lc.LcError) as e:
             lc.lc_search(h, q, 1, lc.lc_default_search_params(4, 2000), ids, ds)
         assert e.value.status == lc.LC_ERR_ARG
+        with pytest.raises(lc.LcError) as e:
+            lc.lc_search(h, q, 1, lc.lc_default_search_params(1, 8, order=3), ids, ds)
+        assert e.value.status == lc.LC_ERR_ARG and "order" in e.value.message
         for beam in (1, 9):
             with pytest.raises(lc.LcError) as e:
                 lc.lc_search(h, q, 1, lc.lc_default_search_params(1, 8, mode=lc.LC_MODE_BATCHED, beam=beam), ids, ds)
