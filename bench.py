@@ -753,7 +753,11 @@ def main():
         "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": int(hq.numel() * hq.element_size()) + (
                     0 if he is None else int(he.numel() * 4)),
                 "d2h_bytes_per_step": nq * k * 8},
-        "gpu_launches": 3 * args.steps,       # per timed search: rotate_kernel, walk_kernel, refine_kernel
+        # per timed search: rotate_kernel, walk_kernel, refine_kernel; a batch of at least twice
+        # the queries the GPU walks at once (<= 16 per SM) is searched in order of entry distance,
+        # which adds the descent launch of walk_kernel and order_kernel
+        "gpu_launches": (5 if nq >= 2 * 16 * torch.cuda.get_device_properties(dev).multi_processor_count
+                         else 3) * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
