@@ -104,8 +104,7 @@ typedef struct {
     int mode;        /* LC_MODE_PLAIN or LC_MODE_BATCHED */
     int visited_log; /* 0: automatic; 10..14: the per-query visited table in shared memory has
                         2^visited_log entries (ids beyond half of it go to a table in global
-                        memory, 2^16 entries per query in flight; beyond half of that the
-                        query fails with LC_ERR_CAPACITY) */
+                        memory, see spill_log) */
     int beam;        /* LC_MODE_BATCHED: expansions per step, 2..8 (ignored in PLAIN mode) */
     int max_dist;    /* search-time cap T (Section 3.1): 0 = none; > 0: the level-0 search stops
                         before an expansion once T distances have been computed there */
@@ -126,6 +125,12 @@ typedef struct {
                         level 0 (those tend to walk longest), and the level-0 searches run in
                         that order, so the batch does not end on a few long walks.  Results do
                         not depend on it */
+    int spill_log;   /* the per-query visited table in global memory (one per query in flight,
+                        taking the ids once the shared table is half full): 0 = automatic,
+                        2^13 .. 2^16 entries as max(ef, k) grows (64 entries per result-set
+                        slot); 8..16: 2^spill_log entries.  A query that would fill it beyond
+                        half fails: LC_ERR_CAPACITY (host pointers) or n_dist = -1 and ids -1
+                        (device pointers), the other queries of the batch are unaffected */
 } lc_search_params;
 
 enum { LC_ORDER_AUTO = 0, LC_ORDER_NEVER = 1, LC_ORDER_ALWAYS = 2 };
@@ -164,8 +169,8 @@ lc_status lc_add_u8(lc_index *ix, const uint8_t *x, int64_t n);
  * squared L2 to the refined reconstruction, or the ADC distance when shortlist < 0; +inf
  * with id -1), stats [nq][3] (int32: distinct nodes scored at level 0, level-0
  * expansions, evaluations on the upper levels; may be NULL).
- * Pointers may all be host memory or all device memory (checked with
- * cudaPointerGetAttributes).  Device pointers: the work is queued on `stream` (a
+ * Pointers may all be host memory or all device memory of the current device (checked with
+ * cudaPointerGetAttributes; another GPU's memory is LC_ERR_ARG).  Device pointers: the work is queued on `stream` (a
  * cudaStream_t, NULL = the default stream) and the call returns without waiting.  Host
  * pointers: the call copies through the device and returns when the results are written.
  * The index is uploaded to the current device on the first search.
@@ -234,17 +239,21 @@ lc_status lc_load(const char *path, lc_index **out);
  * synchronise the whole device and take unbounded time, which a latency-bound request loop
  * cannot afford, and an application that manages device memory through its own pool or a
  * fixed budget cannot have memory taken behind its back.  This call allocates nothing: its
- * scratch is a file-scope device array of 32 MiB + 256 B in liblc.so (held on every GPU that
+ * scratch is a file-scope device array of 64 MiB + 256 B in liblc.so (held on every GPU that
  * loads the library until the process exits), looked up once per device on the call's first
- * use there, so make that first call before any stream capture.  The paper has no
- * counterpart; it is an operational variant of the search above.
- * Requirements: q, ids, dists (and stats, may be NULL) are device pointers; the index is
- * already resident on the current device (an earlier lc_search uploads it), else
- * LC_ERR_STATE; max(ef, k) <= 256, else LC_ERR_ARG.  Work is queued on `stream` and the call
- * returns without waiting.  Every call shares the one scratch array, so calls whose work
- * overlaps on the GPU (other streams, other host threads) race and must be serialised by
- * the caller.  A query whose visited set overflows the scratch reports n_dist = -1 in stats
- * and ids -1.  Errors: LC_ERR_ARG, LC_ERR_STATE, LC_ERR_CUDA, LC_ERR_CAPACITY. */
+ * use there, so make that first call before any stream capture.  Each query in flight gets
+ * the visited tables lc_search gives it at the same efSearch, so results (overflows
+ * included) are those of lc_search; the array bounds the queries in flight (2,048 up to
+ * max(ef, k) = 128, 1,024 up to 256).  The paper has no counterpart; it is an operational
+ * variant of the search above.
+ * Requirements: q, ids, dists (and stats, may be NULL) are device pointers of the current
+ * device; the index is already resident on the current device (an earlier lc_search uploads
+ * it), else LC_ERR_STATE; max(ef, k) <= 256, else LC_ERR_ARG.  Work is queued on `stream` and
+ * the call returns without waiting.  Every call shares the one scratch array, so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must be serialised by
+ * the caller.  A query whose visited set overflows its table reports n_dist = -1 in stats and
+ * ids -1 (as lc_search with device pointers).  Errors: LC_ERR_ARG, LC_ERR_STATE, LC_ERR_CUDA,
+ * LC_ERR_CAPACITY. */
 lc_status lc_search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef,
                                  int32_t *ids, float *dists, int32_t *stats, void *stream);
 

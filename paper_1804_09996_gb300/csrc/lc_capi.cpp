@@ -68,6 +68,10 @@ lc_status check_search_params(const lc_search_params *sp)
         set_error("visited_log = %d outside 10..14", sp->visited_log);
         return LC_ERR_ARG;
     }
+    if (sp->spill_log != 0 && (sp->spill_log < 8 || sp->spill_log > 16)) {
+        set_error("spill_log = %d outside 8..16", sp->spill_log);
+        return LC_ERR_ARG;
+    }
     return LC_OK;
 }
 

@@ -531,7 +531,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     P.beam = sp->mode == LC_MODE_BATCHED ? sp->beam : 1;
     P.tcap = sp->max_dist;
     P.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)P.efp * 32)));
-    P.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)P.efp * 64)));
+    P.spill_log = sp->spill_log ? sp->spill_log : std::min(16, std::max(13, ilog2_ceil((int64_t)P.efp * 64)));
     const int efcap = (int)align_up(P.efp, 32);
     // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
     P.variant = walk_variant(dv->M1, dv->d);
@@ -727,17 +727,28 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
 {
     cudaStream_t st = (cudaStream_t)stream_;
     const int k = sp->k;
-    // pointer kinds: all device or all host
-    auto kind = [](const void *p) {
+    // pointer kinds: all device or all host (2: device memory of another GPU than the current
+    // one, which the kernels would read through peer access or fault on)
+    int cur_dev = -1;
+    if (cudaGetDevice(&cur_dev) != cudaSuccess) {
+        cudaGetLastError();                // no device: every pointer reads as host memory, and
+        cur_dev = -1;                      // the upload below reports the missing device
+    }
+    auto kind = [cur_dev](const void *p) {
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+        if (at.type == cudaMemoryTypeDevice) return at.device == cur_dev ? 1 : 2;
+        return at.type == cudaMemoryTypeManaged ? 1 : 0;
     };
     int kq = kind(q), ki = kind(ids), kd = kind(dists), ks = stats ? kind(stats) : kq;
     int ke = efq ? kind(efq) : kq;
+    if (kq == 2 || ki == 2 || kd == 2 || ks == 2 || ke == 2) {
+        set_error("device pointers must be memory of the current device (%d)", cur_dev);
+        return LC_ERR_ARG;
+    }
     if (kq != ki || kq != kd || kq != ks || kq != ke) {
         set_error("query, efSearch and output pointers must all be host or all be device memory");
         return LC_ERR_ARG;
@@ -846,11 +857,13 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
 // memory through its own pool or a fixed budget cannot have memory taken behind its back.
 // This entry point runs the same walk kernel as lc_search, but its scratch (the query
 // counter, the status word and the per-warp spill tables of the visited sets) lives in the
-// file-scope array below, which every GPU that loads this library holds until exit.
-constexpr int NOALLOC_SPILL_LOG = 12;                  // 4096 ids per query in flight
-constexpr size_t NOALLOC_SLOTS = 2048;                 // queries in flight at most
+// file-scope array below, which every GPU that loads this library holds until exit.  Each
+// query in flight gets a spill table of the size lc_search gives it at the same efSearch
+// (2^13 entries up to max(ef, k) = 128, 2^14 up to 256), so a query overflows here exactly
+// when it overflows in lc_search; the number of queries in flight is what the array bounds.
 constexpr size_t NOALLOC_HEADER = 256;                 // counter (8 B) and status (4 B)
-constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_SLOTS * ((size_t)1 << NOALLOC_SPILL_LOG) * 4;
+constexpr size_t NOALLOC_SPILL_BYTES = (size_t)64 << 20;   // 2048 tables of 2^13 entries
+constexpr size_t NOALLOC_BYTES = NOALLOC_HEADER + NOALLOC_SPILL_BYTES;
 constexpr int NOALLOC_MAX_EF = 256;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
@@ -900,16 +913,18 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
         set_error("index is not resident on device %d: run lc_search (which uploads it) first", dev);
         return LC_ERR_STATE;
     }
-    auto on_device = [](const void *p) {
+    // device memory of the current device (another GPU's memory would be read through peer
+    // access, or fault), or managed memory
+    auto on_device = [dev](const void *p) {
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+        return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
     };
     if (nq > 0 && (!on_device(q) || !on_device(ids) || !on_device(dists) || (stats && !on_device(stats)))) {
-        set_error("the no-allocation walk takes device pointers only");
+        set_error("the no-allocation walk takes device pointers of the current device (%d) only", dev);
         return LC_ERR_ARG;
     }
     if (nq == 0) return LC_OK;
@@ -929,8 +944,9 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     wa.efp = efp; wa.efcap = (int)align_up(efp, 32); wa.k = k;
     wa.R = k; wa.refine = 0;
     wa.beam = 1;
+    // the visited tables of lc_search at this efSearch (same shared table, same spill table)
     wa.hash_log = std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));
-    wa.spill_log = NOALLOC_SPILL_LOG;
+    wa.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)efp * 64)));
     wa.ids_out = ids; wa.dists_out = dists; wa.stats_out = stats;
     wa.counter = reinterpret_cast<unsigned long long *>(scratch);
     wa.status = reinterpret_cast<int32_t *>(scratch + 8);
@@ -950,7 +966,8 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
         return ce == cudaErrorInvalidConfiguration ? LC_ERR_CAPACITY : LC_ERR_CUDA;
     }
     // every warp in flight owns one spill table of the array
-    grid = (int)std::min<int64_t>(grid, (int64_t)(NOALLOC_SLOTS / wpc));
+    const size_t slots = NOALLOC_SPILL_BYTES / ((size_t)4 << wa.spill_log);
+    grid = (int)std::min<int64_t>(grid, (int64_t)(slots / wpc));
     // the array keeps the previous call's contents: the counter and status start at zero
     // (spill tables are cleared by the kernel before a query uses one)
     if (cudaMemsetAsync(scratch, 0, 16, st) != cudaSuccess) {

@@ -164,6 +164,11 @@ void admit(lc_server *s)
         s->queue.pop_front();
         lc_status rs = launch(s, *free_slot, r);
         if (rs != LC_OK) {
+            // a launch that failed part-way may have queued copies and kernels on the slot's
+            // stream that still write the request's arena range: wait for them before the
+            // range is freed and handed to the next request
+            cudaStreamSynchronize(free_slot->st);
+            cudaGetLastError();
             free_slot->req = r;
             deliver(s, *free_slot, rs);
         }

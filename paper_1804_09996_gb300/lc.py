@@ -52,7 +52,7 @@ class lc_params(ctypes.Structure):
 
 class lc_search_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in ("k", "ef", "shortlist", "lut_prec", "mode", "visited_log", "beam", "max_dist", "warps",
-                                                     "walk_full", "order")]
+                                                     "walk_full", "order", "spill_log")]
 
 
 class lc_tune_params(ctypes.Structure):

@@ -75,6 +75,10 @@ def test_state_errors_without_gpu():
             with pytest.raises(lc.LcError) as e:
                 lc.lc_search(h, q, 1, lc.lc_default_search_params(1, 8, mode=lc.LC_MODE_BATCHED, beam=beam), ids, ds)
             assert e.value.status == lc.LC_ERR_ARG and "beam" in e.value.message
+        for bad in (7, 17, -1):
+            with pytest.raises(lc.LcError) as e:
+                lc.lc_search(h, q, 1, lc.lc_default_search_params(1, 8, spill_log=bad), ids, ds)
+            assert e.value.status == lc.LC_ERR_ARG and "spill_log" in e.value.message
         with pytest.raises(lc.LcError) as e:
             lc.lc_train(h, np.zeros((10, 16), np.float32))
         assert e.value.status == lc.LC_ERR_ARG
