@@ -21,4 +21,4 @@ brute force or invariants the paper states; see the tests named test_oracle_*.
 from . import codec, graph, refine  # noqa: F401
 from ._clib import build  # noqa: F401
 from .index import OracleIndex, build_index  # noqa: F401
-from .search import knn, merge_topk, search  # noqa: F401
+from .search import dists, knn, merge_topk, search, trace  # noqa: F401

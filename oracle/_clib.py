@@ -37,7 +37,13 @@ def lib() -> ctypes.CDLL:
             i64, i32 = ctypes.c_int64, ctypes.c_int
             L.orc_search.restype = ctypes.c_int
             L.orc_search.argtypes = [i64, i32, i32, i32, P, P, P, P, P, P, P, i32, i32, i32, P, i32, P, P,
-                                     ctypes.c_int32, i32, i64, P, i32, i32, i32, i32, i32, P, i32, P, P, P, P, P, P, P, P]
+                                     ctypes.c_int32, i32, i64, P, i32, i32, i32, i32, i32, P, i32, P, P, P, P, P,
+                                     P, P, P, P, P]
+            L.orc_dists.restype = ctypes.c_int
+            L.orc_dists.argtypes = [i64, i32, i32, i32, P, P, P, P, P, P, P, i32, i32, i32, P, i64, P, i32, P,
+                                    P, i32, P, P, P]
+            L.orc_trace.restype = ctypes.c_int
+            L.orc_trace.argtypes = [P, i32]
             L.orc_build_graph.restype = ctypes.c_int
             L.orc_build_graph.argtypes = [i64, i32, P, P, P, i32, i32, i32, i32, i32, P, P, i64, P,
                                           P, P]

@@ -30,7 +30,14 @@
  * where it moves on an upper level, the shortlist boundary and the order of the k returned.
  * A GPU run in FP32 may legitimately decide such a comparison the other way when that gap is
  * below its rounding error; every other comparison can change only the order inside the
- * result set, never the nodes expanded.
+ * result set, never the nodes expanded.  Two minima are reported: over every deciding
+ * comparison, and over those that decide the walk and the shortlist only (not the order of
+ * the k returned), so a query whose only near-tie is in its output order can still be held
+ * to the same walk.  orc_trace lists the deciding comparisons one by one (for the tests that
+ * pin this record against hand traces).
+ *
+ *   orc_dists       the walk distance and the refined distance of given (query, id) pairs,
+ *                   computed directly from their definitions (no walk).
  */
 #include <math.h>
 #include <stdint.h>
@@ -59,36 +66,78 @@ static int key_less(double da, int32_t ia, double db, int32_t ib)
     return da < db || (da == db && ia < ib);
 }
 
+/* Kinds of deciding comparison (orc_trace reports them with the two ids compared). */
+enum {
+    GAP_UPPER_SECOND = 1,   /* upper level: best neighbour against the runner-up */
+    GAP_UPPER_MOVE = 2,     /* upper level: best neighbour against the current node */
+    GAP_RUNNER = 3,         /* level 0: node expanded next against the runner-up in C */
+    GAP_OUTSIDE = 4,        /* level 0: node expanded next against the best node outside W */
+    GAP_BREAK = 5,          /* level 0: the furthest of W against the popped node that ends the walk */
+    GAP_END = 6,            /* level 0: C ran empty; the worst of W against the best outside */
+    GAP_BATCH_NEXT = 7,     /* batched: last member taken against the next unexpanded one */
+    GAP_BATCH_OUTSIDE = 8,  /* batched: last member taken against the best node outside W */
+    GAP_BATCH_END = 9,      /* batched: the worst of W against the best outside, at the end */
+    GAP_SHORTLIST = 10,     /* the R-th of W against the (R+1)-th */
+    GAP_OUT_WALK = 11,      /* output without refinement: consecutive returned, k-th vs (k+1)-th */
+    GAP_OUT_REFINED = 12    /* output after refinement: the same on refined distances */
+};
+
 typedef struct {
-    double gap;                 /* smallest relative gap seen so far */
+    double gap;                 /* smallest relative gap seen so far, every kind */
+    double gap_walk;            /* the same over the walk and shortlist kinds (1..10) */
     const uint8_t *codes1;      /* to recognise exact ties between identical code rows */
     int M1;
     const uint8_t *codes2;      /* non-NULL when the walk scores the full decode */
     int M2;
 } gap_rec;
 
-static void note_gap(gap_rec *g, double a, int32_t ia, double b, int32_t ib, int walk)
+/* Trace of deciding comparisons (test use): (kind, first id, second id) triples. */
+static _Thread_local int32_t *trace_buf = NULL;
+static _Thread_local int trace_cap = 0;
+static _Thread_local int trace_n = 0;
+
+/* Starts (cap > 0) or stops (buf NULL) tracing on the calling thread; returns the number of
+   triples written since the last start. */
+int orc_trace(int32_t *buf, int cap)
+{
+    int n = trace_n;
+    trace_buf = buf;
+    trace_cap = buf ? cap : 0;
+    trace_n = 0;
+    return n;
+}
+
+static void note_gap(gap_rec *g, int kind, double a, int32_t ia, double b, int32_t ib)
 {
     if (ia == ib) return;
+    if (trace_buf && trace_n < trace_cap) {
+        trace_buf[3 * trace_n] = kind;
+        trace_buf[3 * trace_n + 1] = ia;
+        trace_buf[3 * trace_n + 2] = ib;
+        trace_n++;
+    }
+    double r;
     if (a == b) {
-        /* Identical code rows give identical sums on any hardware; that tie is decided
-           by id on both sides.  Any other exact tie is treated as unresolved. */
+        /* Identical code rows give identical walk sums on any hardware; that tie is
+           decided by id on both sides.  Any other exact tie is treated as unresolved. */
+        int walk = kind != GAP_OUT_REFINED;
         if (walk && memcmp(g->codes1 + (int64_t)ia * g->M1, g->codes1 + (int64_t)ib * g->M1,
                            (size_t)g->M1) == 0 &&
             (!g->codes2 || memcmp(g->codes2 + (int64_t)ia * g->M2, g->codes2 + (int64_t)ib * g->M2,
                                   (size_t)g->M2) == 0))
             return;
-        g->gap = 0.0;
-        return;
+        r = 0.0;
+    } else {
+        double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+        r = fabs(a - b) / m;
     }
-    double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
-    double r = fabs(a - b) / m;
     if (r < g->gap) g->gap = r;
+    if (kind <= GAP_SHORTLIST && r < g->gap_walk) g->gap_walk = r;
 }
 
-static int cmp_note(gap_rec *g, double da, int32_t ia, double db, int32_t ib, int walk)
+static int cmp_note(gap_rec *g, int kind, double da, int32_t ia, double db, int32_t ib)
 {
-    note_gap(g, da, ia, db, ib, walk);
+    note_gap(g, kind, da, ia, db, ib);
     return key_less(da, ia, db, ib);
 }
 
@@ -159,6 +208,36 @@ static void decode2(const orc_index *ix, const int *off1, const int *len1, const
             out[t] += (double)ix->C2[(int64_t)b[j] * ix->d + t];
 }
 
+/* Squared L2 from the rotated query yr to the refined reconstruction of node i (Section 4.2,
+   4.3): y^ = sum_j beta_j q(v_j) over G = [q(i), q(g1..g8)], g the first 8 entries of i's
+   level-0 row (a -1 entry is a zero column); with a product codebook each block of
+   coordinates takes the weights of its own codeword.  xh, yh: scratch of d doubles (xh) and
+   d doubles (yh). */
+static double refined_dist(const orc_index *ix, const int *off1, const int *len1, const int *off2,
+                           const int *len2, const int *offb, const int *lenb, const double *yr, int32_t i,
+                           double *xh, double *yh)
+{
+    const int d = ix->d;
+    for (int t = 0; t < d; t++) yh[t] = 0.0;
+    for (int j = 0; j <= ORC_KBETA; j++) {
+        int32_t v = j == 0 ? i : ix->adj0[(int64_t)i * ix->deg + (j - 1)];
+        if (j > 0 && (j - 1 >= ix->deg || v < 0)) continue;     /* zero column */
+        decode2(ix, off1, len1, off2, len2, v, xh);
+        for (int m = 0; m < ix->bM; m++) {
+            int b = ix->bK > 1 ? ix->beta[(int64_t)i * ix->bM + m] : 0;
+            double w = (double)ix->B[((int64_t)m * ix->bK + b) * (ORC_KBETA + 1) + j];
+            for (int t = offb[m]; t < offb[m] + lenb[m]; t++) yh[t] += w * xh[t];
+        }
+    }
+    /* Exact squared L2 to the refined reconstruction */
+    double s = 0.0;
+    for (int t = 0; t < d; t++) {
+        double diff = yr[t] - yh[t];
+        s += diff * diff;
+    }
+    return s;
+}
+
 /* Level-0 search in the batched form: each step takes the `beam` best unexpanded members of
    W together, scores all their unvisited neighbours (a node shared by two rows is scored and
    counted once), and keeps the ef' best of W and the new nodes.  With beam = 1 this expands
@@ -192,8 +271,12 @@ static int walk_batched(const orc_index *ix, const walk_ctx *wc, int32_t seed, i
         int last = U[nu - 1], next = -1;
         for (int p = last + 1; p < wn; p++)
             if (!wf[p]) { next = p; break; }
-        if (nu == beam && next >= 0) note_gap(g, wd[last], wi[last], wd[next], wi[next], 1);
-        if (oi >= 0) note_gap(g, wd[last], wi[last], od, oi, 1);
+        if (nu == beam && next >= 0) note_gap(g, GAP_BATCH_NEXT, wd[last], wi[last], wd[next], wi[next]);
+        /* with beam members taken, the best node outside W would be taken instead of the last
+           one if it ranked before it; with fewer, every unexpanded member is taken and the
+           outsider would be too if it ranked inside W at all (before its worst member) */
+        if (oi >= 0 && nu == beam) note_gap(g, GAP_BATCH_OUTSIDE, wd[last], wi[last], od, oi);
+        if (oi >= 0 && nu < beam) note_gap(g, GAP_BATCH_OUTSIDE, wd[wn - 1], wi[wn - 1], od, oi);
         int an = 0;
         for (int p = 0; p < wn; p++) { ad[an] = wd[p]; ai[an] = wi[p]; af[an] = wf[p]; an++; }
         for (int u = 0; u < nu; u++) af[U[u]] = 1;
@@ -225,8 +308,10 @@ static int walk_batched(const orc_index *ix, const walk_ctx *wc, int32_t seed, i
         }
         for (int p = 0; p < wn; p++) { wd[p] = ad[p]; wi[p] = ai[p]; wf[p] = af[p]; }
     }
-    /* termination: the best node outside W against the worst inside */
-    if (oi >= 0 && !(tcap > 0 && *n_dist >= tcap)) note_gap(g, wd[wn - 1], wi[wn - 1], od, oi, 1);
+    /* the end (every member expanded, or the cap T reached): the best node outside W
+       against the worst inside decides whether the walk had a member left to take, and
+       which nodes W holds */
+    if (oi >= 0) note_gap(g, GAP_BATCH_END, wd[wn - 1], wi[wn - 1], od, oi);
     free(ad); free(ai); free(af); free(wf); free(U);
     return wn;
 }
@@ -237,7 +322,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                const int32_t *upper_off, const int32_t *upper_adj, int32_t ep, int max_level,
                int64_t nq, const float *Q, int k, int ef, int shortlist, int beam, int tcap,
                const float *C1w, int walk_full, const float *C2w, int32_t *ids, double *dists,
-               int32_t *stats, double *min_gap,
+               int32_t *stats, double *min_gap, double *min_gap_walk, double *next_dist,
                int32_t *w_ids, double *w_dists, int32_t *w_size)
 {
     orc_index ix = {N, d, M1, M2, deg, deg_up, max_level, ep, R, C1, C2, B, bM, bK,
@@ -272,7 +357,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
 
     for (int64_t q = 0; q < nq; q++) {
         const float *y = Q + q * d;
-        gap_rec g = {INFINITY, codes1, M1, walk_full ? codes2 : NULL, M2};
+        gap_rec g = {INFINITY, INFINITY, codes1, M1, walk_full ? codes2 : NULL, M2};
         walk_ctx wc = {&ix, lut, walk_full, yr, C1w, C2w, sub1, sub2};
         int32_t n_dist = 0, n_expand = 0, n_up = 0;
         int wn = 0, ntouch = 0;
@@ -318,8 +403,8 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                     }
                     /* deciding comparisons: the best neighbour against the runner-up,
                        and against the current node */
-                    if (second >= 0) note_gap(&g, dbest, best, dsecond, second, 1);
-                    if (best >= 0 && cmp_note(&g, dbest, best, dcur, cur, 1)) {
+                    if (second >= 0) note_gap(&g, GAP_UPPER_SECOND, dbest, best, dsecond, second);
+                    if (best >= 0 && cmp_note(&g, GAP_UPPER_MOVE, dbest, best, dcur, cur)) {
                         cur = best;
                         dcur = dbest;
                     } else {
@@ -344,11 +429,10 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                    the ef' best scored nodes, so this is the (ef'+1)-th best */
                 double od0 = INFINITY;
                 int32_t oid = -1;
-                int ended_by_break = 0;
                 while (cn > 0) {
                     /* the search-time cap T of Section 3.1: stop once T distance
                        computations have been made (checked before each expansion) */
-                    if (tcap > 0 && n_dist >= tcap) { ended_by_break = 1; break; }
+                    if (tcap > 0 && n_dist >= tcap) break;
                     /* c = nearest element of C; its order against the runner-up decides
                        which element is expanded first */
                     int64_t bc = 0, b2 = -1;
@@ -356,7 +440,7 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                         if (key_less(cd[s], ci[s], cd[bc], ci[bc])) { b2 = bc; bc = s; }
                         else if (b2 < 0 || key_less(cd[s], ci[s], cd[b2], ci[b2])) b2 = s;
                     }
-                    if (b2 >= 0) note_gap(&g, cd[bc], ci[bc], cd[b2], ci[b2], 1);
+                    if (b2 >= 0) note_gap(&g, GAP_RUNNER, cd[bc], ci[bc], cd[b2], ci[b2]);
                     double dc = cd[bc];
                     int32_t c = ci[bc];
                     cd[bc] = cd[cn - 1]; ci[bc] = ci[cn - 1]; cn--;
@@ -365,13 +449,12 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                     for (int s = 1; s < wn; s++)
                         if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
                     if (key_less(wd[bf], wi[bf], dc, c)) {                 /* c further than f */
-                        note_gap(&g, wd[bf], wi[bf], dc, c, 1);
-                        ended_by_break = 1;
+                        note_gap(&g, GAP_BREAK, wd[bf], wi[bf], dc, c);
                         break;
                     }
                     /* c is expanded next: decided against the runner-up in C (above) and
                        against the best node outside W */
-                    if (oid >= 0) note_gap(&g, dc, c, od0, oid, 1);
+                    if (oid >= 0) note_gap(&g, GAP_OUTSIDE, dc, c, od0, oid);
                     n_expand++;
                     const int32_t *row = adj0 + (int64_t)c * deg;
                     for (int s = 0; s < deg; s++) {
@@ -408,13 +491,15 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
                         }
                     }
                 }
-                /* termination: had the best node outside W ranked inside it, the walk would
-                   have continued */
-                if (!ended_by_break && oid >= 0) {
+                /* the end, however it came (C empty, a popped node beyond the worst of W, or
+                   the cap T): had the best node outside W ranked inside it, the walk would
+                   have had it to expand (the result-list view: W holds an unexpanded member),
+                   and W's members would differ */
+                if (oid >= 0) {
                     int bf = 0;
                     for (int s = 1; s < wn; s++)
                         if (key_less(wd[bf], wi[bf], wd[s], wi[s])) bf = s;
-                    note_gap(&g, wd[bf], wi[bf], od0, oid, 1);
+                    note_gap(&g, GAP_END, wd[bf], wi[bf], od0, oid);
                 }
             }
             for (int s = 0; s < ntouch; s++) visited[touched[s]] = 0;
@@ -439,45 +524,29 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
         int32_t *oi = ids + q * k;
         double *od = dists + q * k;
         for (int s = 0; s < k; s++) { oi[s] = -1; od[s] = INFINITY; }
+        double nd = INFINITY;           /* the distance that follows the k returned */
 
         if (shortlist < 0) {
             /* no refinement: top-k of W by walk distance; the order of the k returned
                and the k-th against the (k+1)-th decide the output */
             for (int s = 0; s < k && s < wn; s++) {
                 oi[s] = wi[s]; od[s] = wd[s];
-                if (s + 1 < wn) note_gap(&g, wd[s], wi[s], wd[s + 1], wi[s + 1], 1);
+                if (s + 1 < wn) note_gap(&g, GAP_OUT_WALK, wd[s], wi[s], wd[s + 1], wi[s + 1]);
             }
+            if (k < wn) nd = wd[k];
         } else {
             /* Shortlist R = the R best of W (at most 10 refined by default, Sec. 5.1);
                the R-th against the (R+1)-th decides its membership */
             int Rn = shortlist > 0 ? shortlist : 10;
             if (Rn < k) Rn = k;
             if (Rn > wn) Rn = wn;
-            if (Rn > 0 && Rn < wn) note_gap(&g, wd[Rn - 1], wi[Rn - 1], wd[Rn], wi[Rn], 1);
+            if (Rn > 0 && Rn < wn) note_gap(&g, GAP_SHORTLIST, wd[Rn - 1], wi[Rn - 1], wd[Rn], wi[Rn]);
             /* Refined reconstruction y^ = sum_j beta_j q(v_j), G = [q(x), q(g1..g8)]; with a
                product codebook each block of coordinates takes the weights of its own
                codeword (one codeword per block: the shared 0-byte weights) */
             for (int r = 0; r < Rn; r++) {
-                int32_t i = wi[r];
-                for (int t = 0; t < d; t++) yh[t] = 0.0;
-                for (int j = 0; j <= ORC_KBETA; j++) {
-                    int32_t v = j == 0 ? i : adj0[(int64_t)i * deg + (j - 1)];
-                    if (j > 0 && (j - 1 >= deg || v < 0)) continue;     /* zero column */
-                    decode2(&ix, off1, len1, off2, len2, v, xh);
-                    for (int m = 0; m < bM; m++) {
-                        int b = bK > 1 ? beta[(int64_t)i * bM + m] : 0;
-                        double w = (double)B[((int64_t)m * bK + b) * (ORC_KBETA + 1) + j];
-                        for (int t = offb[m]; t < offb[m] + lenb[m]; t++) yh[t] += w * xh[t];
-                    }
-                }
-                /* Exact squared L2 to the refined reconstruction */
-                double s = 0.0;
-                for (int t = 0; t < d; t++) {
-                    double diff = yr[t] - yh[t];
-                    s += diff * diff;
-                }
-                rd[r] = s;
-                ri[r] = i;
+                rd[r] = refined_dist(&ix, off1, len1, off2, len2, offb, lenb, yr, wi[r], xh, yh);
+                ri[r] = wi[r];
             }
             for (int a = 0; a < Rn; a++) {
                 int m = a;
@@ -489,8 +558,9 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
             /* the order of the k returned, and the k-th against the (k+1)-th */
             for (int s = 0; s < k && s < Rn; s++) {
                 oi[s] = ri[s]; od[s] = rd[s];
-                if (s + 1 < Rn) note_gap(&g, rd[s], ri[s], rd[s + 1], ri[s + 1], 0);
+                if (s + 1 < Rn) note_gap(&g, GAP_OUT_REFINED, rd[s], ri[s], rd[s + 1], ri[s + 1]);
             }
+            if (k < Rn) nd = rd[k];
         }
         if (stats) {
             stats[q * 3 + 0] = n_dist;
@@ -498,9 +568,68 @@ int orc_search(int64_t N, int d, int M1, int M2, const float *R, const float *C1
             stats[q * 3 + 2] = n_up;
         }
         if (min_gap) min_gap[q] = g.gap;
+        if (min_gap_walk) min_gap_walk[q] = g.gap_walk;
+        if (next_dist) next_dist[q] = nd;
     }
     free(yr); free(lut); free(sub1); free(sub2); free(visited); free(touched); free(cd); free(ci);
     free(wd); free(wi); free(xh); free(yh); free(rd); free(ri);
+    return 0;
+}
+
+/* Walk distance and refined distance of m given ids per query, from their definitions
+   (rotation, ADC table or full decode, refined reconstruction), without any walk: for
+   checking a result list id by id.  ids [nq][m] (-1 gives +inf); walk_d, ref_d [nq][m]. */
+int orc_dists(int64_t N, int d, int M1, int M2, const float *R, const float *C1,
+              const float *C2, const uint8_t *codes1, const uint8_t *codes2,
+              const uint8_t *beta, const float *B, int bM, int bK, int deg, const int32_t *adj0,
+              int64_t nq, const float *Q, int m, const int32_t *ids, const float *C1w, int walk_full,
+              const float *C2w, double *walk_d, double *ref_d)
+{
+    orc_index ix = {N, d, M1, M2, deg, 0, 0, -1, R, C1, C2, B, bM, bK,
+                    codes1, codes2, beta, adj0, NULL, NULL};
+    if (!C1w) C1w = C1;
+    if (!C2w) C2w = C2;
+    int off1[256], len1[256], off2[256], len2[256], offb[256], lenb[256];
+    if (M1 > 256 || M2 > 256 || bM < 1 || bM > 256 || bM > d || bK < 1 || bK > 256) return -1;
+    split_offsets(d, M1, off1, len1);
+    split_offsets(d, M2, off2, len2);
+    split_offsets(d, bM, offb, lenb);
+    int *sub1 = malloc(sizeof(int) * d), *sub2 = malloc(sizeof(int) * d);
+    for (int j = 0; j < M1; j++) for (int t = off1[j]; t < off1[j] + len1[j]; t++) sub1[t] = j;
+    for (int j = 0; j < M2; j++) for (int t = off2[j]; t < off2[j] + len2[j]; t++) sub2[t] = j;
+    double *yr = malloc(sizeof(double) * d);
+    double *lut = malloc(sizeof(double) * 256 * M1);
+    double *xh = malloc(sizeof(double) * d);
+    double *yh = malloc(sizeof(double) * d);
+    for (int64_t q = 0; q < nq; q++) {
+        const float *y = Q + q * d;
+        walk_ctx wc = {&ix, lut, walk_full, yr, C1w, C2w, sub1, sub2};
+        for (int t = 0; t < d; t++) {
+            double s = 0.0;
+            for (int u = 0; u < d; u++) s += (double)R[(int64_t)t * d + u] * (double)y[u];
+            yr[t] = s;
+        }
+        for (int j = 0; j < M1 && !walk_full; j++)
+            for (int c = 0; c < 256; c++) {
+                double s = 0.0;
+                for (int t = off1[j]; t < off1[j] + len1[j]; t++) {
+                    double diff = yr[t] - (double)C1w[(int64_t)c * d + t];
+                    s += diff * diff;
+                }
+                lut[j * 256 + c] = s;
+            }
+        for (int r = 0; r < m; r++) {
+            int32_t i = ids[q * m + r];
+            if (i < 0 || i >= N) {
+                walk_d[q * m + r] = INFINITY;
+                ref_d[q * m + r] = INFINITY;
+                continue;
+            }
+            walk_d[q * m + r] = wdist(&wc, i);
+            ref_d[q * m + r] = refined_dist(&ix, off1, len1, off2, len2, offb, lenb, yr, i, xh, yh);
+        }
+    }
+    free(sub1); free(sub2); free(yr); free(lut); free(xh); free(yh);
     return 0;
 }
 
