@@ -70,6 +70,19 @@ def gaussian_mixture(n: int, d: int = 96, n_centres: int = 64, sigma: float = 0.
     return np.zeros((0, d), np.float32) if out is None else out
 
 
+def sphere(n: int, d: int = 96, seed: int = SEED, stream: int = STREAM_BASE, start: int = 0) -> np.ndarray:
+    """Directions drawn uniformly on the unit sphere (normalised N(0, I)), float32 [n][d]:
+    the mixture without any cluster structure, a stress input on which graph walks are long
+    (every query sees a flat distance landscape)."""
+    def draw(g, rows):
+        x = g.standard_normal((rows, d))
+        x /= np.linalg.norm(x, axis=1, keepdims=True)
+        return x.astype(np.float32)
+
+    out = _chunked(n, start, seed, stream, draw)
+    return np.zeros((0, d), np.float32) if out is None else out
+
+
 def sift_profiles(d: int = 128, n_profiles: int = 1024, seed: int = SEED) -> np.ndarray:
     g = _rng(seed, STREAM_CENTRES, 1)
     return g.gamma(0.5, 40.0, size=(n_profiles, d))

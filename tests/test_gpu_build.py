@@ -63,6 +63,24 @@ def test_device_built_graph_is_well_formed(builds):
     assert same > 0.95
 
 
+def test_device_built_graph_against_the_oracle_build(builds):
+    # the oracle's FP64 batched insertion (orc_build_graph, Section 5.1) on the device build's
+    # own rotation, codes and levels: the upper levels (built on the host) are identical, and
+    # the level-0 rows differ only where an FP32 device distance resolved a near-tie the other
+    # way (and where such a difference propagated to later insertions)
+    from oracle.graph import build_graph
+    h, ix, xb = builds[1]
+    xr = xb.astype(np.float64) @ ix.R.astype(np.float64).T
+    a0, off, ua, ep, ml = build_graph(xr, ix.extra["xh"], ix.levels, deg=32, deg_up=32, efc=40, batch_max=512,
+                                      batch_div=16)
+    assert ep == ix.ep and ml == ix.max_level
+    same = (a0 == ix.adj0).all(1)
+    print(f"level-0 rows identical to the oracle build: {same.mean():.2%}; upper rows identical: "
+          f"{(ua == ix.upper_adj).all(1).mean():.2%}")
+    assert same.mean() > 0.95
+    assert (ua == ix.upper_adj).all(1).mean() > 0.95
+
+
 def test_device_codeword_assignment_is_the_hosts(builds):
     # the device assignment reproduces the host's arithmetic: wherever a vector's G(x) (its
     # first eight neighbours) is the same in both builds, so is its codeword
@@ -120,7 +138,7 @@ def test_device_built_index_parity(builds):
     h, ix, xb = builds[1]
     xq = dg.gaussian_mixture(300, 96, 128, stream=dg.STREAM_QUERY)
     ref = oracle.search(ix, xq, 10, 64)
-    compare(ref, *gpu_search(h, xq, 10, 64), max_exempt=0.1)
+    compare(ref, *gpu_search(h, xq, 10, 64), max_exempt=0.02)             # measured 1 %
 
 
 def test_device_build_in_two_calls():

@@ -52,8 +52,9 @@ SAMPLE = np.append(np.arange(0, N_QUERY, 10), N_QUERY - 1)
 
 # (form, k, efSearch, bound on the near-tie exempt share): the bench's recall-target and
 # headline forms at efSearch 64, the sweep's ends (efSearch 16 at k = 1, efSearch 256), k = 1
-CASES = [("plain_fp32", 10, 64, 0.1), ("batched4_fp16", 10, 64, 0.1), ("plain_fp32", 1, 16, 0.05),
-         ("batched4_fp16", 1, 64, 0.05), ("batched4_fp16", 10, 256, 0.15)]
+# (measured on GB300: 2.8 %, 0.4 %, 0.2 %, 0.4 %, 8.6 %)
+CASES = [("plain_fp32", 10, 64, 0.04), ("batched4_fp16", 10, 64, 0.01), ("plain_fp32", 1, 16, 0.01),
+         ("batched4_fp16", 1, 64, 0.01), ("batched4_fp16", 10, 256, 0.10)]
 
 
 @pytest.mark.parametrize("form,k,ef,max_exempt", CASES)

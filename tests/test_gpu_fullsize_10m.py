@@ -73,10 +73,11 @@ def oracle_per_query_ef(ix, xq, k, efq, beam, c1_walk):
     for ef in np.unique(efq):
         rows = np.flatnonzero(efq == ef)
         r = oracle.search(ix, xq[rows].astype(np.float32), k, int(ef), beam=beam, c1_walk=c1_walk)
-        for key in ("ids", "dists", "stats", "gap"):
+        for key in ("ids", "dists", "stats", "gap", "gap_walk", "next_dist"):
             if key not in ref:
                 ref[key] = np.empty((len(xq),) + r[key].shape[1:], r[key].dtype)
             ref[key][rows] = r[key]
+        ref["ctx"] = dict(r["ctx"], Q=np.ascontiguousarray(xq, np.float32))
     return ref
 
 

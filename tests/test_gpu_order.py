@@ -54,7 +54,7 @@ def test_ordered_equals_query_order_and_oracle(request, name, form):
     c1h = ix.C1.astype(np.float16).astype(np.float32) if f.get("lut_prec") else None
     ref = oracle.search(ix, xq, 10, 64, shortlist=f.get("shortlist", 0), beam=f.get("beam", 1),
                         tcap=f.get("tcap", 0), c1_walk=c1h)
-    compare(ref, *a, max_exempt=0.1)
+    compare(ref, *a, max_exempt=0.06)                     # measured <= 4.7 %
 
 
 def test_ordered_uint8_per_query_ef(sift2k):
@@ -67,7 +67,7 @@ def test_ordered_uint8_per_query_ef(sift2k):
     b = search(h, q8, 10, 128, lc.LC_ORDER_NEVER, efq=efq, u8=True, beam=4)
     same(a, b)
     ref = oracle_uneven(ix, q8.astype(np.float32), 10, efq, beam=4)
-    compare(ref, *a, max_exempt=0.25)
+    compare(ref, *a, max_exempt=0.02)                     # measured 0
 
 
 def test_ordered_full_walk(opq3k):

@@ -1,12 +1,22 @@
 """GPU parity: the CUDA search path, called through the C ABI, against the FP64 oracle on
 the same index (built by the oracle).
 
-Bar (plain mode, FP32 tables): neighbour ids and visit counts (distinct nodes scored at
-level 0, level-0 expansions, upper-level evaluations) are identical to the oracle's for
-every query whose deciding comparisons are not FP64 near-ties (relative gap >= 1e-6, as
-recorded by the oracle); returned distances agree within 1e-5 relative.  Exempt queries
-are counted and bounded.
+Bar (plain mode, FP32 tables), per query, by what the oracle's near-tie record says:
+* no deciding comparison within 1e-6 relative: neighbour ids and visit counts (distinct nodes
+  scored at level 0, level-0 expansions, upper-level evaluations) identical to the oracle's,
+  returned distances within 1e-5 relative;
+* near-ties only in the order of the k returned (the walk and the shortlist are decided):
+  visit counts identical, ids identical at every position outside a run of near-tied
+  distances, distances within 1e-5 relative position by position;
+* every query, near-tie exempt or not: a valid result list (distinct ids, ascending by
+  (distance, id), padding only at the end) whose every distance is the oracle's distance for
+  that id, recomputed directly (ADC sum or refined reconstruction), within 1e-5 relative;
+  over the batch, the GPU returns all but at most 0.5 % of the oracle's ids.
+The share of exempt queries is bounded per test.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -61,17 +71,83 @@ def gpu_search(h, xq, k, ef, shortlist=0, device=True, visited_log=0, beam=1, tc
     return ids, ds, st
 
 
-def compare(ref, ids, ds, st, max_exempt=0.05):
+def _clear_positions(d, nxt):
+    """Positions of the oracle's returned list whose distance is clear (>= TIE relative) of
+    both neighbours in the order (the one after the last being the next distance)."""
+    full = np.concatenate([d, nxt[:, None]], axis=1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r = np.abs(np.diff(full, axis=1)) / np.maximum(np.abs(full[:, 1:]), np.abs(full[:, :-1]))
+    r = np.where(np.isinf(full[:, 1:]) | np.isinf(full[:, :-1]), np.inf, r)
+    clear = r >= TIE                                   # position p against p + 1
+    clear[:, 1:] &= r[:, :-1] >= TIE                   # and against p - 1
+    return clear
+
+
+def check_valid(ref, ids, ds):
+    """Every returned list is valid and every returned distance is the oracle's, recomputed
+    directly for that id.  Returns nothing; asserts."""
+    ctx = ref["ctx"]
+    ix = ctx["ix"]
+    nq, k = ids.shape
+    valid = ids >= 0
+    assert (ids[valid] < ix.N).all()
+    # padding only at the end, with +inf
+    assert (valid[:, 1:] <= valid[:, :-1]).all(), "padding before a result"
+    assert np.isinf(ds[~valid]).all()
+    # distinct ids per query
+    srt = np.sort(np.where(valid, ids, -1 - np.arange(k)), axis=1)
+    assert (np.diff(srt, axis=1) != 0).all(), "a query returned an id twice"
+    # ascending by (distance, id)
+    both = valid[:, 1:] & valid[:, :-1]
+    up = (ds[:, 1:] > ds[:, :-1]) | ((ds[:, 1:] == ds[:, :-1]) & (ids[:, 1:] > ids[:, :-1]))
+    assert up[both].all(), "a result list is out of (distance, id) order"
+    walk, refined = oracle.dists(ix, ctx["Q"], np.ascontiguousarray(ids, np.int32), c1_walk=ctx["c1_walk"],
+                                 walk_full=ctx["walk_full"], c2_walk=ctx["c2_walk"])
+    want = walk if ctx["shortlist"] < 0 else refined
+    np.testing.assert_allclose(ds[valid], want[valid], rtol=RTOL)
+
+
+def _log_shares(rec):
+    path = os.environ.get("LC_PARITY_LOG")
+    if path:
+        rec["test"] = os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+
+
+def compare(ref, ids, ds, st, max_exempt=0.05, max_loss=0.002):
+    """Checks one batch against the oracle (the bar in the module docstring); returns the
+    share of near-tie exempt queries."""
     ok = ref["gap"] >= TIE
+    walk_ok = ref["gap_walk"] >= TIE
+    out_only = walk_ok & ~ok
     exempt = 1.0 - ok.mean()
     assert exempt <= max_exempt, f"{exempt:.3%} of queries are near-tie exempt"
+    # decided queries: bit-exact ids and counts, distances within RTOL
     bad_ids = np.flatnonzero(ok & (ids != ref["ids"]).any(1))
-    bad_st = np.flatnonzero(ok & (st != ref["stats"]).any(1))
+    bad_st = np.flatnonzero(walk_ok & (st != ref["stats"]).any(1))
     assert bad_ids.size == 0, f"ids differ on queries {bad_ids[:10]} (of {ok.sum()} non-exempt)"
     assert bad_st.size == 0, f"visit counts differ on queries {bad_st[:10]}: {st[bad_st[:3]]} vs {ref['stats'][bad_st[:3]]}"
     fin = np.isfinite(ref["dists"][ok])
     np.testing.assert_allclose(ds[ok][fin], ref["dists"][ok][fin], rtol=RTOL)
     assert (np.isinf(ds[ok][~fin]) & (ids[ok][~fin] == -1)).all()
+    # near-ties in the output order only: the same candidates, ids equal outside tie runs
+    if out_only.any():
+        clear = _clear_positions(ref["dists"][out_only], ref["next_dist"][out_only])
+        a, b = ids[out_only], ref["ids"][out_only]
+        assert np.array_equal(a[clear], b[clear]), "ids differ outside a near-tie run"
+        fin = np.isfinite(ref["dists"][out_only])
+        np.testing.assert_allclose(ds[out_only][fin], ref["dists"][out_only][fin], rtol=RTOL)
+        assert np.array_equal(np.isinf(ds[out_only]), ~fin)
+    # every query: a valid list of correctly scored ids
+    check_valid(ref, ids, ds)
+    # over the batch: the oracle's ids the GPU returns too
+    rv = ref["ids"] >= 0
+    hit = np.array([np.isin(r[m], g).sum() for r, m, g in zip(ref["ids"], rv, ids)])
+    loss = 1.0 - hit.sum() / max(rv.sum(), 1)
+    assert loss <= max_loss, f"the GPU misses {loss:.3%} of the oracle's ids"
+    _log_shares(dict(nq=len(ids), exempt=float(exempt), walk_exempt=float(1.0 - walk_ok.mean()),
+                     out_only=float(out_only.mean()), loss=float(loss)))
     return exempt
 
 
@@ -81,8 +157,10 @@ def test_parity_pq16(mix3k, k, ef, shortlist):
     ix, xb, xq = mix3k
     h = handle("mix3k", ix)
     ref = oracle.search(ix, xq, k, ef, shortlist=shortlist)
-    # every adjacent pair of the k returned is a deciding comparison: more near-ties at k = 100
-    compare(ref, *gpu_search(h, xq, k, ef, shortlist), max_exempt=0.25 if ef >= 256 or k >= 100 else 0.05)
+    # every adjacent pair of the k returned is a deciding comparison: more near-ties at k = 100;
+    # walks of efSearch 256 over a third of a 3,000-node graph make many deciding comparisons
+    # (measured: 0.3 % at efSearch <= 64, 21 % at 256, 5 % at k = 100)
+    compare(ref, *gpu_search(h, xq, k, ef, shortlist), max_exempt=0.23 if ef >= 256 else 0.07 if k >= 100 else 0.01)
 
 
 @pytest.mark.parametrize("name", ["opq3k", "sift2k"])
@@ -90,10 +168,11 @@ def test_parity_pq16(mix3k, k, ef, shortlist):
 def test_parity_64_and_128_byte_codes(request, name, ef):
     ix, xb, xq = request.getfixturevalue(name)
     h = handle(name, ix)
+    bound = 0.02 if ef <= 32 else 0.09                      # measured: <= 0.7 %, <= 7 %
     ref = oracle.search(ix, xq, 10, ef)
-    compare(ref, *gpu_search(h, xq, 10, ef), max_exempt=0.1)
+    compare(ref, *gpu_search(h, xq, 10, ef), max_exempt=bound)
     ref = oracle.search(ix, xq, 10, ef, shortlist=-1)
-    compare(ref, *gpu_search(h, xq, 10, ef, shortlist=-1), max_exempt=0.1)
+    compare(ref, *gpu_search(h, xq, 10, ef, shortlist=-1), max_exempt=bound)
 
 
 @pytest.mark.parametrize("beam", [2, 4, 8])
@@ -104,14 +183,14 @@ def test_parity_batched(request, name, beam):
     h = handle(name, ix)
     for shortlist in (0, -1):
         ref = oracle.search(ix, xq, 10, 64, shortlist=shortlist, beam=beam)
-        compare(ref, *gpu_search(h, xq, 10, 64, shortlist, beam=beam), max_exempt=0.1)
+        compare(ref, *gpu_search(h, xq, 10, 64, shortlist, beam=beam), max_exempt=0.04)    # measured <= 3 %
 
 
 def test_batched_spill_and_wide(mix3k):
     ix, xb, xq = mix3k
     h = handle("mix3k", ix)
     ref = oracle.search(ix, xq, 10, 256, beam=4)
-    compare(ref, *gpu_search(h, xq, 10, 256, visited_log=10, beam=4), max_exempt=0.3)
+    compare(ref, *gpu_search(h, xq, 10, 256, visited_log=10, beam=4), max_exempt=0.08)    # measured 6.7 %
 
 
 @pytest.mark.parametrize("tcap", [60, 250])
@@ -121,7 +200,7 @@ def test_parity_tcap(opq3k, tcap, beam):
     ix, xb, xq = opq3k
     h = handle("opq3k", ix)
     ref = oracle.search(ix, xq, 10, 128, beam=beam, tcap=tcap)
-    compare(ref, *gpu_search(h, xq, 10, 128, beam=beam, tcap=tcap), max_exempt=0.1)
+    compare(ref, *gpu_search(h, xq, 10, 128, beam=beam, tcap=tcap), max_exempt=0.01)     # measured 0
 
 
 @pytest.mark.parametrize("name", ["mix3k", "opq3k", "sift2k"])
@@ -134,7 +213,8 @@ def test_parity_fp16_codebook(request, name, beam):
     c1h = ix.C1.astype(np.float16).astype(np.float32)
     for shortlist in (0, -1):
         ref = oracle.search(ix, xq, 10, 64, shortlist=shortlist, beam=beam, c1_walk=c1h)
-        compare(ref, *gpu_search(h, xq, 10, 64, shortlist, beam=beam, lut_prec=lc.LC_LUT_FP16), max_exempt=0.1)
+        compare(ref, *gpu_search(h, xq, 10, 64, shortlist, beam=beam, lut_prec=lc.LC_LUT_FP16),
+                max_exempt=0.035)                                                        # measured <= 2.5 %
 
 
 def test_parity_10k_workload(mix10k):
@@ -142,7 +222,7 @@ def test_parity_10k_workload(mix10k):
     ix, xb, xq = mix10k
     h = handle("mix10k", ix)
     ref = oracle.search(ix, xq, 10, 64)
-    ex = compare(ref, *gpu_search(h, xq, 10, 64))
+    ex = compare(ref, *gpu_search(h, xq, 10, 64), max_exempt=0.025)                       # measured 1.4 %
     print(f"near-tie exempt: {ex:.2%}")
 
 
@@ -162,7 +242,7 @@ def test_visited_spill_to_global_table(mix3k):
     h = handle("mix3k", ix)
     ref = oracle.search(ix, xq, 10, 256)
     assert ref["stats"][:, 0].max() > 512
-    compare(ref, *gpu_search(h, xq, 10, 256, visited_log=10), max_exempt=0.25)
+    compare(ref, *gpu_search(h, xq, 10, 256, visited_log=10), max_exempt=0.23)            # measured 21 %
 
 
 def test_exhaustive_walk_equals_oracle():
@@ -196,7 +276,7 @@ def test_ragged_query_counts(mix3k):
     for nq in (1, 3, 33, 257):
         sub = xq[:nq]
         ref = oracle.search(ix, sub, 5, 40)
-        compare(ref, *gpu_search(h, sub, 5, 40), max_exempt=0.34)
+        compare(ref, *gpu_search(h, sub, 5, 40), max_exempt=0.01)                          # measured <= 0.4 %
 
 
 def test_empty_index_and_no_queries():

@@ -50,9 +50,11 @@ def oracle_uneven(ix, xq, k, efq, beam=1):
         r = oracle.search(ix, xq[rows], k, int(ef), beam=beam)
         if ref is None:
             ref = {key: np.empty((len(xq),) + np.shape(v)[1:], np.asarray(v).dtype) for key, v in r.items()
-                   if key in ("ids", "dists", "stats", "gap")}
+                   if key in ("ids", "dists", "stats", "gap", "gap_walk", "next_dist")}
+            ctx = dict(r["ctx"], Q=np.ascontiguousarray(xq, np.float32))
         for key in ref:
             ref[key][rows] = r[key]
+    ref["ctx"] = ctx
     return ref
 
 
@@ -64,7 +66,7 @@ def test_uneven_ef_parity(request, name, beam):
     efq = datagen.uneven_ef(len(xq))
     assert len(np.unique(efq)) == 5
     ref = oracle_uneven(ix, xq, 10, efq, beam)
-    compare(ref, *search_ex(h, xq, 10, 256, efq, beam), max_exempt=0.15)
+    compare(ref, *search_ex(h, xq, 10, 256, efq, beam), max_exempt=0.11)     # measured <= 9.7 %
 
 
 @pytest.mark.parametrize("device", [True, False])
@@ -119,4 +121,4 @@ def test_u8_queries(sift2k, device, uneven):
         assert np.array_equal(x, y)
     ref = oracle_uneven(ix, xq, 10, efq) if uneven else oracle.search(ix, xq, 10, bound)
     # the widest searches make the most deciding comparisons, hence the most near-ties
-    compare(ref, *a, max_exempt=0.25)
+    compare(ref, *a, max_exempt=0.08)                                         # measured <= 6.5 %

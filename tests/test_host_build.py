@@ -62,6 +62,19 @@ def test_graph_structure(libbuilt):
     check_structure(libbuilt[0])
 
 
+def test_graph_equals_the_oracle_build_on_the_same_codes(libbuilt):
+    # Section 5.1's batched insertion, restated by the oracle in FP64 (orc_build_graph) on the
+    # library's own rotation, codes and levels: the library's host build gives the same graph,
+    # row for row and in row order, at level 0 and above, with the same entry point
+    from oracle.graph import build_graph
+    ix = libbuilt[0]
+    a0, off, ua, ep, ml = build_graph(ix.extra["xr"], ix.extra["xh"], ix.levels, deg=32, deg_up=32, efc=40,
+                                      batch_max=256, batch_div=16)
+    assert np.array_equal(a0, ix.adj0)
+    assert np.array_equal(ua, ix.upper_adj) and np.array_equal(off, ix.upper_off)
+    assert ep == ix.ep and ml == ix.max_level
+
+
 def test_codewords_minimise_refinement_loss(libbuilt):
     ix = libbuilt[0]
     assert np.array_equal(ix.B[0], refine.e0().astype(np.float32))

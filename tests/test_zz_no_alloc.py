@@ -79,6 +79,44 @@ def test_matches_lc_search_on_two_calls(setup, k, ef):
         assert np.array_equal(np.isinf(ds), ~fin)
 
 
+@pytest.fixture(scope="module")
+def wide():
+    # 60,000 directions uniform on the sphere (no cluster structure), built by the library's
+    # host build: walks at efSearch 256 score about 6,000 distinct nodes each, so every query
+    # keeps most of its visited set in the global spill table
+    from paper_1804_09996_gb300 import datagen as dg
+    d, M1, M2 = 96, 32, 31
+    h = lc.lc_create(lc.lc_default_params(d, M1, M2, use_opq=1))
+    lc.lc_train(h, dg.sphere(10_000, d, stream=dg.STREAM_TRAIN))
+    lc.lc_add(h, dg.sphere(60_000, d, stream=dg.STREAM_BASE))
+    yield h, dg.sphere(256, d, stream=dg.STREAM_QUERY)
+    lc.lc_free(h)
+
+
+def test_wide_walks_match_lc_search_on_two_calls(setup, wide):
+    # max(ef, k) = 256, the widest walk the call accepts, with visited sets far beyond the
+    # shared-memory table: each query in flight has the spill table lc_search gives it, so
+    # no query overflows and every output equals lc_search's
+    import torch
+    h, xq = wide
+    nq, k, ef = len(xq), 10, 256
+    q = torch.from_numpy(np.ascontiguousarray(xq)).cuda()
+    s = torch.cuda.Stream()
+    ref = _outputs(nq, k)
+    lc.lc_search(h, q, nq, lc.lc_default_search_params(k, ef, shortlist=-1), *ref, s)
+    s.synchronize()
+    ref = [t.cpu().numpy() for t in ref]
+    assert (ref[2][:, 0] > 4096).all(), "the case must visit beyond 4,096 nodes per query"
+    for call in range(2):
+        got = _outputs(nq, k)
+        lc.lc_search_walk_noalloc(h, q, nq, k, ef, *got, s)
+        s.synchronize()
+        ids, ds, st = (t.cpu().numpy() for t in got)
+        assert (st[:, 0] > 0).all(), f"call {call}: a query overflowed its visited tables"
+        assert np.array_equal(ids, ref[0]) and np.array_equal(st, ref[2]), f"call {call}: results differ"
+        np.testing.assert_allclose(ds, ref[1], rtol=RTOL)
+
+
 def test_sizes_beyond_the_maximum_are_rejected(setup):
     import torch
     h, ix, xq = setup
