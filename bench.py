@@ -89,14 +89,14 @@ def kernel_hash():
 
 
 def profiled_traffic(workload: str, form: str):
-    """DRAM bytes per walk launch of the given form (e.g. 'batched_fp16_ef48') from the
-    committed ncu summary, if it was taken on the current kernel source (its
+    """DRAM bytes per level-0 walk launch of the given form (e.g. 'batched_fp16_ef48') from
+    the committed ncu summary, if it was taken on the current kernel source (its
     'kernel_source_sha256_16' line must match)."""
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         txt = open(f).read()
         m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
         w = re.search(r"workload:\s*(\S+)", txt)
-        t = re.search(r"dram_bytes_per_walk_launch_" + form + r":\s*([0-9.eE+]+)", txt)
+        t = re.search(r"dram_bytes_per_level0_launch_" + form + r":\s*([0-9.eE+]+)", txt)
         if m and w and t and w.group(1) == workload and m.group(1) == kernel_hash():
             return float(t.group(1))
     return None
@@ -301,12 +301,26 @@ def time_oracle(oix, xq, k, ef, budget_s, efq=None, threads=1):
     return state["done"], time.perf_counter() - t0
 
 
+def quantile_ci(x, p, z=1.96):
+    """Distribution-free ~95 % confidence interval of the p-quantile of the population the
+    sample x was drawn from: the order statistics whose ranks bracket n*p by z binomial
+    standard deviations."""
+    x = np.sort(np.asarray(x))
+    n = len(x)
+    sd = np.sqrt(n * p * (1 - p))
+    lo = int(np.clip(np.floor(n * p - z * sd), 1, n))
+    hi = int(np.clip(np.ceil(n * p + z * sd), 1, n))
+    return [float(x[lo - 1]), float(x[hi - 1])]
+
+
 def measure_serving(lc, h, xq, gt, k, args, sp_best):
     """Serving through lc_serve_*.  (1) Saturation: 512-query requests with the headline
-    parameters (same results as the batch search) submitted back to back with up to 16 in
-    flight; QPS over the whole run.  (2) Open loop: Poisson arrivals at fixed query rates,
+    parameters (same results as the batch search) submitted back to back, up to 96
+    outstanding (16 launch slots; the requests waiting when a slot frees run merged into one
+    launch); QPS over the whole run.  (2) Open loop: Poisson arrivals at fixed query rates,
     request sizes log-uniform in [1, 512], k in {1, 10, 100}, efSearch log-uniform in
-    [16, 512], plain; latency = completion - arrival on the host clock."""
+    [16, 512], plain walk with the FP16 level-1 codebook; latency = completion - arrival on
+    the host clock, p99 with a 95 % order-statistic interval."""
     rng = np.random.default_rng(7)
     budget = 8 << 30
     srv = lc.lc_serve_open(h, budget, 16, 512)
@@ -318,7 +332,7 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
         def cb_store(rid, st, i, d):
             done[rid] = (time.perf_counter(), st, None if i is None else i[:, 0].copy())
 
-        n_req = 120
+        n_req = 400
         starts = [(j * 512) % (min(len(xq), len(gt)) - 512) for j in range(n_req)]   # queries with exact neighbours
         t0 = time.perf_counter()
         ids = []
@@ -326,7 +340,7 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
             cb = lc.make_request_cb(cb_store)
             cbs.append(cb)
             ids.append(lc.lc_serve_submit(srv, xq[starts[j]:starts[j] + 512], sp_best, cb))
-            while len(ids) - len(done) > 24:
+            while len(ids) - len(done) > 96:
                 lc.lc_serve_poll(srv, 1)
         while len(done) < n_req:
             lc.lc_serve_poll(srv, 5)
@@ -334,13 +348,13 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
         ok = all(v[1] == 0 for v in done.values())
         rec = float(np.mean([(done[r][2] == gt[s:s + 512]).mean() for r, s in zip(ids, starts)]))
         out["saturation"] = {"qps": n_req * 512 / (t1 - t0), "requests": n_req, "request_size": 512,
-                             "recall_at_1": rec, "all_ok": ok}
+                             "max_outstanding": 96, "recall_at_1": rec, "all_ok": ok}
         # open loop
         sizes_all = np.exp(rng.uniform(0, np.log(512), size=100000)).astype(int)
         mean_size = float(sizes_all.mean())
         points = []
         for lam in args.serve_rates:
-            n = int(min(2000, max(200, lam * args.serve_seconds / mean_size)))
+            n = int(min(6000, max(500, lam * args.serve_seconds / mean_size)))
             gaps = rng.exponential(mean_size / lam, size=n)
             arrive = np.cumsum(gaps)
             sizes = np.exp(rng.uniform(0, np.log(512), size=n)).astype(int)
@@ -362,7 +376,7 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
                 now = time.perf_counter() - tb
                 while j < n and arrive[j] <= now:
                     s0 = int(rng.integers(0, len(xq) - sizes[j]))
-                    sp = lc.lc_default_search_params(int(ks[j]), int(efs[j]))
+                    sp = lc.lc_default_search_params(int(ks[j]), int(efs[j]), lut_prec=lc.LC_LUT_FP16)
                     cb = lc.make_request_cb(cb_lat)
                     cbs2.append(cb)
                     rid = lc.lc_serve_submit(srv, xq[s0:s0 + sizes[j]], sp, cb)
@@ -378,13 +392,130 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
             span = max(v[0] for v in fin.values()) - tb
             points.append({"offered_qps": lam, "requests": n, "achieved_qps": float(sizes.sum() / span),
                            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                           "p99_ci95_ms": quantile_ci(lat, 0.99),
                            "all_ok": all(v[1] == 0 for v in fin.values()), "slowest": slow})
         out["open_loop"] = points
         out["open_loop_mix"] = ("request sizes log-uniform in [1, 512] queries, k uniform in {1, 10, 100}, "
-                                "efSearch log-uniform in [16, 512], plain mode, Poisson arrivals")
+                                "efSearch log-uniform in [16, 512], plain walk, FP16 level-1 codebook, "
+                                "Poisson arrivals")
     finally:
         lc.lc_serve_close(srv)
     return out
+
+
+def level0_bytes(st, row, d, k, ordered, qbytes=None):
+    """Algorithmic bytes of one level-0 walk launch from the kernel's own counters: the
+    128-byte adjacency row of every expanded node, the code row of every node scored, and per
+    query y' (4d bytes) read and the shortlist (4R bytes) written; in an ordered search the
+    entry node, its distance and the upper count are read too (12 bytes), otherwise the launch
+    also runs the upper-level descent (its evaluations' code rows)."""
+    st = np.asarray(st, np.int64)
+    nq = len(st)
+    R = max(10, k)
+    scored = st[:, 0] + (0 if ordered else st[:, 2])
+    per_q = (qbytes if qbytes is not None else 4 * d) + 4 * R + (12 if ordered else 0)
+    return int((st[:, 1] * 128 + scored * row).sum() + nq * per_q)
+
+
+def measure_large(args, dev, flush, stream):
+    """The walk on an index far larger than L2 (the 1M headline's index is largely L2-resident,
+    so its DRAM traffic is a third of its algorithmic bytes): the --large workload built by the
+    GPU-assisted build, --large-queries queries per step.  The plain FP32 walk at --ef sets the
+    1-recall@1 target; the batched form with the FP16 codebook is swept over efSearch for the
+    cheapest level reaching it.  Same timing rules as the headline (L2 flushed before every
+    step, CUDA events on the search stream, clocks sampled during the timed steps)."""
+    import torch
+    from paper_1804_09996_gb300 import lc
+    w = dict(WORKLOADS[args.large], n_query=args.large_queries)
+    t0 = time.time()
+    xt, xb, xq = make_data(w)
+    gen_s = time.time() - t0
+    h, build_s = build_index(w, xt, xb, build_gpu=1)
+    del xt
+    n_gt = min(len(xq), 10_000)
+    gt, gt_d = exact_nn(xb, xq[:n_gt], f"cuda:{dev}")
+    nq, k, d = len(xq), args.k, w["d"]
+    q = torch.from_numpy(xq).cuda()
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    dists = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    stats = torch.empty((nq, 3), dtype=torch.int32, device="cuda")
+    lc.lc_profile(h, True)
+    steps = max(5, args.steps // 2)
+
+    def run(sp, n_steps):
+        for _ in range(3):
+            lc.lc_search(h, q, nq, sp, ids, dists, stats, stream)
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        ph = []
+        for e0, e1 in ev:
+            with torch.cuda.stream(stream):
+                flush.sum(dtype=torch.int64)
+                e0.record(stream)
+            lc.lc_search(h, q, nq, sp, ids, dists, stats, stream)
+            e1.record(stream)
+            ph.append(lc.lc_profile_phases(h))
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        ph = np.mean(np.array(ph), axis=0)
+        return dict(ms=ms, qps=nq / (ms / 1e3), walk_ms=float(ph[0] + ph[1] + ph[2]), refine_ms=float(ph[3]),
+                    rotate_ms=float(ph[0]), descent_ms=float(ph[1]), level0_ms=float(ph[2]),
+                    recall=recall_at_1(ids[:, 0].cpu().numpy(), xb, xq, gt_d),
+                    stats=stats.cpu().numpy().astype(np.int64))
+
+    clocks = Clocks(dev)
+    sp_p = lc.lc_default_search_params(k, args.ef)
+    plain = run(sp_p, steps)
+    target = plain["recall"]
+    sweep, sp_b = [], None
+    for ef in (32, 40, 48, 56, 64, 80, 96, 128):
+        sp_b = lc.lc_default_search_params(k, ef, mode=lc.LC_MODE_BATCHED, beam=args.beam, lut_prec=lc.LC_LUT_FP16)
+        r = run(sp_b, 3)
+        sweep.append((ef, r["recall"], r["qps"]))
+        if r["recall"] >= target:
+            break
+    best = run(sp_b, steps)
+    best_name, best_ef = f"batched(beam={args.beam}), fp16 codebook", sp_b.ef
+    # the library's autotuner on a disjoint sample with exact neighbours (beam, codebook
+    # precision, efSearch and launch shape for this index and batch size)
+    xs = extra_queries(w, nq, 2000)
+    gs, _ = exact_nn(xb, xs, f"cuda:{dev}")
+    tr = lc.lc_autotune(h, xs, gs.astype(np.int32), k=k, ef=args.ef, allow_fp16=True, max_beam=8, reps=3, batch=nq)
+    sp_t = lc.lc_search_params.from_buffer_copy(tr.sp)
+    tuned = run(sp_t, steps)
+    tune = {"beam": sp_t.beam if sp_t.mode else 1, "mode": "batched" if sp_t.mode else "plain",
+            "codebook": "fp16" if sp_t.lut_prec else "fp32", "efSearch": sp_t.ef, "warps": sp_t.warps,
+            "visited_log": sp_t.visited_log, "candidates": tr.tried}
+    if tuned["recall"] >= target and tuned["qps"] > best["qps"]:
+        best, best_ef = tuned, sp_t.ef
+        best_name = f"autotuned ({tune['mode']}, beam {tune['beam']}, {tune['codebook']} codebook)"
+    clk = clocks.stop()
+    lc.lc_free(h)
+    del q, ids, dists, stats
+    torch.cuda.empty_cache()
+
+    def roof(r):
+        b, t = level0_bytes(r["stats"], w["M1"], d, k, r["descent_ms"] > 0), r["level0_ms"]
+        peak, src = peaks()
+        got = b / (t / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": got, "peak": peak, "unit": "GB/s", "frac": got / peak,
+                "kernel": "walk_kernel (level-0 launch)", "launch_ms": t, "peak_source": src,
+                "algorithmic_bytes_per_launch": b}
+
+    def summ(r, ef, form):
+        return {"form": form, "efSearch": ef, "qps": r["qps"], "ms_per_step": r["ms"], "recall_at_1": r["recall"],
+                "walk_ms": r["walk_ms"], "refine_ms": r["refine_ms"], "rotate_ms": r["rotate_ms"],
+                "descent_ms": r["descent_ms"], "level0_ms": r["level0_ms"],
+                "mean_n_dist": float(r["stats"][:, 0].mean()), "mean_n_expand": float(r["stats"][:, 1].mean()),
+                "roofline": roof(r)}
+
+    return {"workload": args.large, "desc": w["desc"].replace("10k queries/step", f"{nq // 1000}k queries/step"),
+            "queries_per_step": nq, "recall_queries": n_gt, "recall_target": target, "steps": steps,
+            "index_build": "GPU-assisted", "data_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
+            "plain": summ(plain, args.ef, "plain, fp32 codebook"),
+            "headline": summ(best, best_ef, best_name),
+            "sweep": sweep, "autotune": tune, "clocks": clk,
+            "l2": "flushed before every step (256 MB read, outside the timed span)"}
 
 
 def dist_init():
@@ -472,6 +603,9 @@ def main():
     ap.add_argument("--walk-full", type=int, default=0, help="single form: 1 = walk on the full two-level decode")
     ap.add_argument("--lut", default="fp32", choices=["fp32", "fp16"],
                     help="level-1 codebook precision of the single form run by --mode plain / batched")
+    ap.add_argument("--large", default="mix10m", choices=["none"] + sorted(WORKLOADS),
+                    help="also measure the walk on this index (far larger than L2) at 1 GPU; none: skip")
+    ap.add_argument("--large-queries", type=int, default=100_000, help="queries per step of the --large measurement")
     ap.add_argument("--mode", default="both", choices=["both", "plain", "batched"],
                     help="both: plain sets the recall target, batched is swept to reach it; "
                          "plain / batched: that form only, at --ef")
@@ -523,7 +657,7 @@ def main():
         stream.synchronize()
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        walk_ms, refine_ms = [], []
+        ph = []
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -533,16 +667,16 @@ def main():
                 ev0[s].record(stream)
             lc.lc_search_ex(h, q, qtype, nq, sp, de, ids, dists, stats, stream)
             ev1[s].record(stream)
-            wm, rm = lc.lc_profile_read(h)
-            walk_ms.append(wm)
-            refine_ms.append(rm)
+            ph.append(lc.lc_profile_phases(h))
         torch.cuda.synchronize()
         barrier(ws)
         wall = time.perf_counter() - t0
         ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)])), ws)
         got = ids.cpu().numpy()
-        return dict(ms=ms, qps=nq * ws / (ms / 1e3), walk_ms=float(np.mean(walk_ms)),
-                    refine_ms=float(np.mean(refine_ms)), recall=recall_at_1(got[:, 0], xb, xq, gt_d),
+        ph = np.mean(np.array(ph), axis=0)
+        return dict(ms=ms, qps=nq * ws / (ms / 1e3), walk_ms=float(ph[0] + ph[1] + ph[2]), refine_ms=float(ph[3]),
+                    rotate_ms=float(ph[0]), descent_ms=float(ph[1]), level0_ms=float(ph[2]),
+                    recall=recall_at_1(got[:, 0], xb, xq, gt_d),
                     stats=stats.cpu().numpy().astype(np.int64), wall=wall)
 
     clocks = Clocks(dev)
@@ -613,16 +747,20 @@ def main():
         measure(best_form, 3)
         best = dict(best, stats=stats.cpu().numpy().astype(np.int64))
 
-    # walk kernel: algorithmic bytes per launch, from its own counters
+    # the dominant kernel, the level-0 walk launch: its algorithmic bytes (from its own
+    # counters) over its CUDA-event duration; the whole walk (rotation, descent, sort, level
+    # 0, with the query bytes) is reported beside it
     st = best["stats"]
     M1 = w["M1"]
     row = M1 + ((w["M2"] + 1 + 15) // 16 * 16 if best_form[0].walk_full else 0)   # code bytes per scored node
     R = max(10, k)
     qbytes = d * (1 if u8 else 4) + (4 if uneven else 0)
     b_walk = int((st[:, 1] * 128 + (st[:, 0] + st[:, 2]) * row).sum() + nq * (qbytes + 4 * d + 4 * R))
-    walk_s = best["walk_ms"] / 1e3
+    ordered = best["descent_ms"] > 0
+    b_l0 = level0_bytes(st, row, d, k, ordered, qbytes=4 * d + (4 if uneven else 0))
     peak, peak_src = peaks()
-    achieved = b_walk / walk_s / 1e9
+    achieved = b_l0 / (best["level0_ms"] / 1e3) / 1e9
+    walk_achieved = b_walk / (best["walk_ms"] / 1e3) / 1e9
     # DRAM traffic from the committed ncu summary of the same kernel build and form, if any
     bsp = best_form[0]
     efp_b = max(bsp.ef, bsp.k)
@@ -710,12 +848,16 @@ def main():
                "single_thread": {"value": n1 / el1, "unit": "queries/s", "cores": 1,
                                  "sample": f"first {n1} of the {nq} queries, {what}"}}
     lc.lc_free(h)
+    large = None
+    if args.large != "none" and ws == 1 and args.mode == "both":
+        large = measure_large(args, dev, flush, stream)
     if rank != 0:
         return
 
     def summary(r, ef, extra=None):
         out = {"efSearch": ef, "qps": r["qps"], "ms_per_step": r["ms"], "recall_at_1": r["recall"],
-               "walk_ms": r["walk_ms"], "refine_ms": r["refine_ms"],
+               "walk_ms": r["walk_ms"], "refine_ms": r["refine_ms"], "rotate_ms": r["rotate_ms"],
+               "descent_ms": r["descent_ms"], "level0_ms": r["level0_ms"],
                "mean_n_dist": float(r["stats"][:, 0].mean()), "mean_n_expand": float(r["stats"][:, 1].mean())}
         out.update(extra or {})
         return out
@@ -726,6 +868,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "k": k, "headline_form": best_name,
+                   "precision": ("walk: FP32 arithmetic on the level-1 codebook rounded to FP16; re-rank: FP32"
+                                 if best_form[0].lut_prec else "FP32 throughout (walk and re-rank)"),
                    "recall_target": target, "recall_at_1": best["recall"], "queries_per_step": nq,
                    "recall_queries": n_gt,
                    "efSearch_levels": ("factor applied to every query's own efSearch" if uneven else "efSearch"),
@@ -744,11 +888,16 @@ def main():
                        {"beam": args.beam, "sweep": forms["batched_full_fp16"]["sweep"],
                         "walk": "full two-level decode q = c1 + c2, codebooks rounded to FP16"}),
                    "served": served,
+                   "large": large,
                    "l2": "flushed before every step (256 MB read, outside the timed span)",
                    "index_build_s": round(build_s, 1), "index_build": "GPU-assisted" if args.gpu_build else "host", "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "walk_kernel",
-                     "peak_source": peak_src, "algorithmic_bytes_per_launch": b_walk},
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "walk_kernel (level-0 launch" + (" of the ordered search)" if ordered else ")"),
+                     "launch_ms": best["level0_ms"], "peak_source": peak_src, "algorithmic_bytes_per_launch": b_l0,
+                     "whole_walk": {"achieved": walk_achieved, "frac": walk_achieved / peak, "ms": best["walk_ms"],
+                                    "algorithmic_bytes": b_walk,
+                                    "what": "rotation + upper-level descents + sort + level-0 walk"}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "queries/s", "h2d_bytes_per_step": int(hq.numel() * hq.element_size()) + (
                     0 if he is None else int(he.numel() * 4)),

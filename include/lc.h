@@ -116,8 +116,8 @@ typedef struct {
                         coordinate's level-1 plus level-2 centroid; reads M1 + M2P code bytes
                         per node).  With LC_LUT_FP16 both codebooks are rounded, which needs a
                         uniform level-1 split (M1 = 16 or 32 at d = 96, M1 = 64 at d = 128) */
-    int order;       /* order in which the walk takes the queries (lc_search / lc_search_ex only;
-                        plans and served requests always use query order).  LC_ORDER_AUTO (0):
+    int order;       /* order in which the walk takes the queries (lc_search, lc_search_ex and the
+                        server's launches; plans always use query order).  LC_ORDER_AUTO (0):
                         ordered once the batch has at least twice as many queries as the GPU
                         walks at once; LC_ORDER_NEVER: query order; LC_ORDER_ALWAYS: ordered.
                         Ordered: a first launch runs every query's upper-level descent, the
@@ -269,14 +269,20 @@ lc_status lc_merge_topk(const int32_t *ids, const float *dists, int S, int64_t n
                         const int64_t *id_offsets, int32_t *ids_out, float *dists_out, void *stream);
 
 /* ---- Serving: continuous batching of requests on one GPU (the paper has no serving
- * component; this is the library's own).  The index stays resident; each request (a batch of
- * 1..max_request host queries with its own k, efSearch, shortlist and mode) needs device state
- * for its queries, results and search scratch, sub-allocated from one arena of
- * device_budget_bytes created at open.  Requests start in arrival order as soon as a stream
- * slot (max_inflight of them) and room in the budget are free, so requests that arrive while
- * others are on the GPU start alongside them and their kernels overlap.  Results are exactly
- * those of lc_search with the same parameters.  A server is driven by one host thread:
- * submit, poll and close from the same thread. */
+ * component; this is the library's own).  The index stays resident; each request is a batch of
+ * 1..max_request host queries with its own k, efSearch, shortlist and mode.  Requests wait in
+ * arrival order; whenever one of the max_inflight launch slots is free, the oldest waiting
+ * request starts together with every later waiting request of the same parameters up to
+ * efSearch (same k, shortlist, mode, beam, codebook precision, caps and table sizes, and
+ * max(ef, k) in the same power-of-two class), up to 8,192 queries (or max_request): their
+ * queries run as one launch in which each query walks with its own request's efSearch.  Under
+ * light load a request starts alone as soon as it arrives and overlaps with those already on
+ * the GPU; under heavy load the requests that queued while the slots were busy run as a few
+ * large launches.  Each launch's device state (queries, results, search scratch) is
+ * sub-allocated from one arena of device_budget_bytes created at open; a merge is cut short
+ * where the arena has no room.  Results are exactly those of lc_search with each request's
+ * parameters.  A server is driven by one host thread: submit, poll and close from the same
+ * thread. */
 typedef struct lc_server lc_server;
 
 /* Completion callback, invoked from lc_serve_poll or lc_serve_close on the calling thread.
@@ -373,6 +379,13 @@ void lc_plan_free(lc_plan *pl);
  * LC_ERR_CUDA. */
 lc_status lc_profile(lc_index *ix, int enable);
 lc_status lc_profile_read(lc_index *ix, float *walk_ms, float *refine_ms);
+
+/* The last profiled search's phases, in milliseconds: the query rotation, the upper-level
+ * descents and the queue sort of an ordered search (0 otherwise: the walk then descends
+ * itself), the level-0 walk launch, and the refinement (0 without refinement).  walk_ms of
+ * lc_profile_read is the sum of the first three.  Any pointer may be NULL.  Errors: as
+ * lc_profile_read. */
+lc_status lc_profile_phases(lc_index *ix, float *rotate_ms, float *descent_ms, float *level0_ms, float *refine_ms);
 
 /* Frees the index and its device memory (NULL is a no-op). */
 void lc_free(lc_index *ix);

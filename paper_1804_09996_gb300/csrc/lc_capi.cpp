@@ -514,4 +514,11 @@ lc_status lc_profile_read(lc_index *ix, float *walk_ms, float *refine_ms)
     return lc::profile_read(ix, walk_ms, refine_ms);
 }
 
+lc_status lc_profile_phases(lc_index *ix, float *rotate_ms, float *descent_ms, float *level0_ms, float *refine_ms)
+{
+    set_error("");
+    if (!ix) { set_error("null index"); return LC_ERR_ARG; }
+    return lc::profile_phases(ix, rotate_ms, descent_ms, level0_ms, refine_ms);
+}
+
 }  // extern "C"

@@ -35,7 +35,9 @@ struct DeviceIndex {
     int32_t *ids_st = nullptr; float *d_st = nullptr; int32_t *s_st = nullptr; size_t out_cap = 0;
     // profiling
     bool profile = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // profiled search: before the rotation, after the level-0 walk, after the refinement,
+    // after the rotation, before the level-0 walk (after the descent and the sort)
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool ev_valid = false, has_refine = false;
     int num_sms = 0;
     uint64_t gen = 0;             // changes with every upload (plans check it)
@@ -62,6 +64,8 @@ struct SearchPlan {
     size_t rsm = 0;
     bool rboth = false;                  // both codebooks in shared memory
     bool ordered = false;                // two walk launches, level 0 in decreasing entry distance
+    int dwpc = 0, dgrid = 0;             // ordered search: the descent launch's warps per CTA, CTAs
+    size_t dsmem = 0;
     size_t yq_elems = 0, sl_elems = 0, spill_elems = 0, ord_elems = 0;
 };
 

@@ -71,6 +71,7 @@ lc_status merge_topk(const int32_t *ids, const float *dists, int S, int64_t nq, 
 lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, int ef, int32_t *ids,
                               float *dists, int32_t *stats, void *stream);
 lc_status profile_read(lc_index *ix, float *walk_ms, float *refine_ms);
+lc_status profile_phases(lc_index *ix, float *rotate_ms, float *descent_ms, float *level0_ms, float *refine_ms);
 // Autotuner (lc_tune.cpp).
 lc_status autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, const lc_tune_params *tp,
                    lc_tune_result *out);

@@ -377,8 +377,6 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
     }
 }
 
-// ------------------------------------------------------------------------------------------
-// Host side
 template <class T>
 static bool dupload(T *&dst, const std::vector<T> &src)
 {
@@ -502,6 +500,7 @@ static int ilog2_ceil(int64_t x)
 
 using RefineFn = void (*)(const RefineArgs);
 
+
 // Refinement instantiation: codebooks placement and coordinates per lane (3 for d = 96,
 // 4 for d = 128, else the checked 8).
 static RefineFn refine_kernel_for(bool both, int d, bool prod)
@@ -566,6 +565,18 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
                 (sp->order == LC_ORDER_ALWAYS ||
                  (sp->order == LC_ORDER_AUTO && nq >= (int64_t)ORDER_MIN_ROUNDS * P.grid * P.wpc));
     P.ord_elems = P.ordered ? (size_t)nq * 4 : 0;
+    if (P.ordered) {
+        // the descent launch: its own kernel, many more warps (no level-0 state)
+        WalkArgs wd{};
+        wd.nq = nq;
+        wd.d = dv->d;
+        wd.M2P = dv->M2P;
+        ce = descent_config(P.half, P.variant, dv->M1, P.full, wd, dv->num_sms, &P.dwpc, &P.dgrid, &P.dsmem);
+        if (ce != cudaSuccess) {
+            set_error("descent kernel configuration failed: %s", cudaGetErrorString(ce));
+            return LC_ERR_CUDA;
+        }
+    }
     {
         const size_t rsm = rotate_smem(dv->d);
         if (cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAX_SMEM_PER_BLOCK) != cudaSuccess) {
@@ -656,6 +667,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
     }
     if (!rotated) rotate_kernel<<<std::max(P.qgrid, 1), ROT_THREADS, P.qsm, st>>>(dq, dq8, nq, dv->d, dv->Rt, sc.yq);
     cudaError_t ce = cudaGetLastError();
+    if (profile) cudaEventRecord(dv->ev[3], st);
     if (ce != cudaSuccess) {
         set_error("rotation kernel launch failed: %s", cudaGetErrorString(ce));
         return LC_ERR_CUDA;
@@ -669,7 +681,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         w1.seed = seed;
         w1.seed_up = seed_up;
         w1.seed_d = seed_d;
-        ce = walk_run(P.half, P.variant, dv->M1, P.full, w1, P.smem, P.wpc, P.grid, st);
+        ce = descent_run(P.half, P.variant, dv->M1, P.full, w1, P.dsmem, P.dwpc, P.dgrid, st);
         if (ce == cudaSuccess && cudaMemsetAsync(sc.counter, 0, sizeof(unsigned long long), st) == cudaSuccess) {
             order_kernel<<<1, ORDER_THREADS, 0, st>>>(seed_d, nq, order);
             ce = cudaGetLastError();
@@ -686,6 +698,7 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         wa.seed_up = seed_up;
         wa.seed_d = seed_d;
     }
+    if (profile) cudaEventRecord(dv->ev[4], st);
     ce = walk_run(P.half, P.variant, dv->M1, P.full, wa, P.smem, P.wpc, P.grid, st);
     if (profile) cudaEventRecord(dv->ev[1], st);
     if (ce != cudaSuccess) {
@@ -1730,6 +1743,29 @@ lc_status profile_read(lc_index *ix, float *walk_ms, float *refine_ms)
     if (dv->has_refine) cudaEventElapsedTime(&b, dv->ev[1], dv->ev[2]);
     if (walk_ms) *walk_ms = a;
     if (refine_ms) *refine_ms = b;
+    return LC_OK;
+}
+
+lc_status profile_phases(lc_index *ix, float *rotate_ms, float *descent_ms, float *level0_ms, float *refine_ms)
+{
+    if (!ix->dev || !ix->dev->profile || !ix->dev->ev_valid) {
+        set_error("no profiled search to read");
+        return LC_ERR_STATE;
+    }
+    DeviceIndex *dv = ix->dev;
+    if (cudaEventSynchronize(dv->ev[2]) != cudaSuccess) {
+        set_error("event synchronisation failed");
+        return LC_ERR_CUDA;
+    }
+    float r = 0, de = 0, l0 = 0, rf = 0;
+    cudaEventElapsedTime(&r, dv->ev[0], dv->ev[3]);
+    cudaEventElapsedTime(&de, dv->ev[3], dv->ev[4]);
+    cudaEventElapsedTime(&l0, dv->ev[4], dv->ev[1]);
+    if (dv->has_refine) cudaEventElapsedTime(&rf, dv->ev[1], dv->ev[2]);
+    if (rotate_ms) *rotate_ms = r;
+    if (descent_ms) *descent_ms = de;
+    if (level0_ms) *level0_ms = l0;
+    if (refine_ms) *refine_ms = rf;
     return LC_OK;
 }
 

@@ -482,6 +482,10 @@ __device__ __forceinline__ uint32_t hash32(int32_t e)
     return x ^ (x >> 15);
 }
 
+// Open addressing with triangular probing: the p-th probe of id e is at hash(e) + p(p+1)/2
+// (mod the power-of-two table size), which visits every slot and, unlike a linear probe, does
+// not grow long runs of occupied slots as the table fills (a warp resolves a row of 32 ids
+// only when its longest probe sequence ends).
 // Inserts e into the visited set; true if it was not there.  The shared table takes
 // inserts until the walk switches to spill mode; from then on it is only read and new ids
 // go to the warp's global table.
@@ -495,7 +499,7 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
             int32_t old = atomicCAS(hash + h, -1, e);
             if (old == -1) return true;
             if (old == e) return false;
-            h = (h + 1) & Hm;
+            h = (h + p + 1) & Hm;
         }
         return false;   // unreachable: the table is kept at most half full
     }
@@ -503,7 +507,7 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
         int32_t v = hash[h];
         if (v == e) return false;
         if (v == -1) break;
-        h = (h + 1) & Hm;
+        h = (h + p + 1) & Hm;
     }
     uint32_t Sm = (1u << slog) - 1;
     h = (hash32(e) >> 3) & Sm;
@@ -511,7 +515,7 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
         int32_t old = atomicCAS(spill + h, -1, e);
         if (old == -1) return true;
         if (old == e) return false;
-        h = (h + 1) & Sm;
+        h = (h + p + 1) & Sm;
     }
     return false;       // unreachable: the spill table is kept at most half full
 }
@@ -691,10 +695,10 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                             const int32_t e = ev[u];
                             bool fresh = e >= 0 && ov[u] == -1;
                             if (e >= 0 && ov[u] != -1 && ov[u] != e) {
-                                // collision: continue the linear probe
+                                // collision: continue the probe sequence
                                 uint32_t h = hash32(e) & Hm;
                                 for (uint32_t p = 1; p <= Hm; p++) {
-                                    h = (h + 1) & Hm;
+                                    h = (h + p) & Hm;
                                     const int32_t old = atomicCAS(hash + h, -1, e);
                                     if (old == -1) { fresh = true; break; }
                                     if (old == e) break;
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                                     const int32_t v = hash[h];
                                     if (v == ev[u]) { seen[u] = true; break; }
                                     if (v == -1) break;
-                                    h = (h + 1) & Hm;
+                                    h = (h + p + 1) & Hm;
                                 }
                             }
                         }
@@ -741,7 +745,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                             if (e >= 0 && !seen[u] && ov[u] != -1 && ov[u] != e) {
                                 uint32_t h = (hash32(e) >> 3) & Sm;
                                 for (uint32_t p = 1; p <= Sm; p++) {
-                                    h = (h + 1) & Sm;
+                                    h = (h + p) & Sm;
                                     const int32_t old = atomicCAS(spill + h, -1, e);
                                     if (old == -1) { fresh = true; break; }
                                     if (old == e) break;
@@ -916,7 +920,166 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
 }
 
 
+// ------------------------------------------------------------------------------------------
+// Upper-level descent alone (the first launch of an ordered search): the greedy descent of
+// Section 2 from the entry point down to level 1, exactly as walk_kernel runs it before level
+// 0, writing each query's level-0 entry node, its walk distance and the upper-level
+// evaluations.  It needs none of the level-0 state (result list, visited tables, merge
+// buffers), so a warp holds only its staged code rows and node list: more warps fit per SM
+// (up to 32), and more descents are in flight at once.
+constexpr int MAX_DESCENT_WARPS = 32;
+
+__host__ __device__ inline size_t descent_smem_per_warp(int M1, int m2p)
+{
+    return align_up((size_t)32 * (M1 + m2p), 16) + 32 * 4;
+}
+
+// threads per CTA the instantiation is compiled for: the full-decode walk keeps more per-lane
+// state (the level-2 sub-space of every coordinate), so it gets registers for 16 warps
+__host__ __device__ constexpr int descent_threads(bool fq) { return fq ? 16 * 32 : MAX_DESCENT_WARPS * 32; }
+
+template <int M1, int D1, typename CT, bool FQ>
+__global__ void __launch_bounds__(descent_threads(FQ)) descent_kernel(const WalkArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = a.d;
+    CT *C1s = reinterpret_cast<CT *>(smem_raw);
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(sizeof(CT) == 4 ? a.C1 : (const void *)a.C1h);
+        uint4 *dst = reinterpret_cast<uint4 *>(C1s);
+        const int n16 = (int)(walk_c1_bytes(d, M1, D1, sizeof(CT)) / 16);
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    const CT *C2 = nullptr;
+    if constexpr (FQ) {
+        if constexpr (sizeof(CT) == 2) {
+            CT *C2s = reinterpret_cast<CT *>(smem_raw + walk_c1_bytes(d, M1, D1, sizeof(CT)));
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.C2h);
+            for (int i = threadIdx.x; i < 256 * d * 2 / 16; i += blockDim.x) reinterpret_cast<uint4 *>(C2s)[i] = __ldg(src + i);
+            C2 = C2s;
+        } else {
+            C2 = reinterpret_cast<const CT *>(a.C2);
+        }
+    }
+    __syncthreads();
+    const int m2p = FQ ? a.M2P : 0;
+    unsigned char *base = smem_raw + walk_cb_bytes(d, M1, D1, sizeof(CT), FQ) + (size_t)warp * descent_smem_per_warp(M1, m2p);
+    uint8_t *stage = base;
+    int32_t *slot = reinterpret_cast<int32_t *>(base + align_up((size_t)32 * (M1 + m2p), 16));
+    const unsigned lt_mask = (1u << lane) - 1;
+
+    for (;;) {
+        int64_t qi = 0;
+        if (lane == 0) qi = atomicAdd(a.counter, 1ull);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= a.nq) break;
+        const int64_t q = qi;
+        const float *yrot = a.yq_in + q * d;       // y' = R y from the rotation kernel
+        LaneGeo<M1, D1> g;
+#pragma unroll
+        for (int k = 0; k < LaneGeo<M1, D1>::NSUB; k++) {
+            const int j = M1 == 16 ? (lane & 15) : lane + 32 * k;
+            g.j[k] = j;
+            g.off[k] = a.s1.off[j];
+            g.len[k] = a.s1.len[j];
+#pragma unroll
+            for (int u = 0; u < LaneGeo<M1, D1>::DMAX; u++) {
+                g.y[k][u] = u < g.len[k] ? yrot[g.off[k] + u] : 0.f;
+                g.m2[k][u] = FQ && u < g.len[k] ? a.sub2[g.off[k] + u] : 0;
+            }
+        }
+        // the entry point's evaluation, then steepest moves level by level (as walk_kernel)
+        int32_t cur = a.ep, n_up = 0;
+        float dcur = 0.f;
+        int lvl = a.max_level;
+        bool first = true;
+        for (;;) {
+            int ns;
+            if (first) {
+                if (lane == 0) slot[0] = cur;
+                ns = 1;
+            } else {
+                const int32_t e = a.upper_adj[((int64_t)a.upper_off[cur] + lvl - 1) * DEG + lane];
+                const unsigned vm = __ballot_sync(FULL, e >= 0);
+                ns = __popc(vm);
+                if (e >= 0) slot[__popc(vm & lt_mask)] = e;
+                n_up += ns;
+            }
+            __syncwarp();
+            uint64_t best = ~0ull;
+            if (ns > 0) {
+                int my_slot;
+                const float de = score_nodes<M1, D1, CT, FQ>(C1s, stage, a.codes1, slot, ns, d, g, lane, &my_slot, C2,
+                                                             a.codes2b, a.M2P);
+                const uint64_t k = my_slot < ns ? make_key(de, slot[my_slot]) : ~0ull;
+                best = warp_min64(k);
+            }
+            __syncwarp();
+            if (first) {
+                first = false;
+                dcur = key_dist(best);
+                if (lvl < 1) break;
+                n_up = 1;                                   // the entry point's evaluation
+            } else if (ns > 0 && best < make_key(dcur, cur)) {
+                cur = key_id(best);                         // greedy move at this level
+                dcur = key_dist(best);
+            } else if (--lvl == 0) {
+                break;
+            }
+        }
+        if (lane == 0) {
+            a.seed[q] = cur;
+            a.seed_d[q] = dcur;
+            a.seed_up[q] = n_up;
+        }
+        __syncwarp();
+    }
+}
+
 constexpr size_t MAX_SMEM_PER_BLOCK = 227 * 1024;
+
+// Launch shape of the descent: as many warps as fit next to the codebook, at most 32.
+template <int M1, int D1, typename CT, bool FQ>
+static cudaError_t launch_descent(const WalkArgs &wa, int sms, int *wpc_out, int *grid_out, size_t *smem_out)
+{
+    const size_t c1 = walk_cb_bytes(wa.d, M1, D1, sizeof(CT), FQ);
+    const size_t per = descent_smem_per_warp(M1, FQ ? wa.M2P : 0);
+    if (c1 + per > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
+    int wpc = (int)std::min<size_t>(MAX_DESCENT_WARPS, (MAX_SMEM_PER_BLOCK - c1) / per);
+    cudaError_t e = cudaFuncSetAttribute(descent_kernel<M1, D1, CT, FQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)MAX_SMEM_PER_BLOCK);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, descent_kernel<M1, D1, CT, FQ>);
+    if (e != cudaSuccess) return e;
+    wpc = std::min(wpc, fa.maxThreadsPerBlock / 32);
+    const size_t smem = c1 + per * wpc;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, descent_kernel<M1, D1, CT, FQ>, wpc * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t need = (wa.nq + wpc - 1) / wpc;
+    *grid_out = (int)std::min<int64_t>(need, (int64_t)per_sm * sms);
+    *wpc_out = wpc;
+    *smem_out = smem;
+    return cudaSuccess;
+}
+
+// Compile-time shape of an instantiation (level-1 sub-quantisers, sub-space width, full walk),
+// for dispatching a generic launcher over the instantiations.
+template <int A, int B, bool C>
+struct WalkShape {
+    static constexpr int M1 = A, D1 = B;
+    static constexpr bool FQ = C;
+};
+
+template <int M1, int D1, typename CT, bool FQ>
+static cudaError_t run_descent(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
+{
+    descent_kernel<M1, D1, CT, FQ><<<grid, wpc * 32, smem, st>>>(wa);
+    return cudaGetLastError();
+}
 
 // Warps per CTA: as many as fit next to the codebook (at most MAX_WALK_WARPS, and at most
 // want if want > 0).
@@ -965,6 +1128,28 @@ cudaError_t walk_config_f16(int variant, int M1, bool fq, const WalkArgs &wa, si
 cudaError_t walk_run_f16(int variant, int M1, bool fq, const WalkArgs &wa, size_t smem, int wpc, int grid,
                          cudaStream_t st);
 const void *walk_fn_f16(int variant, int M1, bool fq);
+
+cudaError_t descent_config_f32(int variant, int M1, bool fq, const WalkArgs &wa, int sms, int *wpc, int *grid,
+                               size_t *smem);
+cudaError_t descent_run_f32(int variant, int M1, bool fq, const WalkArgs &wa, size_t smem, int wpc, int grid,
+                            cudaStream_t st);
+cudaError_t descent_config_f16(int variant, int M1, bool fq, const WalkArgs &wa, int sms, int *wpc, int *grid,
+                               size_t *smem);
+cudaError_t descent_run_f16(int variant, int M1, bool fq, const WalkArgs &wa, size_t smem, int wpc, int grid,
+                            cudaStream_t st);
+
+inline cudaError_t descent_config(bool half, int variant, int M1, bool fq, const WalkArgs &wa, int sms, int *wpc,
+                                  int *grid, size_t *smem)
+{
+    return half ? descent_config_f16(variant, M1, fq, wa, sms, wpc, grid, smem)
+                : descent_config_f32(variant, M1, fq, wa, sms, wpc, grid, smem);
+}
+inline cudaError_t descent_run(bool half, int variant, int M1, bool fq, const WalkArgs &wa, size_t smem, int wpc,
+                               int grid, cudaStream_t st)
+{
+    return half ? descent_run_f16(variant, M1, fq, wa, smem, wpc, grid, st)
+                : descent_run_f32(variant, M1, fq, wa, smem, wpc, grid, st);
+}
 
 inline cudaError_t walk_config(bool half, int variant, int M1, bool fq, const WalkArgs &wa, size_t per_warp, int sms,
                                int want, int *wpc, int *grid, size_t *smem)

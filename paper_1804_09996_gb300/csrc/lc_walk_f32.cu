@@ -90,5 +90,44 @@ cudaError_t walk_run_f32(int variant, int M1, bool fq, const WalkArgs &wa, size_
     }
 }
 
+// The same dispatch as above for a generic launcher f(WalkShape<M1, D1, FQ>).
+template <typename F>
+static cudaError_t by_shape(int variant, int M1, bool fq, F &&f)
+{
+    if (fq) {
+        switch (variant) {
+        case 1: return f(WalkShape<16, 6, true>{});
+        case 2: return f(WalkShape<32, 3, true>{});
+        case 3: return f(WalkShape<64, 2, true>{});
+        default: return M1 == 16 ? f(WalkShape<16, 0, true>{}) : M1 == 32 ? f(WalkShape<32, 0, true>{})
+                                           : f(WalkShape<64, 0, true>{});
+        }
+    }
+    switch (variant) {
+    case 1: return f(WalkShape<16, 6, false>{});
+    case 2: return f(WalkShape<32, 3, false>{});
+    case 3: return f(WalkShape<64, 2, false>{});
+    default: return M1 == 16 ? f(WalkShape<16, 0, false>{}) : M1 == 32 ? f(WalkShape<32, 0, false>{})
+                                                             : f(WalkShape<64, 0, false>{});
+    }
+}
+
+cudaError_t descent_config_f32(int variant, int M1, bool fq, const WalkArgs &wa, int sms, int *wpc, int *grid,
+                               size_t *smem)
+{
+    return by_shape(variant, M1, fq, [&](auto t) {
+        using T = decltype(t);
+        return launch_descent<T::M1, T::D1, float, T::FQ>(wa, sms, wpc, grid, smem);
+    });
+}
+
+cudaError_t descent_run_f32(int variant, int M1, bool fq, const WalkArgs &wa, size_t smem, int wpc, int grid,
+                            cudaStream_t st)
+{
+    return by_shape(variant, M1, fq, [&](auto t) {
+        using T = decltype(t);
+        return run_descent<T::M1, T::D1, float, T::FQ>(wa, smem, wpc, grid, st);
+    });
+}
 
 }  // namespace lc

@@ -24,7 +24,7 @@ EXPORTED = [
     "lc_default_params", "lc_default_search_params", "lc_create", "lc_train", "lc_add", "lc_add_u8",
     "lc_search", "lc_search_ex",
     "lc_import", "lc_size", "lc_upper_rows", "lc_export", "lc_save", "lc_load", "lc_profile",
-    "lc_profile_read", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
+    "lc_profile_read", "lc_profile_phases", "lc_free", "lc_last_error", "lc_search_walk_noalloc",
     "lc_serve_open", "lc_serve_submit", "lc_serve_poll", "lc_serve_close", "lc_merge_topk",
     "lc_plan_create", "lc_plan_buffers", "lc_plan_run", "lc_plan_free", "lc_autotune",
 ]
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
         "lc_serve_poll": (I, [P, I, P]),
         "lc_serve_close": (I, [P]),
         "lc_profile_read": (I, [P, P, P]),
+        "lc_profile_phases": (I, [P, P, P, P, P]),
         "lc_autotune": (I, [P, P, I64, P, P, P]),
         "lc_plan_create": (I, [P, I64, P, I, I, P]),
         "lc_plan_buffers": (I, [P, P, P, P, P, P]),
@@ -313,6 +314,13 @@ def lc_profile_read(ix):
     a, b = ctypes.c_float(), ctypes.c_float()
     _check(lib().lc_profile_read(ix, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def lc_profile_phases(ix):
+    """(rotate_ms, descent_ms, level0_ms, refine_ms) of the last profiled search."""
+    v = [ctypes.c_float() for _ in range(4)]
+    _check(lib().lc_profile_phases(ix, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def lc_free(ix):

@@ -75,3 +75,19 @@ def test_parity_full_size_sampled(index1m, form, k, ef, max_exempt):
         # the sample includes queries whose visited set outgrew the shared-memory table
         assert (ref["stats"][:, 0] > 1024).any()
     print(f"{form} k={k} ef={ef}: {len(SAMPLE)} sampled queries, near-tie exempt {ex:.2%}")
+
+
+def test_fp16_codebook_distance_error(index1m):
+    # Precision form: the walk's ADC distances with the level-1 codebook rounded to FP16,
+    # against the unrounded FP64 ADC distance of the same ids (the oracle's definition on the
+    # FP32 codebook), over the sampled queries of the full-size batch at the headline setting
+    # (batched beam 4, efSearch 64, the walk's own top-10)
+    h, ix, xq = index1m
+    ids, ds, st = gpu_search(h, xq, 10, 64, shortlist=-1, beam=4, lut_prec=lc.LC_LUT_FP16)
+    ids, ds = ids[SAMPLE], ds[SAMPLE]
+    exact, _ = oracle.dists(ix, xq[SAMPLE], ids)
+    rel = np.abs(ds.astype(np.float64) - exact) / exact
+    q = np.percentile(rel, [50, 99, 100])
+    print(f"FP16 codebook, ADC distance vs the unrounded FP64 oracle: median {q[0]:.2e}, p99 {q[1]:.2e}, "
+          f"max {q[2]:.2e} relative")
+    assert q[0] < 5e-4 and q[2] < 1e-2

@@ -1,7 +1,9 @@
 """Serving (lc_serve_*): requests of mixed size, k, efSearch and mode admitted by a device
-memory budget.  Each request's results must be exactly what lc_search returns for it alone;
-a request that can never fit the budget is rejected at submission; queued requests wait for
-room and are cancelled at close."""
+memory budget; requests of the same parameters that wait while the launch slots are busy run
+merged into one launch, each query with its own request's efSearch.  Each request's results
+must be exactly what lc_search returns for it alone, and (served mix with efSearch up to 512)
+the oracle's; a request that can never fit the budget is rejected at submission; queued
+requests wait for room and are cancelled at close."""
 import numpy as np
 import pytest
 
@@ -66,13 +68,13 @@ def served():
     h = lc.lc_create(lc.lc_default_params(ix.d, ix.M1, ix.M2))
     lc.lc_import(h, ix.N, ix.R, ix.C1, ix.C2, ix.codes1, ix.codes2, ix.beta, ix.B, ix.adj0,
                  ix.levels, ix.upper_adj, ix.ep)
-    yield h, xq
+    yield h, xq, ix
     lc.lc_free(h)
 
 
 @pytest.mark.gpu
 def test_results_same_alone_and_in_the_mix(served, rng):
-    h, xq = served
+    h, xq, ix = served
     reqs = _requests(rng, xq, 60)
     srv = lc.lc_serve_open(h, 4 << 30, 16, 64)
     try:
@@ -90,7 +92,7 @@ def test_results_same_alone_and_in_the_mix(served, rng):
 
 @pytest.mark.gpu
 def test_budget_admission_and_rejection(served, rng):
-    h, xq = served
+    h, xq, ix = served
     sp = lc.lc_default_search_params(10, 64)
     tiny = lc.lc_serve_open(h, 64 << 10, 4, 64)
     try:
@@ -119,7 +121,7 @@ def test_budget_admission_and_rejection(served, rng):
 
 @pytest.mark.gpu
 def test_close_cancels_requests_not_started(served):
-    h, xq = served
+    h, xq, ix = served
     sp = lc.lc_default_search_params(10, 64)
     srv = lc.lc_serve_open(h, 1 << 30, 1, 64)
     seen = {}
@@ -128,3 +130,68 @@ def test_close_cancels_requests_not_started(served):
     lc.lc_serve_close(srv)
     assert seen[ids[0]] == lc.LC_OK                  # already on the device: completes
     assert all(seen[r] == lc.LC_ERR_STATE for r in ids[1:])
+
+
+@pytest.mark.gpu
+def test_waiting_requests_run_merged_and_equal_alone(served):
+    # one launch slot: the first request runs alone, the 23 that queue behind it share its
+    # parameters (efSearch 33..64, one class) and run as one merged launch once it is done
+    h, xq, ix = served
+    rng = np.random.default_rng(3)
+    reqs = []
+    for j in range(24):
+        size = int(rng.integers(1, 40))
+        s0 = int(rng.integers(0, len(xq) - size))
+        reqs.append((xq[s0:s0 + size], lc.lc_default_search_params(10, int(rng.integers(33, 65)))))
+    srv = lc.lc_serve_open(h, 1 << 30, 1, 64)
+    try:
+        ids, results, _ = _run(srv, reqs)
+    finally:
+        lc.lc_serve_close(srv)
+    for rid, (q, sp) in zip(ids, reqs):
+        st, i, d = results[rid]
+        assert st == lc.LC_OK
+        ai, ad = _alone(h, q, sp)
+        assert np.array_equal(i, ai) and np.array_equal(d, ad)
+
+
+@pytest.mark.gpu
+def test_served_mix_against_the_oracle(served):
+    # a served mix (k 1 or 10, efSearch 16..512, FP32 and FP16 codebooks, two launch slots so
+    # that requests queue and merge) checked request by request against the oracle with the
+    # parity bar of the batch search (the server does not return visit counts; those are
+    # checked by the batch parity tests)
+    import oracle
+    from test_gpu_parity import compare
+    h, xq, ix = served
+    rng = np.random.default_rng(11)
+    c1h = ix.C1.astype(np.float16).astype(np.float32)
+    reqs = []
+    for j in range(40):
+        size = int(rng.integers(4, 48))
+        s0 = int(rng.integers(0, len(xq) - size))
+        ef = int(np.exp(rng.uniform(np.log(16), np.log(512))))
+        if j < 4:
+            ef = 512
+        sp = lc.lc_default_search_params(int(rng.choice([1, 10])), ef, lut_prec=int(j % 2))
+        reqs.append((xq[s0:s0 + size], sp))
+    srv = lc.lc_serve_open(h, 1 << 30, 2, 64)
+    try:
+        ids, results, _ = _run(srv, reqs)
+    finally:
+        lc.lc_serve_close(srv)
+    # each request against the oracle at its own efSearch, checked together per (k, codebook)
+    groups = {}
+    for rid, (q, sp) in zip(ids, reqs):
+        st, i, d = results[rid]
+        assert st == lc.LC_OK
+        ref = oracle.search(ix, q, sp.k, sp.ef, c1_walk=c1h if sp.lut_prec else None)
+        groups.setdefault((sp.k, sp.lut_prec), []).append((q, i, d, ref))
+    for (k, prec), rows in groups.items():
+        ref = {key: np.concatenate([r[3][key] for r in rows]) for key in
+               ("ids", "dists", "stats", "gap", "gap_walk", "next_dist")}
+        ref["ctx"] = dict(rows[0][3]["ctx"], Q=np.ascontiguousarray(np.concatenate([r[0] for r in rows]), np.float32))
+        i = np.concatenate([r[1] for r in rows])
+        d = np.concatenate([r[2] for r in rows])
+        # walks of efSearch up to 512 on a 3,000-vector index make many deciding comparisons
+        compare(ref, i, d, ref["stats"], max_exempt=0.35, max_loss=0.01)
