@@ -601,7 +601,7 @@ def main():
     ap.add_argument("--gpu-build", type=int, default=0,
                     help="1: the index build runs its level-0 insertion searches on the GPU")
     ap.add_argument("--walk-full", type=int, default=0, help="single form: 1 = walk on the full two-level decode")
-    ap.add_argument("--lut", default="fp32", choices=["fp32", "fp16"],
+    ap.add_argument("--lut", default="fp32", choices=["fp32", "fp16", "table"],
                     help="level-1 codebook precision of the single form run by --mode plain / batched")
     ap.add_argument("--large", default="mix10m", choices=["none"] + sorted(WORKLOADS),
                     help="also measure the walk on this index (far larger than L2) at 1 GPU; none: skip")
@@ -685,13 +685,13 @@ def main():
     levels = ((0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 1.0, 1.25, 1.5, 2.0) if uneven else
               sorted({e for e in (16, 20, 24, 28, 32, 40, 48, 56, 64, 80, 96, 128) if e <= max(2 * args.ef, 16)}))
     batched = None
-    lut1 = lc.LC_LUT_FP16 if args.lut == "fp16" else lc.LC_LUT_FP32
+    lut1 = {"fp16": lc.LC_LUT_FP16, "table": lc.LC_LUT_TABLE}.get(args.lut, lc.LC_LUT_FP32)
     if args.mode == "batched":
         f_b = params(base_level, lc.LC_MODE_BATCHED, lut1, args.visited_log, args.walk_full)
         batched = measure(f_b, args.steps)
         batched.update(ef=base_level, sweep=[])
         plain, target = None, batched["recall"]
-        best, best_form, best_name = batched, f_b, f"batched(beam={args.beam}){', fp16 codebook' if lut1 else ''}"
+        best, best_form, best_name = batched, f_b, f"batched(beam={args.beam}){', ' + args.lut if lut1 else ''}"
     else:
         f_p = params(base_level, lc.LC_MODE_PLAIN,
                      *((lut1, args.visited_log, args.walk_full) if args.mode == "plain" else ()))
@@ -702,8 +702,10 @@ def main():
     forms = {}
     if args.mode == "both" and args.beam > 1:
         # the cheapest level at which each faster form reaches the plain form's recall
+        table_ok = w["d"] == 96 and w["M1"] == 32 and not u8          # the table kernel's shape
         for name, prec, full in (("batched", lc.LC_LUT_FP32, 0), ("batched_fp16", lc.LC_LUT_FP16, 0),
-                                 ("batched_full_fp16", lc.LC_LUT_FP16, 1)):
+                                 ("batched_full_fp16", lc.LC_LUT_FP16, 1)) + (
+                                     (("batched_table", lc.LC_LUT_TABLE, 0),) if table_ok else ()):
             sweep = []
             for lv in levels:
                 r = measure(params(lv, lc.LC_MODE_BATCHED, prec, full=full), max(10, args.steps // 5))
@@ -717,7 +719,8 @@ def main():
             forms[name] = r
             if r["recall"] >= target and r["qps"] > best["qps"]:
                 best, best_form = r, f_b
-                best_name = (f"batched(beam={args.beam}){', fp16 codebook' if prec else ''}"
+                best_name = (f"batched(beam={args.beam})"
+                             f"{', per-query FP16 ADC tables (tensor cores)' if prec == lc.LC_LUT_TABLE else ', fp16 codebook' if prec else ''}"
                              f"{', full-decode walk' if full else ''}")
         batched = forms.get("batched")
         if not uneven:
@@ -757,7 +760,10 @@ def main():
     qbytes = d * (1 if u8 else 4) + (4 if uneven else 0)
     b_walk = int((st[:, 1] * 128 + (st[:, 0] + st[:, 2]) * row).sum() + nq * (qbytes + 4 * d + 4 * R))
     ordered = best["descent_ms"] > 0
-    b_l0 = level0_bytes(st, row, d, k, ordered, qbytes=4 * d + (4 if uneven else 0))
+    # the table form reads its query's 256 x M1 FP16 ADC table in place of y'
+    b_l0 = level0_bytes(st, row, d, k, ordered,
+                        qbytes=(2 * 256 * M1 if best_form[0].lut_prec == lc.LC_LUT_TABLE else 4 * d)
+                        + (4 if uneven else 0))
     peak, peak_src = peaks()
     achieved = b_l0 / (best["level0_ms"] / 1e3) / 1e9
     walk_achieved = b_walk / (best["walk_ms"] / 1e3) / 1e9
@@ -766,7 +772,8 @@ def main():
     efp_b = max(bsp.ef, bsp.k)
     auto_vlog = min(12, max(10, int(np.ceil(np.log2(32 * efp_b)))))      # the library's automatic table size
     form_key = None if (bsp.warps or bsp.visited_log not in (0, auto_vlog) or (bsp.mode and bsp.beam != args.beam)) else (
-        ("batched" if bsp.mode else "plain") + ("_full" if bsp.walk_full else "") + ("_fp16" if bsp.lut_prec else "")
+        ("batched" if bsp.mode else "plain") + ("_full" if bsp.walk_full else "")
+        + ("_table" if bsp.lut_prec == lc.LC_LUT_TABLE else "_fp16" if bsp.lut_prec else "")
         + f"_ef{bsp.ef}")
     traffic = profiled_traffic(args.workload, form_key) if form_key else None
 
@@ -868,7 +875,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "k": k, "headline_form": best_name,
-                   "precision": ("walk: FP32 arithmetic on the level-1 codebook rounded to FP16; re-rank: FP32"
+                   "precision": ("walk: FP32 sums of per-query FP16 ADC table entries built on the tensor "
+                                 "cores; re-rank: FP32" if best_form[0].lut_prec == lc.LC_LUT_TABLE else
+                                 "walk: FP32 arithmetic on the level-1 codebook rounded to FP16; re-rank: FP32"
                                  if best_form[0].lut_prec else "FP32 throughout (walk and re-rank)"),
                    "recall_target": target, "recall_at_1": best["recall"], "queries_per_step": nq,
                    "recall_queries": n_gt,
@@ -887,6 +896,11 @@ def main():
                        forms["batched_full_fp16"], forms["batched_full_fp16"]["ef"],
                        {"beam": args.beam, "sweep": forms["batched_full_fp16"]["sweep"],
                         "walk": "full two-level decode q = c1 + c2, codebooks rounded to FP16"}),
+                   "batched_table": None if "batched_table" not in forms else summary(
+                       forms["batched_table"], forms["batched_table"]["ef"],
+                       {"beam": args.beam, "sweep": forms["batched_table"]["sweep"],
+                        "walk": "per-query ADC tables [256][32] built by table_kernel (FP16 tensor-core products, "
+                                "FP32 accumulation, FP16 entries), 16 KB per query in shared memory"}),
                    "served": served,
                    "large": large,
                    "l2": "flushed before every step (256 MB read, outside the timed span)",

@@ -90,8 +90,14 @@ enum { LC_MODE_PLAIN = 0, LC_MODE_BATCHED = 1 };
 /* Precision of the level-1 codebook the walk scores with (the ADC terms).  FP32: exact FP32
  * terms.  FP16: the codebook rounded to FP16 (nearest even) and held at half the shared
  * memory, so more queries are in flight per SM; arithmetic stays FP32, and the re-rank always
- * uses the FP32 codebooks. */
-enum { LC_LUT_FP32 = 0, LC_LUT_FP16 = 1 };
+ * uses the FP32 codebooks.  TABLE: per-query ADC tables (Section 4.1): a tensor-core kernel
+ * builds, for the whole batch, every query's table of ||y'_j - C1_j[c]||^2 over sub-spaces j
+ * and centroids c (y' and C1 rounded to FP16, FP32 accumulation, entries stored in FP16, 16 KB
+ * per query), and the walk and the upper-level descent add table entries; for 32 level-1
+ * sub-spaces at d = 96 and the level-1 walk (LC_ERR_ARG otherwise), in every search call
+ * (lc_search, lc_search_ex, plans, the server).  FP16 and TABLE change distances at FP16
+ * precision. */
+enum { LC_LUT_FP32 = 0, LC_LUT_FP16 = 1, LC_LUT_TABLE = 2 };
 
 /* Search parameters (Section 2 search, Section 4.1 two-stage strategy). */
 typedef struct {
@@ -100,7 +106,7 @@ typedef struct {
     int shortlist;   /* 0: refine max(k, 10) candidates (Section 5.1 refines at most 10);
                         > 0: refine max(shortlist, k) (at most 256); < 0: no refinement,
                         return the walk's own top-k by ADC distance */
-    int lut_prec;    /* LC_LUT_FP32 or LC_LUT_FP16 */
+    int lut_prec;    /* LC_LUT_FP32, LC_LUT_FP16 or LC_LUT_TABLE */
     int mode;        /* LC_MODE_PLAIN or LC_MODE_BATCHED */
     int visited_log; /* 0: automatic; 10..14: the per-query visited table in shared memory has
                         2^visited_log entries (ids beyond half of it go to a table in global

@@ -51,7 +51,10 @@ lc_status check_search_params(const lc_search_params *sp)
     if (sp->ef < 1) { set_error("ef must be >= 1"); return LC_ERR_ARG; }
     if ((sp->ef > sp->k ? sp->ef : sp->k) > MAX_EF) { set_error("max(ef, k) exceeds %d", MAX_EF); return LC_ERR_ARG; }
     if (sp->shortlist > MAX_SHORTLIST) { set_error("shortlist exceeds %d", MAX_SHORTLIST); return LC_ERR_ARG; }
-    if (sp->lut_prec != LC_LUT_FP32 && sp->lut_prec != LC_LUT_FP16) { set_error("unsupported lut_prec %d", sp->lut_prec); return LC_ERR_ARG; }
+    if (sp->lut_prec != LC_LUT_FP32 && sp->lut_prec != LC_LUT_FP16 && sp->lut_prec != LC_LUT_TABLE) {
+        set_error("unsupported lut_prec %d", sp->lut_prec);
+        return LC_ERR_ARG;
+    }
     if (sp->mode != LC_MODE_PLAIN && sp->mode != LC_MODE_BATCHED) { set_error("unsupported mode %d", sp->mode); return LC_ERR_ARG; }
     if (sp->mode == LC_MODE_BATCHED && (sp->beam < 2 || sp->beam > 8)) {
         set_error("beam = %d outside 2..8 for the batched mode", sp->beam);

@@ -27,6 +27,7 @@ struct DeviceIndex {
     int32_t *shortlist = nullptr; size_t sl_cap = 0;
     int32_t *spill = nullptr; size_t spill_cap = 0;
     int32_t *ord = nullptr; size_t ord_cap = 0;       // ordered search: 4 words per query
+    uint16_t *tab = nullptr; size_t tab_cap = 0;      // table form: FP16 ADC tables [nq][256][32]
     int32_t *status = nullptr;
     unsigned long long *counter = nullptr;
     // staging for host-pointer calls
@@ -64,6 +65,8 @@ struct SearchPlan {
     size_t rsm = 0;
     bool rboth = false;                  // both codebooks in shared memory
     bool ordered = false;                // two walk launches, level 0 in decreasing entry distance
+    bool tab = false;                    // table form: table_kernel, then the walk's table instantiation
+    size_t tab_elems = 0;                // FP16 table entries of the batch
     int dwpc = 0, dgrid = 0;             // ordered search: the descent launch's warps per CTA, CTAs
     size_t dsmem = 0;
     size_t yq_elems = 0, sl_elems = 0, spill_elems = 0, ord_elems = 0;
@@ -74,6 +77,7 @@ struct SearchScratch {
     float *yq = nullptr;                 // [nq][d] rotated queries
     int32_t *shortlist = nullptr;        // [nq][R] (refinement only)
     int32_t *spill = nullptr;            // [grid * wpc][2^spill_log]
+    uint16_t *tab = nullptr;             // table form: [nq][256][32] FP16
     int32_t *ord = nullptr;              // ordered search: entry node, upper evaluations, queue
                                          // order (int32) and entry distance (float), [nq] each
     int32_t *status = nullptr;           // 1 word

@@ -41,6 +41,7 @@ void device_free(DeviceIndex *dv)
     cfree(dv->codes1); cfree(dv->codes2b);
     cfree(dv->adj0); cfree(dv->upper_off); cfree(dv->upper_adj);
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->ord); cfree(dv->status); cfree(dv->counter);
+    cfree(dv->tab);
     cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx); cfree(dv->b_sel);
     cfree(dv->q_st); cfree(dv->ef_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
     for (auto &e : dv->ev) if (e) cudaEventDestroy(e);
@@ -188,6 +189,113 @@ __global__ void __launch_bounds__(ORDER_THREADS) order_kernel(const float *key, 
     }
 }
 
+// Per-query ADC tables on the tensor cores (table_kernel, search form LC_LUT_TABLE), for the
+// uniform split of 96 coordinates into 32 sub-spaces of 3: for query q, sub-space j and
+// centroid c, T[q][c][j] = ||y'_j||^2 + ||C1_j[c]||^2 - 2 <y'_j, C1_j[c]> (Section 4.1's ADC
+// table), with y' and C1 rounded to FP16 (C1 is the walk's FP16 codebook), the inner products
+// taken by FP16 tensor-core products with FP32 accumulation (mma.sync m16n8k8: 16 centroids x
+// 8 queries, the sub-space's 3 coordinates padded to the 8 of the instruction), the norms in
+// FP32 from the same rounded values, the entry rounded to FP16.  One warp builds the tables of
+// 8 queries: per block of 16 centroids a lane gathers its 4 (centroid, query) entries over the
+// 32 sub-spaces and writes them as 64-byte rows, so each query's table is one contiguous
+// 16 KB block [256][32] (the layout the table walk copies into shared memory).
+constexpr int TAB_WARPS = 4;
+constexpr int TAB_M1 = 32;
+
+__device__ __forceinline__ uint32_t pack_half2(float lo, float hi)
+{
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+__global__ void __launch_bounds__(TAB_WARPS * 32) table_kernel(const float *yq, int64_t nq, const __half *C1h,
+                                                               __half *T)
+{
+    constexpr int M1 = TAB_M1, D = 96;
+    // the FP16 codebook in the walk's split layout: half2 [256][32] (coordinates 0, 1 of every
+    // sub-space), then half [256][32] (coordinate 2)
+    __shared__ __align__(16) __half cb[256 * M1 * 3];
+    for (int i = threadIdx.x; i < 256 * M1 * 3 / 8; i += blockDim.x)
+        reinterpret_cast<uint4 *>(cb)[i] = __ldg(reinterpret_cast<const uint4 *>(C1h) + i);
+    __syncthreads();
+    const __half2 *cb2 = reinterpret_cast<const __half2 *>(cb);
+    const __half *cb1 = cb + 256 * M1 * 2;
+    const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+    const int64_t q0 = ((int64_t)blockIdx.x * TAB_WARPS + (threadIdx.x >> 5)) * 8;
+    if (q0 >= nq) return;
+    // B fragments (8 queries: query g, coordinates 2tg, 2tg + 1 of each sub-space) and the
+    // queries' sub-space norms, for all 32 sub-spaces
+    const int64_t qb = min(q0 + g, nq - 1);
+    uint32_t bf[M1];
+    float yn[M1];
+#pragma unroll
+    for (int j = 0; j < M1; j++) {
+        float y0 = 0.f, y1 = 0.f;
+        if (tg == 0) { y0 = __ldg(yq + qb * D + 3 * j); y1 = __ldg(yq + qb * D + 3 * j + 1); }
+        if (tg == 1) y0 = __ldg(yq + qb * D + 3 * j + 2);
+        bf[j] = pack_half2(y0, y1);
+        const __half2 h = *reinterpret_cast<const __half2 *>(&bf[j]);
+        const float r0 = __low2float(h), r1 = __high2float(h);
+        float p = r0 * r0 + r1 * r1;                     // this lane's part of ||y'_j||^2
+        p += __shfl_xor_sync(FULL, p, 1);
+        p += __shfl_xor_sync(FULL, p, 2);
+        yn[j] = p;                                       // query q0 + g
+    }
+    for (int ct = 0; ct < 16; ct++) {
+        const int clo = ct * 16 + g, chi = clo + 8;
+        uint32_t out[4][M1 / 2];                         // (clo, 2tg), (clo, 2tg+1), (chi, 2tg), (chi, 2tg+1)
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+        for (int j = 0; j < M1; j++) {
+            // A fragment: centroids clo and chi, coordinates 2tg, 2tg + 1 of sub-space j
+            uint32_t a0 = 0, a1 = 0;
+            if (tg == 0) {
+                a0 = *reinterpret_cast<const uint32_t *>(cb2 + clo * M1 + j);
+                a1 = *reinterpret_cast<const uint32_t *>(cb2 + chi * M1 + j);
+            } else if (tg == 1) {
+                a0 = pack_half2(__half2float(cb1[clo * M1 + j]), 0.f);
+                a1 = pack_half2(__half2float(cb1[chi * M1 + j]), 0.f);
+            }
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+            asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5}, {%6}, "
+                         "{%0, %1, %2, %3};"
+                         : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+                         : "r"(a0), "r"(a1), "r"(bf[j]));
+            // centroid norms (FP32 of the rounded values), summed over the quad's lanes
+            const __half2 hl = *reinterpret_cast<const __half2 *>(&a0), hh = *reinterpret_cast<const __half2 *>(&a1);
+            float nl = __low2float(hl) * __low2float(hl) + __high2float(hl) * __high2float(hl);
+            float nh = __low2float(hh) * __low2float(hh) + __high2float(hh) * __high2float(hh);
+            nl += __shfl_xor_sync(FULL, nl, 1);
+            nl += __shfl_xor_sync(FULL, nl, 2);
+            nh += __shfl_xor_sync(FULL, nh, 1);
+            nh += __shfl_xor_sync(FULL, nh, 2);
+            const float ya = __shfl_sync(FULL, yn[j], (2 * tg) * 4), yb = __shfl_sync(FULL, yn[j], (2 * tg + 1) * 4);
+            const float t0 = ya + nl - 2.f * d0, t1 = yb + nl - 2.f * d1, t2 = ya + nh - 2.f * d2, t3 = yb + nh - 2.f * d3;
+            // entries of consecutive sub-spaces share a 32-bit word (sub-space j - 1 low)
+            if ((j & 1) == 0) {
+                p0 = t0; p1 = t1; p2 = t2; p3 = t3;
+            } else {
+                out[0][j / 2] = pack_half2(p0, t0);
+                out[1][j / 2] = pack_half2(p1, t1);
+                out[2][j / 2] = pack_half2(p2, t2);
+                out[3][j / 2] = pack_half2(p3, t3);
+            }
+        }
+        // rows (query, centroid) of 32 entries = 64 bytes
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int c = e < 2 ? clo : chi;
+            const int64_t q = q0 + 2 * tg + (e & 1);
+            if (q >= nq) continue;
+            uint4 *dst = reinterpret_cast<uint4 *>(T + (q * 256 + c) * M1);
+            const uint4 *src = reinterpret_cast<const uint4 *>(&out[e][0]);
+#pragma unroll
+            for (int u = 0; u < 4; u++) dst[u] = src[u];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 constexpr int REF_CH = 8;            // candidates staged at a time
 
 __host__ __device__ inline int pow2_at_least(int r)
@@ -544,9 +652,21 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     WalkArgs wa{};
     wa.nq = nq;
     wa.d = dv->d;
-    P.half = sp->lut_prec == LC_LUT_FP16;
-    cudaError_t ce = walk_config(P.half, P.variant, dv->M1, P.full, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc,
-                                 &P.grid, &P.smem);
+    P.tab = sp->lut_prec == LC_LUT_TABLE;
+    if (P.tab && (P.variant != 2 || P.full)) {
+        set_error("the table form is built for 32 level-1 sub-spaces of 3 coordinates (d = 96) and the level-1 walk");
+        return LC_ERR_ARG;
+    }
+    P.half = sp->lut_prec == LC_LUT_FP16 || P.tab;
+    cudaError_t ce;
+    if (P.tab) {
+        P.per_warp += (size_t)256 * TAB_M1 * 2;                 // the query's table
+        P.tab_elems = (size_t)nq * 256 * TAB_M1;
+        ce = walk_config_tab(wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid, &P.smem);
+    } else {
+        ce = walk_config(P.half, P.variant, dv->M1, P.full, wa, P.per_warp, dv->num_sms, sp->warps, &P.wpc, &P.grid,
+                         &P.smem);
+    }
     if (ce == cudaErrorInvalidConfiguration) {
         set_error("search too wide for shared memory (%zu B per query in flight next to a %zu B codebook); "
                   "lower efSearch or visited_log", P.per_warp,
@@ -571,7 +691,8 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
         wd.nq = nq;
         wd.d = dv->d;
         wd.M2P = dv->M2P;
-        ce = descent_config(P.half, P.variant, dv->M1, P.full, wd, dv->num_sms, &P.dwpc, &P.dgrid, &P.dsmem);
+        ce = P.tab ? descent_config_tab(wd, dv->num_sms, &P.dwpc, &P.dgrid, &P.dsmem)
+                   : descent_config(P.half, P.variant, dv->M1, P.full, wd, dv->num_sms, &P.dwpc, &P.dgrid, &P.dsmem);
         if (ce != cudaSuccess) {
             set_error("descent kernel configuration failed: %s", cudaGetErrorString(ce));
             return LC_ERR_CUDA;
@@ -667,6 +788,13 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
     }
     if (!rotated) rotate_kernel<<<std::max(P.qgrid, 1), ROT_THREADS, P.qsm, st>>>(dq, dq8, nq, dv->d, dv->Rt, sc.yq);
     cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess && P.tab) {
+        // the batch's ADC tables on the tensor cores, from y'
+        table_kernel<<<(unsigned)((nq + TAB_WARPS * 8 - 1) / (TAB_WARPS * 8)), TAB_WARPS * 32, 0, st>>>(
+            sc.yq, nq, static_cast<const __half *>(dv->C1h), reinterpret_cast<__half *>(sc.tab));
+        ce = cudaGetLastError();
+        wa.tab = reinterpret_cast<const __half *>(sc.tab);
+    }
     if (profile) cudaEventRecord(dv->ev[3], st);
     if (ce != cudaSuccess) {
         set_error("rotation kernel launch failed: %s", cudaGetErrorString(ce));
@@ -681,7 +809,8 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         w1.seed = seed;
         w1.seed_up = seed_up;
         w1.seed_d = seed_d;
-        ce = descent_run(P.half, P.variant, dv->M1, P.full, w1, P.dsmem, P.dwpc, P.dgrid, st);
+        ce = P.tab ? descent_run_tab(w1, P.dsmem, P.dwpc, P.dgrid, st)
+                   : descent_run(P.half, P.variant, dv->M1, P.full, w1, P.dsmem, P.dwpc, P.dgrid, st);
         if (ce == cudaSuccess && cudaMemsetAsync(sc.counter, 0, sizeof(unsigned long long), st) == cudaSuccess) {
             order_kernel<<<1, ORDER_THREADS, 0, st>>>(seed_d, nq, order);
             ce = cudaGetLastError();
@@ -699,7 +828,8 @@ lc_status run_search(DeviceIndex *dv, const SearchPlan &P, const float *dq, int6
         wa.seed_d = seed_d;
     }
     if (profile) cudaEventRecord(dv->ev[4], st);
-    ce = walk_run(P.half, P.variant, dv->M1, P.full, wa, P.smem, P.wpc, P.grid, st);
+    ce = P.tab ? walk_run_tab(wa, P.smem, P.wpc, P.grid, st)
+               : walk_run(P.half, P.variant, dv->M1, P.full, wa, P.smem, P.wpc, P.grid, st);
     if (profile) cudaEventRecord(dv->ev[1], st);
     if (ce != cudaSuccess) {
         set_error("walk kernel launch failed: %s", cudaGetErrorString(ce));
@@ -830,7 +960,8 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
     }
     if (!grow(dv->spill, dv->spill_cap, P.spill_elems) || !grow(dv->yq, dv->yq_cap, P.yq_elems) ||
         (P.refine && !grow(dv->shortlist, dv->sl_cap, P.sl_elems)) ||
-        (P.ordered && !grow(dv->ord, dv->ord_cap, P.ord_elems))) {
+        (P.ordered && !grow(dv->ord, dv->ord_cap, P.ord_elems)) ||
+        (P.tab && !grow(dv->tab, dv->tab_cap, P.tab_elems))) {
         set_error("cudaMalloc failed for search scratch");
         return LC_ERR_OOM;
     }
@@ -839,6 +970,7 @@ lc_status search(lc_index *ix, const void *q, int qtype, int64_t nq, const lc_se
     sc.shortlist = dv->shortlist;
     sc.spill = dv->spill;
     sc.ord = dv->ord;
+    sc.tab = dv->tab;
     sc.status = dv->status;
     sc.counter = dv->counter;
     rs = run_search(dv, P, u8 ? nullptr : static_cast<const float *>(dq), nq, dids, ddists, dstats, sc, st,
@@ -1121,6 +1253,7 @@ void plan_free(lc_plan *pl)
     if (pl->graph) cudaGraphDestroy(pl->graph);
     cfree(pl->q); cfree(pl->ef); cfree(pl->ids); cfree(pl->dists); cfree(pl->stats);
     cfree(pl->sc.yq); cfree(pl->sc.shortlist); cfree(pl->sc.spill); cfree(pl->sc.status); cfree(pl->sc.counter);
+    cfree(pl->sc.tab);
     delete pl;
 }
 
@@ -1152,7 +1285,8 @@ lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, 
               alloc(pl->ids, (size_t)nq_max * k * 4) && alloc(pl->dists, (size_t)nq_max * k * 4) &&
               alloc(pl->stats, (size_t)nq_max * 12) && alloc(pl->sc.spill, P.spill_elems * 4) &&
               alloc(pl->sc.status, 4) && alloc(pl->sc.counter, 8) &&
-              alloc(pl->sc.yq, P.yq_elems * 4) && (!P.refine || alloc(pl->sc.shortlist, P.sl_elems * 4));
+              alloc(pl->sc.yq, P.yq_elems * 4) && (!P.refine || alloc(pl->sc.shortlist, P.sl_elems * 4)) &&
+              (!P.tab || alloc(pl->sc.tab, P.tab_elems * 2));
     if (!ok) {
         plan_free(pl);
         set_error("cudaMalloc failed for the plan's buffers");
@@ -1185,7 +1319,9 @@ lc_status plan_create(lc_index *ix, int64_t nq_max, const lc_search_params *sp, 
         return rs == LC_OK ? LC_ERR_CUDA : rs;
     }
     // find the two kernel nodes whose batch size a smaller call updates
-    const void *wf = walk_fn(P.half, P.variant, dv->M1, P.full);
+    // (the rotation and, in the table form, the table launch keep the largest batch: their
+    // extra rows are computed and not read)
+    const void *wf = P.tab ? walk_fn_tab() : walk_fn(P.half, P.variant, dv->M1, P.full);
     const void *rf = P.refine ? (const void *)refine_kernel_for(P.rboth, d, dv->bM > 1) : nullptr;
     size_t nn = 0;
     cudaGraphGetNodes(pl->graph, nullptr, &nn);

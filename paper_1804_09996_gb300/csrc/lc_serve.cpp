@@ -47,7 +47,7 @@ struct Batch {
     lc::SearchPlan plan;
     size_t need = 0, off = 0;
     // byte offsets of the batch's arrays inside its block
-    size_t o_q = 0, o_ef = 0, o_ids = 0, o_d = 0, o_st = 0, o_yq = 0, o_sl = 0, o_sp = 0, o_ord = 0, o_hdr = 0;
+    size_t o_q = 0, o_ef = 0, o_ids = 0, o_d = 0, o_st = 0, o_yq = 0, o_sl = 0, o_sp = 0, o_ord = 0, o_tab = 0, o_hdr = 0;
 };
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
@@ -85,6 +85,7 @@ void layout(Batch &b, int d)
     b.o_sl = o;  o += al(b.plan.sl_elems * 4);
     b.o_sp = o;  o += al(b.plan.spill_elems * 4);
     b.o_ord = o; o += al(b.plan.ord_elems * 4);
+    b.o_tab = o; o += al(b.plan.tab_elems * 2);
     b.o_hdr = o; o += 256;                    // status word and query counter
     b.need = o;
 }
@@ -211,6 +212,7 @@ lc_status launch(lc_server *s, lc_server::Slot &sl, Batch *b)
     sc.shortlist = reinterpret_cast<int32_t *>(base + b->o_sl);
     sc.spill = reinterpret_cast<int32_t *>(base + b->o_sp);
     sc.ord = reinterpret_cast<int32_t *>(base + b->o_ord);
+    sc.tab = reinterpret_cast<uint16_t *>(base + b->o_tab);
     sc.status = reinterpret_cast<int32_t *>(base + b->o_hdr);
     sc.counter = reinterpret_cast<unsigned long long *>(base + b->o_hdr + 8);
     float *hq = reinterpret_cast<float *>(sl.host + s->h_q);

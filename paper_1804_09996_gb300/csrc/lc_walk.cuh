@@ -97,6 +97,7 @@ struct WalkArgs {
     // order[i] (order may be null: position i is query i)
     int mode;
     const int32_t *order;
+    const __half *tab;     // table form: the queries' ADC tables [nq][256][M1] (FP16)
     int32_t *seed, *seed_up;
     float *seed_d;
 };
@@ -370,13 +371,18 @@ __device__ __forceinline__ float part_full(const CT *C1s, const CT *C2, int d, i
     return s;
 }
 
-// Sub-space terms of S slots (S = 16 or 32) for this lane, summed by reduce_slots<S>.
-template <int M1, int D1, int S, typename CT, bool FQ>
+// Sub-space terms of S slots (S = 16 or 32) for this lane, summed by reduce_slots<S>.  TAB:
+// C1s is the query's ADC table [256][M1] (FP16) and the term of code c is its entry [c][lane].
+template <int M1, int D1, int S, typename CT, bool FQ, bool TAB = false>
 __device__ __forceinline__ float score_slots(const CT *C1s, const uint8_t *stage, int nf, int d,
                                              const LaneGeo<M1, D1> &g, int lane, const CT *C2, int M2P)
 {
     float v[S];
-    if constexpr (FQ) {
+    if constexpr (TAB) {
+        static_assert(M1 == 32 && !FQ, "the table form is built for 32 sub-spaces");
+#pragma unroll
+        for (int i = 0; i < S; i++) v[i] = i < nf ? to_f(C1s[(int)stage[i * M1 + lane] * M1 + lane]) : 0.f;
+    } else if constexpr (FQ) {
         // full walk: one slot per step; the residual rows follow the 32 level-1 rows
         const uint8_t *stage2 = stage + 32 * M1;
         if (M1 == 16) {
@@ -446,7 +452,7 @@ __device__ __forceinline__ float score_slots(const CT *C1s, const uint8_t *stage
 // Walk distances of the nf nodes in slot[0..nf) (1 <= nf <= 32): their code rows are staged
 // in shared memory, each lane computes its sub-space terms, and the totals are formed with
 // 16 or 32 slots.  Returns lane's total; *my_slot = the slot it holds (>= 32: none).
-template <int M1, int D1, typename CT, bool FQ>
+template <int M1, int D1, typename CT, bool FQ, bool TAB = false>
 __device__ __forceinline__ float score_nodes(const CT *C1s, uint8_t *stage, const uint8_t *codes1,
                                              const int32_t *slot, int nf, int d,
                                              const LaneGeo<M1, D1> &g, int lane, int *my_slot,
@@ -466,10 +472,10 @@ __device__ __forceinline__ float score_nodes(const CT *C1s, uint8_t *stage, cons
     __syncwarp();
     float r;
     if (nf <= 16) {
-        r = score_slots<M1, D1, 16, CT, FQ>(C1s, stage, nf, d, g, lane, C2, M2P);
+        r = score_slots<M1, D1, 16, CT, FQ, TAB>(C1s, stage, nf, d, g, lane, C2, M2P);
         *my_slot = lane < 16 ? lane : 32;           // lanes l and l + 16 hold slot l
     } else {
-        r = score_slots<M1, D1, 32, CT, FQ>(C1s, stage, nf, d, g, lane, C2, M2P);
+        r = score_slots<M1, D1, 32, CT, FQ, TAB>(C1s, stage, nf, d, g, lane, C2, M2P);
         *my_slot = slot_of_lane(lane, 5);
     }
     __syncwarp();
@@ -520,7 +526,9 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
     return false;       // unreachable: the spill table is kept at most half full
 }
 
-template <int M1, int D1, typename CT, bool FQ>
+// TAB (the table form, LC_LUT_TABLE): no codebook; each warp keeps its query's ADC table
+// [256][M1] (FP16, built by table_kernel) in shared memory and scores nodes by table lookups.
+template <int M1, int D1, typename CT, bool FQ, bool TAB = false>
 __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -528,7 +536,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
     const int d = a.d;
     // the level-1 codebook, shared by every warp of the CTA
     CT *C1s = reinterpret_cast<CT *>(smem_raw);
-    {
+    if constexpr (!TAB) {
         const uint4 *src = reinterpret_cast<const uint4 *>(sizeof(CT) == 4 ? a.C1 : (const void *)a.C1h);
         uint4 *dst = reinterpret_cast<uint4 *>(C1s);
         const int n16 = (int)(walk_c1_bytes(d, M1, D1, sizeof(CT)) / 16);
@@ -548,7 +556,9 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
     }
     __syncthreads();
     const WalkSmem L = walk_smem(M1, d, a.efcap, a.hash_log, a.beam, a.yq_in == nullptr, FQ ? a.M2P : 0);
-    unsigned char *base = smem_raw + walk_cb_bytes(d, M1, D1, sizeof(CT), FQ) + (size_t)warp * L.total;
+    constexpr size_t TABB = TAB ? (size_t)256 * M1 * 2 : 0;            // the query's table
+    unsigned char *base = smem_raw + (TAB ? 0 : walk_cb_bytes(d, M1, D1, sizeof(CT), FQ)) + (size_t)warp * (L.total + TABB);
+    if constexpr (TAB) C1s = reinterpret_cast<CT *>(base + L.total);
     float *yq = reinterpret_cast<float *>(base + L.yq);
     uint8_t *stage = base + L.stage;
     uint64_t *wkey = reinterpret_cast<uint64_t *>(base + L.wkey);
@@ -571,6 +581,13 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         const int64_t q = a.order ? (int64_t)__ldg(a.order + qi) : qi;
         // this query's ef' = max(ef, k)
         const int efp = a.efq ? max(min(max(__ldg(a.efq + q), 1), a.efp), a.k) : a.efp;
+        if constexpr (TAB) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.tab + q * 256 * M1);
+            uint4 *dst = reinterpret_cast<uint4 *>(C1s);
+#pragma unroll 4
+            for (int i = lane; i < 256 * M1 * 2 / 16; i += 32) dst[i] = __ldg(src + i);
+            __syncwarp();
+        }
         // rotation y' = R y (fixed order u = 0..d-1); uint8 queries convert exactly to FP32
         const float *yrot = a.yq_in ? a.yq_in + q * d : yq;
         if (a.yq_in) {
@@ -791,7 +808,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             int nc = 0;
             for (int ch = 0; ch < ns; ch += 32) {
                 const int nf = min(32, ns - ch);
-                const float de = score_nodes<M1, D1, CT, FQ>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot,
+                const float de = score_nodes<M1, D1, CT, FQ, TAB>(C1s, stage, a.codes1, slot + ch, nf, d, g, lane, &my_slot,
                                                              C2, a.codes2b, a.M2P);
                 uint64_t k = my_slot < nf ? make_key(de, slot[ch + my_slot]) : ~0ull;
                 if (phase < 2) {
@@ -938,14 +955,14 @@ __host__ __device__ inline size_t descent_smem_per_warp(int M1, int m2p)
 // state (the level-2 sub-space of every coordinate), so it gets registers for 16 warps
 __host__ __device__ constexpr int descent_threads(bool fq) { return fq ? 16 * 32 : MAX_DESCENT_WARPS * 32; }
 
-template <int M1, int D1, typename CT, bool FQ>
+template <int M1, int D1, typename CT, bool FQ, bool TAB = false>
 __global__ void __launch_bounds__(descent_threads(FQ)) descent_kernel(const WalkArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int d = a.d;
     CT *C1s = reinterpret_cast<CT *>(smem_raw);
-    {
+    if constexpr (!TAB) {
         const uint4 *src = reinterpret_cast<const uint4 *>(sizeof(CT) == 4 ? a.C1 : (const void *)a.C1h);
         uint4 *dst = reinterpret_cast<uint4 *>(C1s);
         const int n16 = (int)(walk_c1_bytes(d, M1, D1, sizeof(CT)) / 16);
@@ -964,7 +981,8 @@ __global__ void __launch_bounds__(descent_threads(FQ)) descent_kernel(const Walk
     }
     __syncthreads();
     const int m2p = FQ ? a.M2P : 0;
-    unsigned char *base = smem_raw + walk_cb_bytes(d, M1, D1, sizeof(CT), FQ) + (size_t)warp * descent_smem_per_warp(M1, m2p);
+    unsigned char *base = smem_raw + (TAB ? 0 : walk_cb_bytes(d, M1, D1, sizeof(CT), FQ)) +
+                          (size_t)warp * descent_smem_per_warp(M1, m2p);
     uint8_t *stage = base;
     int32_t *slot = reinterpret_cast<int32_t *>(base + align_up((size_t)32 * (M1 + m2p), 16));
     const unsigned lt_mask = (1u << lane) - 1;
@@ -976,6 +994,8 @@ __global__ void __launch_bounds__(descent_threads(FQ)) descent_kernel(const Walk
         if (qi >= a.nq) break;
         const int64_t q = qi;
         const float *yrot = a.yq_in + q * d;       // y' = R y from the rotation kernel
+        // TAB: the query's ADC table [256][M1], read through L1 (a descent scores few nodes)
+        const CT *T1 = TAB ? reinterpret_cast<const CT *>(a.tab + q * 256 * M1) : C1s;
         LaneGeo<M1, D1> g;
 #pragma unroll
         for (int k = 0; k < LaneGeo<M1, D1>::NSUB; k++) {
@@ -1010,8 +1030,8 @@ __global__ void __launch_bounds__(descent_threads(FQ)) descent_kernel(const Walk
             uint64_t best = ~0ull;
             if (ns > 0) {
                 int my_slot;
-                const float de = score_nodes<M1, D1, CT, FQ>(C1s, stage, a.codes1, slot, ns, d, g, lane, &my_slot, C2,
-                                                             a.codes2b, a.M2P);
+                const float de = score_nodes<M1, D1, CT, FQ, TAB>(T1, stage, a.codes1, slot, ns, d, g, lane, &my_slot,
+                                                                  C2, a.codes2b, a.M2P);
                 const uint64_t k = my_slot < ns ? make_key(de, slot[my_slot]) : ~0ull;
                 best = warp_min64(k);
             }
@@ -1040,23 +1060,23 @@ __global__ void __launch_bounds__(descent_threads(FQ)) descent_kernel(const Walk
 constexpr size_t MAX_SMEM_PER_BLOCK = 227 * 1024;
 
 // Launch shape of the descent: as many warps as fit next to the codebook, at most 32.
-template <int M1, int D1, typename CT, bool FQ>
+template <int M1, int D1, typename CT, bool FQ, bool TAB = false>
 static cudaError_t launch_descent(const WalkArgs &wa, int sms, int *wpc_out, int *grid_out, size_t *smem_out)
 {
-    const size_t c1 = walk_cb_bytes(wa.d, M1, D1, sizeof(CT), FQ);
+    const size_t c1 = TAB ? 0 : walk_cb_bytes(wa.d, M1, D1, sizeof(CT), FQ);
     const size_t per = descent_smem_per_warp(M1, FQ ? wa.M2P : 0);
     if (c1 + per > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
     int wpc = (int)std::min<size_t>(MAX_DESCENT_WARPS, (MAX_SMEM_PER_BLOCK - c1) / per);
-    cudaError_t e = cudaFuncSetAttribute(descent_kernel<M1, D1, CT, FQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(descent_kernel<M1, D1, CT, FQ, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)MAX_SMEM_PER_BLOCK);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, descent_kernel<M1, D1, CT, FQ>);
+    e = cudaFuncGetAttributes(&fa, descent_kernel<M1, D1, CT, FQ, TAB>);
     if (e != cudaSuccess) return e;
     wpc = std::min(wpc, fa.maxThreadsPerBlock / 32);
     const size_t smem = c1 + per * wpc;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, descent_kernel<M1, D1, CT, FQ>, wpc * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, descent_kernel<M1, D1, CT, FQ, TAB>, wpc * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int64_t need = (wa.nq + wpc - 1) / wpc;
@@ -1074,31 +1094,31 @@ struct WalkShape {
     static constexpr bool FQ = C;
 };
 
-template <int M1, int D1, typename CT, bool FQ>
+template <int M1, int D1, typename CT, bool FQ, bool TAB = false>
 static cudaError_t run_descent(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
 {
-    descent_kernel<M1, D1, CT, FQ><<<grid, wpc * 32, smem, st>>>(wa);
+    descent_kernel<M1, D1, CT, FQ, TAB><<<grid, wpc * 32, smem, st>>>(wa);
     return cudaGetLastError();
 }
 
 // Warps per CTA: as many as fit next to the codebook (at most MAX_WALK_WARPS, and at most
 // want if want > 0).
-template <int M1, int D1, typename CT, bool FQ>
+template <int M1, int D1, typename CT, bool FQ, bool TAB = false>
 static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num_sms, int want, int *wpc_out,
                                int *grid_out, size_t *smem_out)
 {
-    size_t c1 = walk_cb_bytes(wa.d, M1, D1, sizeof(CT), FQ);
+    size_t c1 = TAB ? 0 : walk_cb_bytes(wa.d, M1, D1, sizeof(CT), FQ);
     if (c1 + smem_per_warp > MAX_SMEM_PER_BLOCK) return cudaErrorInvalidConfiguration;
     int wpc = (int)std::min<size_t>(MAX_WALK_WARPS, (MAX_SMEM_PER_BLOCK - c1) / smem_per_warp);
     if (want > 0) wpc = std::min(wpc, want);
     size_t smem = c1 + smem_per_warp * wpc;
     // the attribute is an upper bound: set to the maximum, so plans made in any order (the
     // server plans at submission and launches later) all remain launchable
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1, CT, FQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<M1, D1, CT, FQ, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)MAX_SMEM_PER_BLOCK);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1, CT, FQ>, wpc * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<M1, D1, CT, FQ, TAB>, wpc * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int64_t need = (wa.nq + wpc - 1) / wpc;
@@ -1108,10 +1128,10 @@ static cudaError_t launch_walk(const WalkArgs &wa, size_t smem_per_warp, int num
     return cudaSuccess;
 }
 
-template <int M1, int D1, typename CT, bool FQ>
+template <int M1, int D1, typename CT, bool FQ, bool TAB = false>
 static cudaError_t run_walk(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
 {
-    walk_kernel<M1, D1, CT, FQ><<<grid, wpc * 32, smem, st>>>(wa);
+    walk_kernel<M1, D1, CT, FQ, TAB><<<grid, wpc * 32, smem, st>>>(wa);
     return cudaGetLastError();
 }
 
@@ -1150,6 +1170,14 @@ inline cudaError_t descent_run(bool half, int variant, int M1, bool fq, const Wa
     return half ? descent_run_f16(variant, M1, fq, wa, smem, wpc, grid, st)
                 : descent_run_f32(variant, M1, fq, wa, smem, wpc, grid, st);
 }
+
+// The table form (LC_LUT_TABLE; M1 = 32 at d = 96): launch shape, launch, kernel address of
+// the walk, and the descent launch of an ordered search.
+cudaError_t walk_config_tab(const WalkArgs &wa, size_t per_warp, int sms, int want, int *wpc, int *grid, size_t *smem);
+cudaError_t walk_run_tab(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st);
+const void *walk_fn_tab();
+cudaError_t descent_config_tab(const WalkArgs &wa, int sms, int *wpc, int *grid, size_t *smem);
+cudaError_t descent_run_tab(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st);
 
 inline cudaError_t walk_config(bool half, int variant, int M1, bool fq, const WalkArgs &wa, size_t per_warp, int sms,
                                int want, int *wpc, int *grid, size_t *smem)

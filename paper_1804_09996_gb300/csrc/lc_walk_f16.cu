@@ -114,4 +114,26 @@ cudaError_t descent_run_f16(int variant, int M1, bool fq, const WalkArgs &wa, si
     });
 }
 
+cudaError_t walk_config_tab(const WalkArgs &wa, size_t per_warp, int sms, int want, int *wpc, int *grid, size_t *smem)
+{
+    return launch_walk<32, 3, __half, false, true>(wa, per_warp, sms, want, wpc, grid, smem);
+}
+
+cudaError_t walk_run_tab(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
+{
+    return run_walk<32, 3, __half, false, true>(wa, smem, wpc, grid, st);
+}
+
+const void *walk_fn_tab() { return (const void *)walk_kernel<32, 3, __half, false, true>; }
+
+cudaError_t descent_config_tab(const WalkArgs &wa, int sms, int *wpc, int *grid, size_t *smem)
+{
+    return launch_descent<32, 3, __half, false, true>(wa, sms, wpc, grid, smem);
+}
+
+cudaError_t descent_run_tab(const WalkArgs &wa, size_t smem, int wpc, int grid, cudaStream_t st)
+{
+    return run_descent<32, 3, __half, false, true>(wa, smem, wpc, grid, st);
+}
+
 }  // namespace lc

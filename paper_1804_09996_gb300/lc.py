@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblc.so")
 LC_OK, LC_ERR_ARG, LC_ERR_OOM, LC_ERR_STATE, LC_ERR_CUDA = 0, 1, 2, 3, 4
 LC_ERR_TIMEOUT, LC_ERR_BUDGET, LC_ERR_IO, LC_ERR_CAPACITY = 5, 6, 7, 8
 LC_MODE_PLAIN, LC_MODE_BATCHED = 0, 1
-LC_LUT_FP32, LC_LUT_FP16 = 0, 1
+LC_LUT_FP32, LC_LUT_FP16, LC_LUT_TABLE = 0, 1, 2
 LC_QUERY_F32, LC_QUERY_U8 = 0, 1
 LC_ORDER_AUTO, LC_ORDER_NEVER, LC_ORDER_ALWAYS = 0, 1, 2
 
