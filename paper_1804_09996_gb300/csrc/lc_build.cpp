@@ -415,15 +415,22 @@ lc_status build_train(lc_index *ix, const float *xt, int64_t nt_)
             pq_train(Xr.data(), nt_, d, p.M1, 1, p.seed + 11, ix->C1.data(), true, nt);
             pq_encode(Xr.data(), nt_, d, p.M1, ix->C1.data(), codes.data(), nt);
             pq_decode(codes.data(), nt_, d, p.M1, ix->C1.data(), dec.data(), false, nt);
-            // M = sum_i xhat_i x_i^T; the rotation maximising tr(R^T M) is its polar factor
-            std::vector<std::vector<double>> part(nt, std::vector<double>((size_t)d * d, 0.0));
-            parallel_for(nt_, nt, 4096, [&](int64_t a, int64_t b, int t) {
-                auto &Mp = part[t];
-                for (int64_t i = a; i < b; i++)
-                    for (int r = 0; r < d; r++) {
-                        double y = dec[(size_t)i * d + r];
-                        for (int c = 0; c < d; c++) Mp[(size_t)r * d + c] += y * (double)xt[i * d + c];
-                    }
+            // M = sum_i xhat_i x_i^T; the rotation maximising tr(R^T M) is its polar factor.
+            // Partial sums over fixed chunks of rows, added in chunk order: M (and so R and
+            // the whole index) does not depend on the thread count or the scheduling.
+            constexpr int64_t MCH = 4096;
+            const int64_t nch = (nt_ + MCH - 1) / MCH;
+            std::vector<std::vector<double>> part((size_t)nch);
+            parallel_for(nch, nt, 1, [&](int64_t a, int64_t b, int) {
+                for (int64_t ch = a; ch < b; ch++) {
+                    auto &Mp = part[(size_t)ch];
+                    Mp.assign((size_t)d * d, 0.0);
+                    for (int64_t i = ch * MCH; i < std::min(nt_, (ch + 1) * MCH); i++)
+                        for (int r = 0; r < d; r++) {
+                            double y = dec[(size_t)i * d + r];
+                            for (int c = 0; c < d; c++) Mp[(size_t)r * d + c] += y * (double)xt[i * d + c];
+                        }
+                }
             });
             std::vector<double> M((size_t)d * d, 0.0);
             for (auto &Mp : part)

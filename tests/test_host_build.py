@@ -124,6 +124,27 @@ def test_add_in_two_calls_keeps_ids_and_structure():
         lc.lc_free(h)
 
 
+def test_build_does_not_depend_on_the_thread_count():
+    # every parallel reduction of train/add has a fixed order: 1, 3 and all threads build the
+    # same index bit for bit (OPQ rotation, both codebooks, codes, graph, codewords)
+    d, M1, M2 = 96, 32, 31
+    xt = dg.gaussian_mixture(40000, d, 64, stream=dg.STREAM_TRAIN)
+    xb = dg.gaussian_mixture(2500, d, 64, stream=dg.STREAM_BASE)
+    out = []
+    for nt in (1, 3, 0):
+        h = lc.lc_create(lc.lc_default_params(d, M1, M2, use_opq=1, opq_iters=2, kmeans_iters=4, batch_max=256,
+                                              n_threads=nt))
+        try:
+            lc.lc_train(h, xt)
+            lc.lc_add(h, xb)
+            out.append(lc.lc_export(h, d, M1, M2))
+        finally:
+            lc.lc_free(h)
+    for ex in out[1:]:
+        for key in ("R", "C1", "C2", "codes1", "codes2", "beta", "B", "adj0", "levels", "upper_adj"):
+            assert np.array_equal(np.asarray(ex[key]), np.asarray(out[0][key])), key
+
+
 def test_add_u8_equals_add_of_the_same_values():
     d = 32
     xt = dg.sift_like(1500, d, 32, stream=dg.STREAM_TRAIN)
