@@ -427,23 +427,38 @@ __global__ void __launch_bounds__(16 * 32) refine_kernel(const RefineArgs a)
             __syncwarp();
             for (int r = 0; r < nc; r++) {
                 // y^_t = sum_j beta_j (C1[c1_j][t] + C2[c2_j][t]) for this lane's coordinates,
-                // accumulated over j in order; then sum_t (y'_t - y^_t)^2 over t ascending
-                float yh[DU];
+                // accumulated over j in order; then sum_t (y'_t - y^_t)^2 over t ascending.
+                // A missing neighbour (id -1) takes weight 0: its staged rows hold stale but
+                // valid codes, and fma(0, x, s) = s for the finite x of a codebook, so every
+                // C2 read of the candidate is issued before the first is used (up to 4
+                // coordinates per lane; beyond, the 9 x DU values would not stay in registers).
+                constexpr bool HOIST = DU <= 4;
+                float yh[DU], x2[HOIST ? 9 : 1][DU];
+                if constexpr (HOIST) {
+#pragma unroll
+                    for (int j = 0; j < 9; j++) {
+                        const uint8_t *c2r = st2 + (r * 9 + j) * M2P;
+#pragma unroll
+                        for (int u = 0; u < DU; u++) x2[j][u] = C2[(int)c2r[s2v[u]] * d + lane + 32 * u];
+                    }
+                }
 #pragma unroll
                 for (int u = 0; u < DU; u++) yh[u] = 0.f;
 #pragma unroll
                 for (int j = 0; j < 9; j++) {
                     const int tt = r * 9 + j;
-                    if (vid[tt] < 0) continue;
-                    const float w0 = wt[r * BM * 9 + j];
+                    const bool have = vid[tt] >= 0;
+                    if (!HOIST && !have) continue;
+                    const float w0 = have ? wt[r * BM * 9 + j] : 0.f;
                     const uint8_t *c1r = st1 + tt * M1, *c2r = st2 + tt * M2P;
 #pragma unroll
                     for (int u = 0; u < DU; u++) {
                         const int t = lane + 32 * u;
                         if (DU == 8 && t >= d) continue;
                         // the weight of this coordinate's regression block
-                        const float w = PROD ? wt[(r * BM + sbv[u]) * 9 + j] : w0;
-                        const float x = C1s[(int)c1r[s1v[u]] * d + t] + C2[(int)c2r[s2v[u]] * d + t];
+                        const float w = PROD ? (have ? wt[(r * BM + sbv[u]) * 9 + j] : 0.f) : w0;
+                        const float x = C1s[(int)c1r[s1v[u]] * d + t] +
+                                        (HOIST ? x2[HOIST ? j : 0][u] : C2[(int)c2r[s2v[u]] * d + t]);
                         yh[u] = fmaf(w, x, yh[u]);
                     }
                 }

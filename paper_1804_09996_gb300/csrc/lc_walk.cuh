@@ -150,18 +150,21 @@ __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
 
 // own_rot: the walk rotates the query itself (y' in shared memory); otherwise y' is read from
-// the rotation kernel's output.  The adjacency rows of a step are only read before the
-// candidates are collected, so they share the unsorted-candidate area.
+// the rotation kernel's output.  Areas whose lives do not overlap within a step share memory:
+// the adjacency rows are read before the candidates are collected (the unsorted-candidate
+// area), and the staged code rows are dead once the step's nodes are scored, before the
+// candidates are sorted (the sorted-candidate area).  W is one buffer, merged in place.
 __host__ __device__ inline WalkSmem walk_smem(int M1, int d, int efcap, int hash_log, int beam, bool own_rot,
                                              int m2p = 0)
 {
     WalkSmem s;
     size_t o = 0;
     s.yq = o;        o += own_rot ? align_up((size_t)d * 4, 16) : 0;
-    s.stage = o;     o += (size_t)32 * (M1 + m2p);     // level-1 rows, then (full walk) residual rows
-    s.wkey = o;      o += (size_t)2 * efcap * 8;
-    s.wflag = o;     o += align_up((size_t)2 * efcap, 16);
-    s.cand = o;      o += (size_t)32 * beam * 8;
+    s.stage = o;                                       // level-1 rows, then (full walk) residual rows
+    const size_t st_b = (size_t)32 * (M1 + m2p), cd_b = (size_t)32 * beam * 8;
+    s.cand = o;      o += align_up(st_b > cd_b ? st_b : cd_b, 16);
+    s.wkey = o;      o += (size_t)efcap * 8;
+    s.wflag = o;     o += align_up((size_t)efcap, 16);
     s.cunsorted = o; o += (size_t)32 * beam * 8;
     s.rowbuf = s.cunsorted;
     s.slot = o;      o += (size_t)32 * beam * 4;
@@ -632,7 +635,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
         float dcur = 0.f;
         int lvl = a.max_level;             // upper level being descended
         int phase = 0;                     // 0: entry point, 1: upper levels, 2: level 0
-        int buf = 0, wn = 1;
+        int wn = 1;
         bool spilled = false, failed = false;
         int32_t hcount = 1, scount = 0;
         int scan_from = 0;
@@ -652,8 +655,8 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             __syncwarp();
         }
         for (;;) {
-            uint64_t *W = wkey + buf * a.efcap;
-            uint8_t *F = wflag + buf * a.efcap;
+            uint64_t *W = wkey;
+            uint8_t *F = wflag;
             int ns = 0, pos0 = 0;
             uint64_t ckey0 = 0;
             if (phase == 0) {
@@ -868,20 +871,12 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                 cand[r] = mk;
             }
             __syncwarp();
-            // merge W (wn keys) with the nc candidates into the other buffer, keep ef'
-            uint64_t *W2 = wkey + (buf ^ 1) * a.efcap;
-            uint8_t *F2 = wflag + (buf ^ 1) * a.efcap;
+            // merge the nc candidates into W (wn keys) in place, keep ef': a candidate's place
+            // is its rank plus the members below it, a member's its index plus the candidates
+            // below it.  The candidates' places are taken first (into slot[], free after
+            // scoring); members only move up, so chunks of 32 move from the last one down,
+            // each read whole before it is written; the candidates are written last.
             const int wn2 = min(efp, wn + nc);
-            for (int p = lane; p < wn; p += 32) {
-                const uint64_t key = W[p];
-                int lo = 0, hi = nc;                     // candidates below key
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cand[mid] < key) lo = mid + 1; else hi = mid;
-                }
-                const int np = p + lo;
-                if (np < wn2) { W2[np] = key; F2[np] = F[p]; }
-            }
             int first_new = efp;
             for (int m0 = lane; m0 < nc; m0 += 32) {
                 const uint64_t ck = cand[m0];
@@ -890,11 +885,35 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                     const int mid = (lo + hi) >> 1;
                     if (W[mid] < ck) lo = mid + 1; else hi = mid;
                 }
-                const int np = m0 + lo;
-                if (np < wn2) { W2[np] = ck; F2[np] = 0; }
-                if (m0 == 0) first_new = np;
+                slot[m0] = m0 + lo;
+                if (m0 == 0) first_new = m0 + lo;
             }
             first_new = __shfl_sync(FULL, first_new, 0);
+            __syncwarp();
+            // members before the first candidate's place keep theirs
+            for (int c0 = (wn - 1) & ~31; c0 >= (first_new & ~31); c0 -= 32) {
+                const int p = c0 + lane;
+                uint64_t key = 0;
+                uint8_t f = 0;
+                int np = p;
+                if (p < wn) {
+                    key = W[p];
+                    f = F[p];
+                    int lo = 0, hi = nc;                 // candidates below key
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (cand[mid] < key) lo = mid + 1; else hi = mid;
+                    }
+                    np = p + lo;
+                }
+                __syncwarp();
+                if (np != p && np < wn2) { W[np] = key; F[np] = f; }
+                __syncwarp();
+            }
+            for (int m0 = lane; m0 < nc; m0 += 32) {
+                const int np = slot[m0];
+                if (np < wn2) { W[np] = cand[m0]; F[np] = 0; }
+            }
             // everything before min(first new candidate, first expanded node's new place) is
             // expanded
             int below = 0;
@@ -902,7 +921,6 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             scan_from = min(first_new, pos0 + below);
             scan_from -= scan_from % 32;
             wn = wn2;
-            buf ^= 1;
             __syncwarp();
         }
 
@@ -911,7 +929,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
             continue;
         }
         // outputs
-        const uint64_t *W = wkey + buf * a.efcap;
+        const uint64_t *W = wkey;
         if (a.refine) {
             if (!a.yq_in)
                 for (int t = lane; t < d; t += 32) a.yq_out[q * d + t] = yq[t];
