@@ -88,17 +88,20 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, form: str):
-    """DRAM bytes per level-0 walk launch of the given form (e.g. 'batched_fp16_ef48') from
-    the committed ncu summary, if it was taken on the current kernel source (its
-    'kernel_source_sha256_16' line must match)."""
+def profiled_traffic(workload: str, form: str, nq: int):
+    """DRAM bytes of a level-0 walk launch of nq queries of the given form (e.g.
+    'batched_fp16_ef48') from the committed ncu summary, if it was taken on the current kernel
+    source (its 'kernel_source_sha256_16' line must match).  A summary taken on another batch
+    size ('queries_per_launch') is scaled by the query count: the walks are independent, so
+    the traffic grows with the queries."""
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         txt = open(f).read()
         m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
         w = re.search(r"workload:\s*(\S+)", txt)
         t = re.search(r"dram_bytes_per_level0_launch_" + form + r":\s*([0-9.eE+]+)", txt)
+        n = re.search(r"queries_per_launch:\s*([0-9]+)", txt)
         if m and w and t and w.group(1) == workload and m.group(1) == kernel_hash():
-            return float(t.group(1))
+            return float(t.group(1)) * (nq / int(n.group(1)) if n else 1.0)
     return None
 
 
@@ -488,7 +491,7 @@ def measure_large(args, dev, flush, stream):
         if r["recall"] >= target:
             break
     best = run(sp_b, steps)
-    best_name, best_ef = f"batched(beam={args.beam}), fp16 codebook", sp_b.ef
+    best_name, best_ef, best_sp = f"batched(beam={args.beam}), fp16 codebook", sp_b.ef, sp_b
     # the library's autotuner on a disjoint sample with exact neighbours (beam, codebook
     # precision, efSearch and launch shape for this index and batch size)
     xs = extra_queries(w, nq, 2000)
@@ -500,33 +503,40 @@ def measure_large(args, dev, flush, stream):
             "codebook": "fp16" if sp_t.lut_prec else "fp32", "efSearch": sp_t.ef, "warps": sp_t.warps,
             "visited_log": sp_t.visited_log, "candidates": tr.tried}
     if tuned["recall"] >= target and tuned["qps"] > best["qps"]:
-        best, best_ef = tuned, sp_t.ef
+        best, best_ef, best_sp = tuned, sp_t.ef, sp_t
         best_name = f"autotuned ({tune['mode']}, beam {tune['beam']}, {tune['codebook']} codebook)"
     clk = clocks.stop()
     lc.lc_free(h)
     del q, ids, dists, stats
     torch.cuda.empty_cache()
 
-    def roof(r):
+    def roof(r, sp):
         b, t = level0_bytes(r["stats"], w["M1"], d, k, r["descent_ms"] > 0), r["level0_ms"]
         peak, src = peaks()
         got = b / (t / 1e3) / 1e9
+        # DRAM traffic from the committed ncu summary of this workload (taken on 10k queries,
+        # scaled to this launch's query count), for the default launch shape only
+        key = (("batched" if sp.mode else "plain") + ("_full" if sp.walk_full else "")
+               + ("_table" if sp.lut_prec == lc.LC_LUT_TABLE else "_fp16" if sp.lut_prec else "") + f"_ef{sp.ef}")
+        traffic = None if (sp.warps or sp.visited_log not in (0, 11) or (sp.mode and sp.beam != args.beam)) else \
+            profiled_traffic(args.large, key, nq)
         return {"bound": "hbm", "achieved": got, "peak": peak, "unit": "GB/s", "frac": got / peak,
                 "kernel": "walk_kernel (level-0 launch)", "launch_ms": t, "peak_source": src,
-                "algorithmic_bytes_per_launch": b}
+                "algorithmic_bytes_per_launch": b, "traffic": traffic,
+                "traffic_source": None if traffic is None else "ncu summary of a 10k-query launch, scaled by queries"}
 
-    def summ(r, ef, form):
+    def summ(r, ef, form, sp):
         return {"form": form, "efSearch": ef, "qps": r["qps"], "ms_per_step": r["ms"], "recall_at_1": r["recall"],
                 "walk_ms": r["walk_ms"], "refine_ms": r["refine_ms"], "rotate_ms": r["rotate_ms"],
                 "descent_ms": r["descent_ms"], "level0_ms": r["level0_ms"],
                 "mean_n_dist": float(r["stats"][:, 0].mean()), "mean_n_expand": float(r["stats"][:, 1].mean()),
-                "roofline": roof(r)}
+                "roofline": roof(r, sp)}
 
     return {"workload": args.large, "desc": w["desc"].replace("10k queries/step", f"{nq // 1000}k queries/step"),
             "queries_per_step": nq, "recall_queries": n_gt, "recall_target": target, "steps": steps,
             "index_build": "GPU-assisted", "data_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
-            "plain": summ(plain, args.ef, "plain, fp32 codebook"),
-            "headline": summ(best, best_ef, best_name),
+            "plain": summ(plain, args.ef, "plain, fp32 codebook", sp_p),
+            "headline": summ(best, best_ef, best_name, best_sp),
             "sweep": sweep, "autotune": tune, "clocks": clk,
             "l2": "flushed before every step (256 MB read, outside the timed span)"}
 
@@ -788,7 +798,7 @@ def main():
         ("batched" if bsp.mode else "plain") + ("_full" if bsp.walk_full else "")
         + ("_table" if bsp.lut_prec == lc.LC_LUT_TABLE else "_fp16" if bsp.lut_prec else "")
         + f"_ef{bsp.ef}")
-    traffic = profiled_traffic(args.workload, form_key) if form_key else None
+    traffic = profiled_traffic(args.workload, form_key, nq) if form_key else None
 
     # e2e through the same C ABI call with pinned host buffers
     best_sp, best_efq = best_form

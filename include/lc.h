@@ -109,8 +109,8 @@ typedef struct {
     int lut_prec;    /* LC_LUT_FP32, LC_LUT_FP16 or LC_LUT_TABLE */
     int mode;        /* LC_MODE_PLAIN or LC_MODE_BATCHED */
     int visited_log; /* 0: automatic; 10..14: the per-query visited table in shared memory has
-                        2^visited_log entries (ids beyond half of it go to a table in global
-                        memory, see spill_log) */
+                        2^visited_log entries (ids beyond three quarters of it go to a table
+                        in global memory, see spill_log) */
     int beam;        /* LC_MODE_BATCHED: expansions per step, 2..8 (ignored in PLAIN mode) */
     int max_dist;    /* search-time cap T (Section 3.1): 0 = none; > 0: the level-0 search stops
                         before an expansion once T distances have been computed there */
@@ -132,9 +132,9 @@ typedef struct {
                         that order, so the batch does not end on a few long walks.  Results do
                         not depend on it */
     int spill_log;   /* the per-query visited table in global memory (one per query in flight,
-                        taking the ids once the shared table is half full): 0 = automatic,
-                        2^13 .. 2^16 entries as max(ef, k) grows (64 entries per result-set
-                        slot); 8..16: 2^spill_log entries.  A query that would fill it beyond
+                        taking the ids once the shared table is three quarters full):
+                        0 = automatic, 2^13 .. 2^16 entries as max(ef, k) grows (64 entries per
+                        result-set slot); 8..16: 2^spill_log entries.  A query that would fill it beyond
                         half fails: LC_ERR_CAPACITY (host pointers) or n_dist = -1 and ids -1
                         (device pointers), the other queries of the batch are unaffected */
 } lc_search_params;

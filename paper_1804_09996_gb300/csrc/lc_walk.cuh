@@ -498,6 +498,12 @@ __device__ __forceinline__ uint32_t hash32(int32_t e)
 // Inserts e into the visited set; true if it was not there.  The shared table takes
 // inserts until the walk switches to spill mode; from then on it is only read and new ids
 // go to the warp's global table.
+// Ids the shared visited table of H entries takes before the walk switches to the global one.
+// Filling to three quarters rather than half (triangular probing: probe sequences stay short)
+// measured 0.606 against 0.645 ms for the 1M workload's level-0 launch (fewer walks spill);
+// seven eighths measured 0.654 ms.
+__host__ __device__ constexpr int shared_visited_cap(int H) { return H - H / 4; }
+
 __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool spilled,
                                       int32_t *spill, int slog)
 {
@@ -510,7 +516,7 @@ __device__ __forceinline__ bool visit(int32_t e, int32_t *hash, int hlog, bool s
             if (old == e) return false;
             h = (h + p + 1) & Hm;
         }
-        return false;   // unreachable: the table is kept at most half full
+        return false;   // unreachable: the table is kept at most three quarters full
     }
     for (uint32_t p = 0; p <= Hm; p++) {
         int32_t v = hash[h];
@@ -696,7 +702,7 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                 }
                 __syncwarp();
                 // visited test row by row (row order, then slot order); fresh nodes are appended
-                if (!spilled && hcount + 32 * nb <= H / 2) {
+                if (!spilled && hcount + 32 * nb <= shared_visited_cap(H)) {
                     // every row fits in the shared table without a switch to the spill table: the
                     // first probes of up to 4 rows are issued together, then each row is resolved
                     // in row order (a node in two rows probes the same bucket first, so it is
@@ -780,8 +786,8 @@ __global__ void __launch_bounds__(MAX_WALK_WARPS * 32) walk_kernel(const WalkArg
                         }
                     }
                 } else for (int r = 0; r < nb; r++) {
-                    // switch to the global table before the shared one passes half full
-                    if (!spilled && hcount + 32 > H / 2) {
+                    // switch to the global table before the shared one passes its limit
+                    if (!spilled && hcount + 32 > shared_visited_cap(H)) {
                         spilled = true;
                         for (int i = lane; i < (1 << a.spill_log); i += 32) spill[i] = -1;
                         __syncwarp();

@@ -2,11 +2,11 @@
 own, and the batch reports it, while every other query of the batch is unaffected.
 
 The walk keeps the visited set of Section 2's search in a shared-memory table of
-2^visited_log entries, filled to half, then in a global table of 2^spill_log entries, filled
-to half.  Both tables are made small here (2^10 and 2^9 entries) so that, at efSearch 128
-on the 3,000-vector index, the walks that score more than 768 distinct nodes (the oracle
-counts them) cannot fit and must fail, while those that score fewer than 706 (the two
-halves less one 32-node row each, the headroom the walk keeps before a row) always fit.
+2^visited_log entries, filled to three quarters, then in a global table of 2^spill_log
+entries, filled to half.  Both tables are made small here (2^10 and 2^9 entries) so that, at
+efSearch 192 on the 3,000-vector index, the walks that score more than 1,024 distinct nodes
+(the oracle counts them) cannot fit and must fail, while those that score fewer than 962 (the
+two limits less one 32-node row each, the headroom the walk keeps before a row) always fit.
 Host pointers: the call returns LC_ERR_CAPACITY.  Device pointers: the failed queries
 report n_dist = -1 and ids -1; every query that fits equals the oracle, as in the parity
 tests.  The kernel reports the overflow and returns; nothing waits.
@@ -20,9 +20,10 @@ from test_gpu_parity import TIE, compare, handle
 
 pytestmark = pytest.mark.gpu
 
-VLOG, SLOG, EF = 10, 9, 128
-FITS = (1 << VLOG) // 2 + (1 << SLOG) // 2 - 62       # below this, no query can fail
-OVER = (1 << VLOG) // 2 + (1 << SLOG) // 2             # above this, every query must fail
+VLOG, SLOG, EF = 10, 9, 192
+SHARED = (1 << VLOG) - (1 << VLOG) // 4                # ids the shared table takes
+FITS = SHARED + (1 << SLOG) // 2 - 62                  # below this, no query can fail
+OVER = SHARED + (1 << SLOG) // 2                       # above this, every query must fail
 
 
 def search(h, xq, k, shortlist, beam, device=True):
@@ -71,7 +72,9 @@ def test_overflowing_queries_fail_alone(mix3k, shortlist, beam):
     assert not failed[fits].any()
     # the rest of the batch is exactly the oracle's
     ok = ~failed
-    compare(rows_of(ref, ok), ids[ok], ds[ok], st[ok], max_exempt=0.05)     # measured <= 3.4 %
+    # near-tie shares of the fitting queries at efSearch 192 (from the oracle): 10.1 % plain,
+    # 2.8-3.2 % batched
+    compare(rows_of(ref, ok), ids[ok], ds[ok], st[ok], max_exempt=0.13)
     # host pointers: the batch reports the overflow
     with pytest.raises(lc.LcError) as e:
         search(h, xq, 10, shortlist, beam, device=False)
