@@ -506,6 +506,9 @@ def measure_large(args, dev, flush, stream):
         best, best_ef, best_sp = tuned, sp_t.ef, sp_t
         best_name = f"autotuned ({tune['mode']}, beam {tune['beam']}, {tune['codebook']} codebook)"
     clk = clocks.stop()
+    # the request server on this index (the serving workload's 10M index): saturation and
+    # open-loop latency, as for the headline workload
+    served = measure_serving(lc, h, xq, gt, k, args, best_sp) if args.serve else None
     lc.lc_free(h)
     del q, ids, dists, stats
     torch.cuda.empty_cache()
@@ -537,7 +540,7 @@ def measure_large(args, dev, flush, stream):
             "index_build": "GPU-assisted", "data_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
             "plain": summ(plain, args.ef, "plain, fp32 codebook", sp_p),
             "headline": summ(best, best_ef, best_name, best_sp),
-            "sweep": sweep, "autotune": tune, "clocks": clk,
+            "sweep": sweep, "autotune": tune, "clocks": clk, "served": served,
             "l2": "flushed before every step (256 MB read, outside the timed span)"}
 
 

@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "liblc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU = ["lc_search.cu", "lc_walk_f32.cu", "lc_walk_f16.cu"]
+CU = ["lc_search.cu", "lc_walk_f32.cu", "lc_walk_f16.cu", "lc_build_gpu.cu"]
 CPP = ["lc_capi.cpp", "lc_build.cpp", "lc_serve.cpp", "lc_tune.cpp"]
 
 

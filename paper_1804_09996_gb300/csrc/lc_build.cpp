@@ -589,7 +589,8 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
     const bool gpu = p.build_gpu != 0;
     if (gpu) {
         lc_status rs = build_gpu_begin(ix);
-        if (rs != LC_OK) return rs;
+        if (rs == LC_OK) rs = build_gpu_link0_begin(ix);
+        if (rs != LC_OK) { build_gpu_end(ix); return rs; }
     }
     const int efc = p.ef_construction;
     std::vector<int64_t> gmem;                  // batch members searched on the device
@@ -657,12 +658,14 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
                 }
             }
         });
-        // the new nodes' own rows, sorted by decoded-to-decoded distance
+        // the new nodes' own rows, sorted by decoded-to-decoded distance (level 0 on the
+        // device in the GPU-assisted build)
+        const int l_own = gpu ? 1 : 0;
         parallel_for(b, nt, 64, [&](int64_t a, int64_t e, int) {
             for (int64_t u = a; u < e; u++) {
                 int64_t x = ncur + u;
                 int top = std::min((int)ix->levels[x], ml0);
-                for (int l = 0; l <= top && ep0 >= 0; l++) {
+                for (int l = l_own; l <= top && ep0 >= 0; l++) {
                     const int32_t *s = sel[u].data() + (size_t)l * (DEG + 1);
                     int cnt = s[DEG];
                     Key ks[DEG];
@@ -693,26 +696,41 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
             if (i == 0 || links[i].level != links[i - 1].level || links[i].target != links[i - 1].target)
                 starts.push_back(i);
         starts.push_back(links.size());
-        parallel_for((int64_t)starts.size() - 1, nt, 64, [&](int64_t a, int64_t e, int) {
-            for (int64_t gi = a; gi < e; gi++)
+        // GPU-assisted build: level 0's own rows and back-links on the device (the groups of
+        // level 0 come first), the upper levels here
+        size_t g0 = 0;
+        if (gpu)
+            while (g0 + 1 < starts.size() && links[starts[g0]].level == 0) g0++;
+        if (gpu && ep0 >= 0) {
+            std::vector<int32_t> sel0((size_t)b * (DEG + 1));
+            for (int64_t u = 0; u < b; u++) std::memcpy(sel0.data() + u * (DEG + 1), sel[u].data(), sizeof(int32_t) * (DEG + 1));
+            std::vector<int32_t> tg(g0), st(g0 + 1), src(starts[g0]);
+            for (size_t gi = 0; gi < g0; gi++) {
+                tg[gi] = links[starts[gi]].target;
+                st[gi] = (int32_t)starts[gi];
+            }
+            st[g0] = (int32_t)starts[g0];
+            for (size_t i = 0; i < starts[g0]; i++) src[i] = links[i].src;
+            lc_status rs = build_gpu_link0(ix, ncur, b, sel0.data(), tg.data(), st.data(), (int64_t)g0, src.data());
+            if (rs != LC_OK) { build_gpu_end(ix); return rs; }
+        }
+        parallel_for((int64_t)(starts.size() - 1 - g0), nt, 64, [&](int64_t a, int64_t e, int) {
+            for (int64_t gi = a + (int64_t)g0; gi < e + (int64_t)g0; gi++)
                 for (size_t i = starts[gi]; i < starts[gi + 1]; i++)
                     add_link(g, links[i].level, links[i].target, links[i].src);
         });
         if (gpu) {
-            // re-send every row the batch wrote: the members' own rows and the link targets'
-            std::vector<int32_t> rows0;
+            // re-send the upper rows the batch wrote (level 0 was written on the device)
             std::vector<int64_t> rowsu;
             for (int64_t u = 0; u < b; u++) {
                 int64_t x = ncur + u;
-                rows0.push_back((int32_t)x);
                 for (int l = 1; l <= std::min((int)ix->levels[x], ml0); l++) rowsu.push_back(ix->upper_off[x] + l - 1);
             }
-            for (size_t gi = 0; gi + 1 < starts.size(); gi++) {
+            for (size_t gi = g0; gi + 1 < starts.size(); gi++) {
                 const Link &lk = links[starts[gi]];
-                if (lk.level == 0) rows0.push_back(lk.target);
-                else rowsu.push_back(ix->upper_off[lk.target] + lk.level - 1);
+                rowsu.push_back(ix->upper_off[lk.target] + lk.level - 1);
             }
-            lc_status rs = build_gpu_rows(ix, rows0.data(), (int64_t)rows0.size(), rowsu.data(), (int64_t)rowsu.size());
+            lc_status rs = build_gpu_rows(ix, nullptr, 0, rowsu.data(), (int64_t)rowsu.size());
             if (rs != LC_OK) { build_gpu_end(ix); return rs; }
         }
         for (int64_t u = 0; u < b; u++) {

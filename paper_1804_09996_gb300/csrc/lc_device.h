@@ -49,7 +49,11 @@ struct DeviceIndex {
     int32_t *b_rows = nullptr; size_t b_rows_cap = 0;
     int64_t *b_idx = nullptr; size_t b_idx_cap = 0;
     int32_t *b_sel = nullptr; size_t b_sel_cap = 0;
+    struct LinkDev *lk = nullptr;  // level-0 linking of the GPU-assisted build (lc_build_gpu.cu)
 };
+
+// Frees the level-0 linking state of the GPU-assisted build (no-op without one).
+void link0_free(DeviceIndex *dv);
 
 // Launch configuration of one search and the scratch it needs.
 struct SearchPlan {

@@ -86,6 +86,16 @@ lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, in
 // Re-sends level-0 rows of nodes0 [n0] and upper rows (indexes into upper_adj) rows_up [nu].
 lc_status build_gpu_rows(lc_index *ix, const int32_t *nodes0, int64_t n0, const int64_t *rows_up, int64_t nu);
 void build_gpu_end(lc_index *ix);
+// Level-0 linking of a batch on the device (lc_build_gpu.cu).  link0_begin uploads the decoded
+// vectors (ix->xh) and the level-0 row distances (ix->adj0_d) of the whole index.  link0 takes
+// the level-0 selections of the batch's members first .. first + b - 1 (sel0 [b][DEG + 1]:
+// ids, then count) and the batch's level-0 back-links grouped by target (targets [G], group
+// g's sources src[starts[g] .. starts[g + 1]) in increasing id), writes the members' own rows
+// and applies the back-links on the device copy exactly as the host build does, then copies
+// every row it wrote back into ix->adj0 and ix->adj0_d.
+lc_status build_gpu_link0_begin(lc_index *ix);
+lc_status build_gpu_link0(lc_index *ix, int64_t first, int64_t b, const int32_t *sel0, const int32_t *targets,
+                          const int32_t *starts, int64_t G, const int32_t *src);
 // Codeword assignment of vectors [first, first + n) (rotated xr [n][d], host) on the device,
 // after the graph is final; writes ix->beta exactly as the host assignment would.
 lc_status build_gpu_assign(lc_index *ix, const float *xr, int64_t first, int64_t n);

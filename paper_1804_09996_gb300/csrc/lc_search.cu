@@ -43,6 +43,7 @@ void device_free(DeviceIndex *dv)
     cfree(dv->yq); cfree(dv->shortlist); cfree(dv->spill); cfree(dv->ord); cfree(dv->status); cfree(dv->counter);
     cfree(dv->tab);
     cfree(dv->b_yq); cfree(dv->b_ids); cfree(dv->b_d); cfree(dv->b_rows); cfree(dv->b_idx); cfree(dv->b_sel);
+    link0_free(dv);
     cfree(dv->q_st); cfree(dv->ef_st); cfree(dv->ids_st); cfree(dv->d_st); cfree(dv->s_st);
     for (auto &e : dv->ev) if (e) cudaEventDestroy(e);
     if (cur >= 0) cudaSetDevice(cur);
@@ -1870,6 +1871,7 @@ void build_gpu_end(lc_index *ix)
         dv->b_yq = nullptr; dv->b_ids = nullptr; dv->b_d = nullptr; dv->b_rows = nullptr; dv->b_idx = nullptr;
         dv->b_sel = nullptr;
         dv->b_yq_cap = dv->b_ids_cap = dv->b_d_cap = dv->b_rows_cap = dv->b_idx_cap = dv->b_sel_cap = 0;
+        link0_free(dv);
     }
     ix->dev_dirty = true;                       // codewords are assigned after the graph
 }

@@ -1,7 +1,8 @@
 """GPU-assisted build (lc_params.build_gpu): lc_add encodes on the device, runs the level-0
 insertion searches and neighbour selections of each batch on the device (the batch searches the
-graph as it stood at its start, Section 5.1), keeps back-links on the host, and assigns the
-codewords on the device.  The FP32 device distances may order
+graph as it stood at its start, Section 5.1), writes the members' level-0 rows and applies the
+level-0 back-links on the device (the upper levels stay on the host), and assigns the codewords
+on the device.  The FP32 device distances may order
 near-equal candidates differently from the host build, so the graphs are not bit-identical;
 the checks are the structural invariants of the host build's graph, search quality equal to
 the host build's, and search parity against the oracle on the device-built index."""
