@@ -581,6 +581,32 @@ static void add_link(Graph &g, int l, int32_t owner, int32_t x)
 
 }  // namespace
 
+// A back-link of an insertion batch: level, the node whose row receives it, the new node.
+struct Link { int32_t level, target, src; };
+
+// Orders the links by (level, target), keeping the order of equal keys (the batch lists them
+// by increasing source): a stable least-significant-digit radix sort on 11-bit digits of
+// (level << 32 | target).
+static void sort_links(std::vector<Link> &links)
+{
+    const size_t n = links.size();
+    if (n < 2) return;
+    uint64_t top = 0;
+    for (const Link &l : links) top = std::max(top, ((uint64_t)l.level << 32) | (uint32_t)l.target);
+    std::vector<Link> tmp(n);
+    constexpr int BITS = 11, NB = 1 << BITS;
+    for (int shift = 0; shift < 64 && (top >> shift) != 0; shift += BITS) {
+        size_t cnt[NB + 1] = {};
+        auto digit = [&](const Link &l) {
+            return (size_t)(((((uint64_t)l.level << 32) | (uint32_t)l.target) >> shift) & (NB - 1));
+        };
+        for (const Link &l : links) cnt[digit(l) + 1]++;
+        for (int i = 0; i < NB; i++) cnt[i + 1] += cnt[i];
+        for (const Link &l : links) tmp[cnt[digit(l)]++] = l;
+        links.swap(tmp);
+    }
+}
+
 static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int64_t count, int nt)
 {
     const lc_params &p = ix->p;
@@ -619,7 +645,8 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
             for (int64_t i = 0; i < m; i++)
                 std::memcpy(gxr.data() + i * p.d, xr + (ncur + gmem[i] - first) * p.d, sizeof(float) * p.d);
             gsel.resize((size_t)m * (DEG + 1));
-            lc_status rs = build_gpu_search(ix, gxr.data(), m, efc, ep0, ml0, nullptr, nullptr, gsel.data());
+            // queued on the device; the host searches of the higher-level members run meanwhile
+            lc_status rs = build_gpu_select_start(ix, gxr.data(), m, efc, ep0, ml0);
             if (rs != LC_OK) { build_gpu_end(ix); return rs; }
         }
         parallel_for(b, nt, 8, [&](int64_t a, int64_t e, int t) {
@@ -631,11 +658,7 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
                 int top = std::min(Lx, ml0);
                 sel[u].assign((size_t)(top + 1) * (DEG + 1), -1);
                 if (ep0 < 0) continue;
-                if (gslot[u] >= 0) {
-                    // level 0 searched and its neighbours selected on the device
-                    std::memcpy(sel[u].data(), gsel.data() + (size_t)gslot[u] * (DEG + 1), sizeof(int32_t) * (DEG + 1));
-                    continue;
-                }
+                if (gslot[u] >= 0) continue;       // level 0 searched and selected on the device
                 int32_t cur = ep0;
                 float dcur = l2f(xv, g.xh + (int64_t)cur * p.d, p.d);
                 for (int l = ml0; l > Lx; l--) {
@@ -658,6 +681,13 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
                 }
             }
         });
+        if (gpu && ep0 >= 0) {
+            lc_status rs = build_gpu_select_finish(ix, (int64_t)gmem.size(), gsel.data());
+            if (rs != LC_OK) { build_gpu_end(ix); return rs; }
+            for (int64_t u = 0; u < b; u++)
+                if (gslot[u] >= 0)
+                    std::memcpy(sel[u].data(), gsel.data() + (size_t)gslot[u] * (DEG + 1), sizeof(int32_t) * (DEG + 1));
+        }
         // the new nodes' own rows, sorted by decoded-to-decoded distance (level 0 on the
         // device in the GPU-assisted build)
         const int l_own = gpu ? 1 : 0;
@@ -678,7 +708,6 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
             }
         });
         // back-links, grouped by (level, target); within a group in id order of the source
-        struct Link { int32_t level, target, src; };
         std::vector<Link> links;
         for (int64_t u = 0; u < b; u++) {
             int64_t x = ncur + u;
@@ -688,9 +717,7 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
                 for (int i = 0; i < s[DEG]; i++) links.push_back({l, s[i], (int32_t)x});
             }
         }
-        std::stable_sort(links.begin(), links.end(), [](const Link &a, const Link &c) {
-            return a.level < c.level || (a.level == c.level && a.target < c.target);
-        });
+        sort_links(links);
         std::vector<size_t> starts;
         for (size_t i = 0; i < links.size(); i++)
             if (i == 0 || links[i].level != links[i - 1].level || links[i].target != links[i - 1].target)
@@ -739,7 +766,11 @@ static lc_status insert_range(lc_index *ix, const float *xr, int64_t first, int6
         }
         done += b;
     }
-    if (gpu) build_gpu_end(ix);
+    if (gpu) {
+        lc_status rs = build_gpu_link0_end(ix);
+        build_gpu_end(ix);
+        if (rs != LC_OK) return rs;
+    }
     return LC_OK;
 }
 

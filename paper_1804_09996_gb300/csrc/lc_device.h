@@ -4,6 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "lc_internal.h"
 
 namespace lc {
@@ -54,6 +57,34 @@ struct DeviceIndex {
 
 // Frees the level-0 linking state of the GPU-assisted build (no-op without one).
 void link0_free(DeviceIndex *dv);
+
+inline void cfree(void *p) { if (p) cudaFree(p); }
+
+// dst = a fresh device copy of src (at least 16 bytes allocated)
+template <class T>
+inline bool dupload(T *&dst, const std::vector<T> &src)
+{
+    cfree(dst);
+    dst = nullptr;
+    size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
+    if (cudaMalloc(&dst, bytes) != cudaSuccess) return false;
+    if (!src.empty() && cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+        return false;
+    return true;
+}
+
+// p holds at least need elements (reallocated, contents dropped, when it is smaller)
+template <class T>
+inline bool grow(T *&p, size_t &cap, size_t need)
+{
+    if (need <= cap && p) return true;
+    cfree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, std::max<size_t>(need, 1) * sizeof(T)) != cudaSuccess) return false;
+    cap = need;
+    return true;
+}
 
 // Launch configuration of one search and the scratch it needs.
 struct SearchPlan {

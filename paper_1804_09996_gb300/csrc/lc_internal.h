@@ -75,14 +75,15 @@ lc_status profile_phases(lc_index *ix, float *rotate_ms, float *descent_ms, floa
 // Autotuner (lc_tune.cpp).
 lc_status autotune(lc_index *ix, const float *q, int64_t n, const int32_t *gt, const lc_tune_params *tp,
                    lc_tune_result *out);
-// GPU-assisted build (lc_search.cu): the device copy of the index under construction serves
+// GPU-assisted build (lc_build_gpu.cu): the device copy of the index under construction serves
 // the level-0 insertion searches of each batch; rows changed by a batch are re-sent.
 lc_status build_gpu_begin(lc_index *ix);
 // m rotated vectors xr [m][d] (host) search level 0 from ep after a greedy descent of levels
-// max_level..1, keeping efc: ids/dists [m][efc] (host, sorted by (distance, id), -1 padded);
-// or, with sel non-NULL, the neighbour selection of each: sel [m][DEG + 1] (ids, then count).
-lc_status build_gpu_search(lc_index *ix, const float *xr, int64_t m, int efc, int32_t ep, int max_level,
-                           int32_t *ids, float *dists, int32_t *sel = nullptr);
+// max_level..1, keeping efc, and their neighbours are selected: select_start queues the work
+// (the host may work meanwhile), select_finish waits and writes sel [m][DEG + 1] (host: ids,
+// then count).  Needs build_gpu_link0_begin.
+lc_status build_gpu_select_start(lc_index *ix, const float *xr, int64_t m, int efc, int32_t ep, int max_level);
+lc_status build_gpu_select_finish(lc_index *ix, int64_t m, int32_t *sel);
 // Re-sends level-0 rows of nodes0 [n0] and upper rows (indexes into upper_adj) rows_up [nu].
 lc_status build_gpu_rows(lc_index *ix, const int32_t *nodes0, int64_t n0, const int64_t *rows_up, int64_t nu);
 void build_gpu_end(lc_index *ix);
@@ -92,10 +93,12 @@ void build_gpu_end(lc_index *ix);
 // ids, then count) and the batch's level-0 back-links grouped by target (targets [G], group
 // g's sources src[starts[g] .. starts[g + 1]) in increasing id), writes the members' own rows
 // and applies the back-links on the device copy exactly as the host build does, then copies
-// every row it wrote back into ix->adj0 and ix->adj0_d.
+// the ids of every row it wrote back into ix->adj0; link0_end copies the level-0 row distances
+// back into ix->adj0_d.
 lc_status build_gpu_link0_begin(lc_index *ix);
 lc_status build_gpu_link0(lc_index *ix, int64_t first, int64_t b, const int32_t *sel0, const int32_t *targets,
                           const int32_t *starts, int64_t G, const int32_t *src);
+lc_status build_gpu_link0_end(lc_index *ix);
 // Codeword assignment of vectors [first, first + n) (rotated xr [n][d], host) on the device,
 // after the graph is final; writes ix->beta exactly as the host assignment would.
 lc_status build_gpu_assign(lc_index *ix, const float *xr, int64_t first, int64_t n);
