@@ -17,7 +17,8 @@
 //    squares); codeword 0 is e0 = (1, 0, ..., 0) and is never updated, so no vector is
 //    refined worse than q(x).  Trained on a seeded subset of at most 250k vectors.
 //
-// This is the build side of the library; the search path runs on the GPU (lc_search.cu).
+// This is the build side of the library; the search path runs on the GPU (lc_search.cu), and
+// with build_gpu = 1 the level-0 insertions of each batch do too (lc_build_gpu.cu).
 #include <algorithm>
 #include <atomic>
 #include <cmath>

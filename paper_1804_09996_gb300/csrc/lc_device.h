@@ -1,5 +1,6 @@
 // Host-side view of the device index and of one search's launch plan and scratch, shared by
-// the search (lc_search.cu) and the request server (lc_serve.cpp).  Not part of the ABI.
+// the search (lc_search.cu), the GPU-assisted build (lc_build_gpu.cu) and the request server
+// (lc_serve.cpp).  Not part of the ABI.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -2,6 +2,8 @@
 // host side of a search and the kernels other than the walk (which is in lc_walk.cuh).
 //
 // rotate_kernel  y' = R y for a batch of queries (OPQ rotation, Section 3.3 / 5.1).
+// table_kernel   per-query ADC tables on the tensor cores (the LC_LUT_TABLE form, Section 4.1).
+// order_kernel   queue order of an ordered search (decreasing distance to the level-0 entry).
 // walk           lc_walk.cuh / lc_walk_f32.cu / lc_walk_f16.cu: upper-level descent and level-0
 //                search (Section 2) scored by ADC on the level-1 code (Section 4.1).
 // refine_kernel  (one warp per query) for each shortlisted x: G(x) = [q(x), q(g_1..g_8)]
@@ -10,9 +12,8 @@
 //                y', and the final top-k by (distance, id).
 // merge_kernel   top-k merge of per-shard results (sharded search).
 // Host side      device copy of the index (upload), launch planning (plan_search), one search
-//                (run_search / search), captured plans (lc_plan_*), the GPU-assisted build
-//                (encoding, insertion searches and neighbour selection, row re-sends, codeword
-//                assignment), the walk without allocation, and kernel timing.
+//                (run_search / search), captured plans (lc_plan_*), the walk without
+//                allocation, and kernel timing.  The GPU-assisted build is in lc_build_gpu.cu.
 //
 // Ordering everywhere is by (distance, id), smaller id first on equal distances.
 
