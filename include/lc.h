@@ -280,7 +280,7 @@ lc_status lc_merge_topk(const int32_t *ids, const float *dists, int S, int64_t n
  * arrival order; whenever one of the max_inflight launch slots is free, the oldest waiting
  * request starts together with every later waiting request of the same parameters up to
  * efSearch (same k, shortlist, mode, beam, codebook precision, caps and table sizes, and
- * max(ef, k) in the same power-of-two class), up to 8,192 queries (or max_request): their
+ * max(ef, k) in the same power-of-two class), up to 16,384 queries (or max_request): their
  * queries run as one launch in which each query walks with its own request's efSearch.  Under
  * light load a request starts alone as soon as it arrives and overlaps with those already on
  * the GPU; under heavy load the requests that queued while the slots were busy run as a few

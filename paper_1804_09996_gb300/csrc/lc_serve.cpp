@@ -27,7 +27,11 @@
 
 namespace {
 
-constexpr int MERGE_QUERIES = 8192;     // largest merged launch (queries), unless max_request is larger
+// Largest merged launch (queries), unless max_request is larger.  Measured at saturation (512-query
+// requests, 4 launch slots, up to 96 outstanding): 8,192 / 16,384 / 32,768 gave 12.7 / 13.4 /
+// 10.5M queries/s on the 1M workload and 9.0 / 9.5 / 8.2M on the 10M one (the largest cap
+// leaves too few requests queued behind a launch to keep the slots busy).
+constexpr int MERGE_QUERIES = 16384;
 
 struct Req {
     uint64_t id = 0;
