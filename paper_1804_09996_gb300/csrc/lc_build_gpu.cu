@@ -166,10 +166,13 @@ lc_status build_gpu_select_start(lc_index *ix, const float *xr, int64_t m, int e
     sp.shortlist = -1;                          // the walk's own result list, sorted
     sp.walk_full = 1;
     SearchPlan P;
-    lc_status rs = plan_search(dv, m, &sp, &P);
+    // an ordered search (longest walks first) once the batch fills the GPU twice; results do not
+    // depend on the order
+    lc_status rs = plan_search(dv, m, &sp, &P, true);
     if (rs != LC_OK) return rs;
     if (!grow(dv->b_yq, dv->b_yq_cap, (size_t)m * dv->d) || !grow(dv->b_ids, dv->b_ids_cap, (size_t)m * efc) ||
-        !grow(dv->b_d, dv->b_d_cap, (size_t)m * efc) || !grow(dv->spill, dv->spill_cap, P.spill_elems)) {
+        !grow(dv->b_d, dv->b_d_cap, (size_t)m * efc) || !grow(dv->spill, dv->spill_cap, P.spill_elems) ||
+        (P.ordered && !grow(dv->ord, dv->ord_cap, P.ord_elems))) {
         set_error("cudaMalloc failed for the build's search buffers");
         return LC_ERR_OOM;
     }
@@ -182,6 +185,7 @@ lc_status build_gpu_select_start(lc_index *ix, const float *xr, int64_t m, int e
     SearchScratch sc;
     sc.yq = dv->b_yq;
     sc.spill = dv->spill;
+    sc.ord = dv->ord;
     sc.status = dv->status;
     sc.counter = dv->counter;
     rs = run_search(dv, P, nullptr, m, dv->b_ids, dv->b_d, nullptr, sc, 0, false, nullptr, nullptr, true);
