@@ -23,6 +23,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <queue>
 #include <thread>
 #include <utility>
@@ -133,9 +134,13 @@ static inline float l2f(const float *a, const float *b, int d)
 // ties go to the lowest centre index; an empty cluster is re-seeded with the point of the
 // largest cluster furthest from its centre.  Points are rows of X at the given stride,
 // coordinates [0, dim).
+// dev, when given, runs the assignment step elsewhere (the device) with the same arithmetic:
+// dev(C, cn, as, dm) fills as / dm for centres C [K][dim] with squared norms cn, or returns
+// false (the step then runs here).
 template <class T>
 static void kmeans(const T *X, int64_t n, int64_t stride, int dim, int K, int iters,
-                   uint64_t seed, T *C, bool have_init, int nt)
+                   uint64_t seed, T *C, bool have_init, int nt,
+                   const std::function<bool(const T *, const T *, int32_t *, double *)> &dev = nullptr)
 {
     if (!have_init) {
         if (n >= K) {
@@ -163,6 +168,7 @@ static void kmeans(const T *X, int64_t n, int64_t stride, int dim, int K, int it
             }
             cn[c] = s;
         }
+        if (!(dev && dev(C, cn.data(), as.data(), dm.data())))
         parallel_for(n, nt, 2048, [&](int64_t a, int64_t b, int) {
             std::vector<T> acc(K);
             for (int64_t i = a; i < b; i++) {
@@ -882,7 +888,7 @@ static int argmin_codeword(const NormalEq &ne, const double *Bd, int K)
 // beta_K > 1: k-means of the per-vector least-squares weights initialises codewords
 // 1..K-1 (codeword 0 stays e0), then EM alternates argmin assignment and per-cluster least
 // squares.  beta_K = 1: the shared least-squares weights beta* of Section 4.2 per block.
-static void train_codebook(lc_index *ix, const float *xr, int64_t first, int64_t count, int nt)
+static lc_status train_codebook(lc_index *ix, const float *xr, int64_t first, int64_t count, int nt)
 {
     const lc_params &p = ix->p;
     const int bM = p.beta_M, bK = p.beta_K;
@@ -914,12 +920,45 @@ static void train_codebook(lc_index *ix, const float *xr, int64_t first, int64_t
         }
         for (int c = 0; c < bK; c++) Bd[(size_t)c * 9] = 1.0;          // e0 everywhere to start
         int K = (int)std::min<int64_t>(bK - 1, ns);
-        if (K > 0) kmeans<double>(per.data(), ns, 9, 9, K, 25, p.seed + 31 + 101 * (uint64_t)m, Bd + 9, false, nt);
+        // GPU-assisted build: the assignment steps of the k-means and of the EM on the device
+        // (the same arithmetic; the sums stay here, in the same order)
+        EmDev *em = nullptr;
+        if (p.build_gpu) {
+            std::vector<double> ne55((size_t)ns * 55);
+            for (int64_t s = 0; s < ns; s++) {
+                std::memcpy(ne55.data() + s * 55, ne[s].A, sizeof(double) * 45);
+                std::memcpy(ne55.data() + s * 55 + 45, ne[s].b, sizeof(double) * 9);
+                ne55[s * 55 + 54] = ne[s].xx;
+            }
+            em = em_begin(per.data(), ns, 9, ne55.data());
+            if (!em) {
+                set_error("device memory for the regression-codebook training failed: %s",
+                          cudaGetErrorString(cudaGetLastError()));
+                return LC_ERR_CUDA;
+            }
+        }
+        bool dev_ok = true;
+        std::function<bool(const double *, const double *, int32_t *, double *)> dev_nearest;
+        if (em)
+            dev_nearest = [&](const double *C, const double *cn, int32_t *a, double *dmv) {
+                return dev_ok = dev_ok && em_nearest(em, C, cn, K, a, dmv);
+            };
+        if (K > 0)
+            kmeans<double>(per.data(), ns, 9, 9, K, 25, p.seed + 31 + 101 * (uint64_t)m, Bd + 9, false, nt, dev_nearest);
         std::vector<int32_t> as(ns);
         for (int it = 0; it < p.beta_iters; it++) {
-            parallel_for(ns, nt, 2048, [&](int64_t a, int64_t b, int) {
-                for (int64_t s = a; s < b; s++) as[s] = argmin_codeword(ne[s], Bd, bK);
-            });
+            if (em) {
+                dev_ok = dev_ok && em_assign(em, Bd, bK, as.data());
+            } else {
+                parallel_for(ns, nt, 2048, [&](int64_t a, int64_t b, int) {
+                    for (int64_t s = a; s < b; s++) as[s] = argmin_codeword(ne[s], Bd, bK);
+                });
+            }
+            if (!dev_ok) {
+                em_free(em);
+                set_error("regression-codebook training on the device failed");
+                return LC_ERR_CUDA;
+            }
             std::vector<double> SA((size_t)bK * 45, 0.0), Sb((size_t)bK * 9, 0.0);
             std::vector<int64_t> cnt(bK, 0);
             for (int64_t s = 0; s < ns; s++) {
@@ -931,10 +970,16 @@ static void train_codebook(lc_index *ix, const float *xr, int64_t first, int64_t
             for (int c = 1; c < bK; c++)
                 if (cnt[c] > 0) ridge_solve(SA.data() + (size_t)c * 45, Sb.data() + (size_t)c * 9, Bd + (size_t)c * 9);
         }
+        em_free(em);
+        if (!dev_ok) {
+            set_error("regression-codebook training on the device failed");
+            return LC_ERR_CUDA;
+        }
     }
     ix->B.resize(Ball.size());
     for (size_t k = 0; k < ix->B.size(); k++) ix->B[k] = (float)Ball[k];
     ix->has_codebook = true;
+    return LC_OK;
 }
 
 // Each vector's codeword per block: argmin of the block's loss under the index's codebooks.
@@ -1036,7 +1081,10 @@ lc_status build_add(lc_index *ix, const float *x, int64_t n)
     ix->n = total;
     lc_status rs = insert_range(ix, xr.data(), first, n, nt);
     if (rs != LC_OK) return rs;
-    if (!ix->has_codebook) train_codebook(ix, xr.data(), first, n, nt);
+    if (!ix->has_codebook) {
+        rs = train_codebook(ix, xr.data(), first, n, nt);
+        if (rs != LC_OK) return rs;
+    }
     if (p.build_gpu) {
         rs = build_gpu_assign(ix, xr.data(), first, n);
         if (rs != LC_OK) return rs;

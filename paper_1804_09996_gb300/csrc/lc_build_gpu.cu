@@ -789,4 +789,143 @@ lc_status build_gpu_link0_end(lc_index *ix)
     return LC_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Regression-codebook training (Section 4.3) on the device: the assignment steps of the
+// k-means that initialises the codewords and of the EM that refines them, each in the host
+// build's double arithmetic (every product and sum rounded on its own, in the host's order,
+// first minimum), so the assignments, and with the host's sums the codebook, are the host's.
+
+struct EmDev {
+    int device = -1;
+    int64_t n = 0;
+    int dim = 0;
+    double *X = nullptr;           // [n][dim] points of the k-means
+    double *ne = nullptr;          // [n][55] normal equations: A (45, packed upper triangle), b (9), xx
+    double *C = nullptr;           // [K][dim] centres, or [K][9] codewords
+    double *cn = nullptr;          // [K] squared centre norms
+    size_t c_cap = 0, cn_cap = 0;
+    int32_t *as = nullptr;         // [n]
+    double *dm = nullptr;          // [n]
+};
+
+// as[i] = argmin_c cn[c] + sum_t (-2 x_t) C[c][t] (t in order, first minimum); dm[i] = the
+// squared distance to that centre, sum over t in order.
+__global__ void em_nearest_kernel(const double *X, int64_t n, int dim, const double *C, const double *cn, int K,
+                                  int32_t *as, double *dm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *x = X + i * dim;
+    double m2x[16];
+    for (int t = 0; t < dim; t++) m2x[t] = __dmul_rn(-2.0, __ldg(x + t));
+    int best = 0;
+    double bv = 0.0;
+    for (int c = 0; c < K; c++) {
+        double acc = __ldg(cn + c);
+        for (int t = 0; t < dim; t++) acc = __dadd_rn(acc, __dmul_rn(m2x[t], __ldg(C + (int64_t)c * dim + t)));
+        if (c == 0 || acc < bv) { bv = acc; best = c; }
+    }
+    double s = 0.0;
+    for (int t = 0; t < dim; t++) {
+        const double df = __dsub_rn(__ldg(x + t), __ldg(C + (int64_t)best * dim + t));
+        s = __dadd_rn(s, __dmul_rn(df, df));
+    }
+    as[i] = best;
+    dm[i] = s;
+}
+
+// as[s] = argmin_c ||x - beta_c^T G||^2 = xx - 2 beta.b + beta^T A beta over codewords
+// B [K][9], accumulated in the host's order (first minimum).
+__global__ void em_assign_kernel(const double *ne, int64_t n, const double *B, int K, int32_t *as)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double *e = ne + s * 55;
+    int best = 0;
+    double bl = __longlong_as_double(0x7ff0000000000000ll);               // +inf
+    for (int c = 0; c < K; c++) {
+        const double *be = B + (int64_t)c * 9;
+        double l = __ldg(e + 54);
+        int u = 0;
+        for (int p = 0; p < 9; p++) {
+            const double bp = __ldg(be + p);
+            l = __dsub_rn(l, __dmul_rn(__dmul_rn(2.0, bp), __ldg(e + 45 + p)));
+            l = __dadd_rn(l, __dmul_rn(__dmul_rn(bp, bp), __ldg(e + u)));
+            u++;
+            for (int q = p + 1; q < 9; q++, u++)
+                l = __dadd_rn(l, __dmul_rn(__dmul_rn(__dmul_rn(2.0, bp), __ldg(be + q)), __ldg(e + u)));
+        }
+        if (l < bl) { bl = l; best = c; }
+    }
+    as[s] = best;
+}
+
+void em_free(EmDev *em)
+{
+    if (!em) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (em->device >= 0) cudaSetDevice(em->device);
+    cfree(em->X); cfree(em->ne); cfree(em->C); cfree(em->cn); cfree(em->as); cfree(em->dm);
+    if (cur >= 0) cudaSetDevice(cur);
+    delete em;
+}
+
+EmDev *em_begin(const double *X, int64_t n, int dim, const double *ne55)
+{
+    if (n <= 0 || dim > 16) return nullptr;
+    EmDev *em = new EmDev();
+    if (cudaGetDevice(&em->device) != cudaSuccess) { cudaGetLastError(); delete em; return nullptr; }
+    em->n = n;
+    em->dim = dim;
+    bool ok = cudaMalloc(&em->X, sizeof(double) * (size_t)n * dim) == cudaSuccess &&
+              cudaMalloc(&em->ne, sizeof(double) * (size_t)n * 55) == cudaSuccess &&
+              cudaMalloc(&em->as, sizeof(int32_t) * (size_t)n) == cudaSuccess &&
+              cudaMalloc(&em->dm, sizeof(double) * (size_t)n) == cudaSuccess &&
+              cudaMemcpy(em->X, X, sizeof(double) * (size_t)n * dim, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(em->ne, ne55, sizeof(double) * (size_t)n * 55, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        em_free(em);
+        return nullptr;
+    }
+    return em;
+}
+
+bool em_nearest(EmDev *em, const double *C, const double *cn, int K, int32_t *as, double *dm)
+{
+    if (!em || K < 1) return false;
+    if (!grow(em->C, em->c_cap, (size_t)K * em->dim) || !grow(em->cn, em->cn_cap, (size_t)K) ||
+        cudaMemcpy(em->C, C, sizeof(double) * (size_t)K * em->dim, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(em->cn, cn, sizeof(double) * (size_t)K, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    em_nearest_kernel<<<(unsigned)((em->n + 127) / 128), 128>>>(em->X, em->n, em->dim, em->C, em->cn, K, em->as, em->dm);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(as, em->as, sizeof(int32_t) * (size_t)em->n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(dm, em->dm, sizeof(double) * (size_t)em->n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+bool em_assign(EmDev *em, const double *B, int K, int32_t *as)
+{
+    if (!em || K < 1) return false;
+    if (!grow(em->C, em->c_cap, (size_t)K * 9) ||
+        cudaMemcpy(em->C, B, sizeof(double) * (size_t)K * 9, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    em_assign_kernel<<<(unsigned)((em->n + 127) / 128), 128>>>(em->ne, em->n, em->C, K, em->as);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpy(as, em->as, sizeof(int32_t) * (size_t)em->n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 }  // namespace lc

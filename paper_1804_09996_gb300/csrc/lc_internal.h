@@ -102,6 +102,16 @@ lc_status build_gpu_link0_end(lc_index *ix);
 // Codeword assignment of vectors [first, first + n) (rotated xr [n][d], host) on the device,
 // after the graph is final; writes ix->beta exactly as the host assignment would.
 lc_status build_gpu_assign(lc_index *ix, const float *xr, int64_t first, int64_t n);
+// Regression-codebook training on the device (lc_build_gpu.cu), in the host build's double
+// arithmetic.  em_begin uploads the k-means points X [n][dim] (dim <= 16) and the samples'
+// normal equations ne55 [n][55] (A packed upper triangle 45, b 9, ||x||^2); em_nearest writes
+// each point's nearest centre of C [K][dim] (cn [K]: squared norms) and its squared distance;
+// em_assign writes each sample's argmin codeword of B [K][9].  NULL / false on a CUDA failure.
+struct EmDev;
+EmDev *em_begin(const double *X, int64_t n, int dim, const double *ne55);
+bool em_nearest(EmDev *em, const double *C, const double *cn, int K, int32_t *as, double *dm);
+bool em_assign(EmDev *em, const double *B, int K, int32_t *as);
+void em_free(EmDev *em);
 // Rotation and two-level encoding of x [n][d] (host) on the device, with the host build's
 // arithmetic: xr [n][d], codes c1 [n][M1], c2 [n][M2] (host).
 lc_status build_gpu_encode(lc_index *ix, const float *x, int64_t n, float *xr, uint8_t *c1, uint8_t *c2);

@@ -1,8 +1,8 @@
 """GPU-assisted build (lc_params.build_gpu): lc_add encodes on the device, runs the level-0
 insertion searches and neighbour selections of each batch on the device (the batch searches the
 graph as it stood at its start, Section 5.1), writes the members' level-0 rows and applies the
-level-0 back-links on the device (the upper levels stay on the host), and assigns the codewords
-on the device.  The FP32 device distances may order
+level-0 back-links on the device (the upper levels stay on the host), runs the assignment steps
+of the regression-codebook training on the device, and assigns the codewords on the device.  The FP32 device distances may order
 near-equal candidates differently from the host build, so the graphs are not bit-identical;
 the checks are the structural invariants of the host build's graph, search quality equal to
 the host build's, and search parity against the oracle on the device-built index."""
@@ -88,6 +88,10 @@ def test_device_codeword_assignment_is_the_hosts(builds):
     hg, ixg, _ = builds[1]
     hh, ixh, _ = builds[0]
     assert np.array_equal(ixg.B, ixh.B) or not np.array_equal(ixg.adj0, ixh.adj0)
+    if np.array_equal(ixg.adj0, ixh.adj0):
+        # the same graph: the codebook trained with the device's k-means and EM assignments, and
+        # every codeword, are the host's
+        assert np.array_equal(ixg.B, ixh.B) and np.array_equal(ixg.beta, ixh.beta)
     same_g = (ixg.adj0[:, :8] == ixh.adj0[:, :8]).all(1)
     assert same_g.mean() > 0.3
     if np.array_equal(ixg.B, ixh.B):
@@ -111,6 +115,8 @@ def test_device_assignment_product_codebook(bM, bK):
         finally:
             lc.lc_free(h)
     same_g = (out[0]["adj0"][:, :8] == out[1]["adj0"][:, :8]).all(1)
+    if np.array_equal(out[0]["adj0"], out[1]["adj0"]):
+        assert np.array_equal(out[0]["B"], out[1]["B"]) and np.array_equal(out[0]["beta"], out[1]["beta"])
     if np.array_equal(out[0]["B"], out[1]["B"]):
         assert np.array_equal(out[0]["beta"][same_g], out[1]["beta"][same_g])
     # and every device choice is the blockwise argmin under the device build's own codebooks
