@@ -436,9 +436,9 @@ def level0_bytes(st, row, d, k, ordered, qbytes=None):
 def measure_large(args, dev, flush, stream):
     """The walk on an index far larger than L2 (the 1M headline's index is largely L2-resident,
     so its DRAM traffic is a third of its algorithmic bytes): the --large workload built by the
-    GPU-assisted build, --large-queries queries per step.  The plain FP32 walk at --ef sets the
-    1-recall@1 target; the batched form with the FP16 codebook is swept over efSearch for the
-    cheapest level reaching it.  Same timing rules as the headline (L2 flushed before every
+    GPU-assisted build, --large-queries queries per step.  The plain FP32 walk at --large-ef
+    (128, the 10M and 50M configurations' setting) sets the 1-recall@1 target; the batched form
+    with the FP16 codebook is swept over efSearch for the cheapest level reaching it.  Same timing rules as the headline (L2 flushed before every
     step, CUDA events on the search stream, clocks sampled during the timed steps)."""
     import torch
     from paper_1804_09996_gb300 import lc
@@ -480,7 +480,7 @@ def measure_large(args, dev, flush, stream):
                     stats=stats.cpu().numpy().astype(np.int64))
 
     clocks = Clocks(dev)
-    sp_p = lc.lc_default_search_params(k, args.ef)
+    sp_p = lc.lc_default_search_params(k, args.large_ef)
     plain = run(sp_p, steps)
     target = plain["recall"]
     # the batched FP16 form's efSearch is chosen on a query sample disjoint from the timed
@@ -497,7 +497,7 @@ def measure_large(args, dev, flush, stream):
         return recall_at_1(ids[:n_sel, 0].cpu().numpy(), xb, xsel, gsel_d)
 
     target_sel = sel_recall(sp_p)
-    efs = (32, 40, 48, 56, 64, 80, 96, 128)
+    efs = tuple(e for e in (32, 40, 48, 56, 64, 80, 96, 112, 128, 160, 192, 256) if e <= 2 * args.large_ef)
     sweep, li = [], 0
     for li, ef in enumerate(efs):
         sp_b = lc.lc_default_search_params(k, ef, mode=lc.LC_MODE_BATCHED, beam=args.beam, lut_prec=lc.LC_LUT_FP16)
@@ -519,7 +519,8 @@ def measure_large(args, dev, flush, stream):
     # precision, efSearch and launch shape for this index and batch size)
     xs = extra_queries(w, nq, 2000)
     gs, _ = exact_nn(xb, xs, f"cuda:{dev}")
-    tr = lc.lc_autotune(h, xs, gs.astype(np.int32), k=k, ef=args.ef, allow_fp16=True, max_beam=8, reps=3, batch=nq)
+    tr = lc.lc_autotune(h, xs, gs.astype(np.int32), k=k, ef=args.large_ef, allow_fp16=True, max_beam=8, reps=3,
+                        batch=nq)
     sp_t = lc.lc_search_params.from_buffer_copy(tr.sp)
     tuned = run(sp_t, steps)
     tune = {"beam": sp_t.beam if sp_t.mode else 1, "mode": "batched" if sp_t.mode else "plain",
@@ -561,7 +562,7 @@ def measure_large(args, dev, flush, stream):
     return {"workload": args.large, "desc": w["desc"].replace("10k queries/step", f"{nq // 1000}k queries/step"),
             "queries_per_step": nq, "recall_queries": n_gt, "recall_target": target, "steps": steps,
             "index_build": "GPU-assisted", "data_s": round(gen_s, 1), "index_build_s": round(build_s, 1),
-            "plain": summ(plain, args.ef, "plain, fp32 codebook", sp_p),
+            "plain": summ(plain, args.large_ef, "plain, fp32 codebook", sp_p),
             "headline": summ(best, best_ef, best_name, best_sp),
             "sweep": sweep, "sweep_format": "(efSearch, R@1 on a disjoint 4,000-query selection sample)",
             "selection_plain_recall_at_1": target_sel, "raised_on_timed": raised,
@@ -657,6 +658,9 @@ def main():
     ap.add_argument("--large", default="mix10m", choices=["none"] + sorted(WORKLOADS),
                     help="also measure the walk on this index (far larger than L2) at 1 GPU; none: skip")
     ap.add_argument("--large-queries", type=int, default=100_000, help="queries per step of the --large measurement")
+    ap.add_argument("--large-ef", type=int, default=128,
+                    help="efSearch of the plain walk that sets the --large measurement's recall target (128 for "
+                         "the 10M and 50M configurations, as 64 for the 1M one)")
     ap.add_argument("--mode", default="both", choices=["both", "plain", "batched"],
                     help="both: plain sets the recall target, batched is swept to reach it; "
                          "plain / batched: that form only, at --ef")
@@ -851,7 +855,7 @@ def main():
     # DRAM traffic from the committed ncu summary of the same kernel build and form, if any
     bsp = best_form[0]
     efp_b = max(bsp.ef, bsp.k)
-    auto_vlog = min(12, max(10, int(np.ceil(np.log2(32 * efp_b)))))      # the library's automatic table size
+    auto_vlog = min(11, max(10, int(np.ceil(np.log2(32 * efp_b)))))      # the library's automatic table size
     form_key = None if (bsp.warps or bsp.visited_log not in (0, auto_vlog) or (bsp.mode and bsp.beam != args.beam)) else (
         ("batched" if bsp.mode else "plain") + ("_full" if bsp.walk_full else "")
         + ("_table" if bsp.lut_prec == lc.LC_LUT_TABLE else "_fp16" if bsp.lut_prec else "")

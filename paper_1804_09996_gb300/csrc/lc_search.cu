@@ -595,6 +595,15 @@ lc_status upload(lc_index *ix)
     return LC_OK;
 }
 
+static int ilog2_ceil(int64_t x);
+
+// Automatic size (log2 entries) of the walk's shared visited table: 2^10 up to efSearch 32,
+// else 2^11.  A larger table fits fewer walks per SM, and that costs more than the global
+// spills it saves: on the 10M mixture at efSearch 96 / 128 / 256, 2^11 against 2^12 took
+// 4.5 / 6.3 / 15.2 ms against 6.5 / 8.9 / 23.1 ms (plain level-0 launch, 20k queries) and
+// 2.9 / 4.1 / 8.6 against 3.4 / 4.6 / 11.0 ms (batched beam 4, FP16 codebook).
+static int auto_visited_log(int efp) { return std::min(11, std::max(10, ilog2_ceil((int64_t)efp * 32))); }
+
 static int ilog2_ceil(int64_t x)
 {
     int l = 0;
@@ -634,7 +643,7 @@ lc_status plan_search(const DeviceIndex *dv, int64_t nq, const lc_search_params 
     }
     P.beam = sp->mode == LC_MODE_BATCHED ? sp->beam : 1;
     P.tcap = sp->max_dist;
-    P.hash_log = sp->visited_log ? sp->visited_log : std::min(12, std::max(10, ilog2_ceil((int64_t)P.efp * 32)));
+    P.hash_log = sp->visited_log ? sp->visited_log : auto_visited_log(P.efp);
     P.spill_log = sp->spill_log ? sp->spill_log : std::min(16, std::max(13, ilog2_ceil((int64_t)P.efp * 64)));
     const int efcap = (int)align_up(P.efp, 32);
     // compile-time sub-space width for the uniform splits 96/16, 96/32, 128/64
@@ -1087,7 +1096,7 @@ lc_status search_walk_noalloc(lc_index *ix, const float *q, int64_t nq, int k, i
     wa.R = k; wa.refine = 0;
     wa.beam = 1;
     // the visited tables of lc_search at this efSearch (same shared table, same spill table)
-    wa.hash_log = std::min(12, std::max(10, ilog2_ceil((int64_t)efp * 32)));
+    wa.hash_log = auto_visited_log(efp);
     wa.spill_log = std::min(16, std::max(13, ilog2_ceil((int64_t)efp * 64)));
     wa.ids_out = ids; wa.dists_out = dists; wa.stats_out = stats;
     wa.counter = reinterpret_cast<unsigned long long *>(scratch);
