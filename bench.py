@@ -382,7 +382,7 @@ def measure_serving(lc, h, xq, gt, k, args, sp_best):
             def cb_lat(rid, st, i, d):
                 fin[rid] = (time.perf_counter(), st)
 
-            # the Python driver's garbage collector runs before the point, not during it (a
+            # the Python loop's garbage collector runs before the point, not during it (a
             # full collection inside the loop stalled submissions and polls by ~35 ms)
             gc.collect()
             gc.disable()
