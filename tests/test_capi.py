@@ -166,6 +166,11 @@ def test_search_ex_argument_errors_without_gpu(mix3k):
             with pytest.raises(lc.LcError) as e:
                 lc.lc_search_ex(h, q, lc.LC_QUERY_F32, 4, sp, efq, ids, ds)
             assert e.value.status == lc.LC_ERR_ARG and "query 1" in e.value.message
+        # codebook precisions: FP32, FP16 and the table form; anything else is refused
+        for bad in (-1, lc.LC_LUT_TABLE + 1):
+            with pytest.raises(lc.LcError) as e:
+                lc.lc_search(h, q, 4, lc.lc_default_search_params(10, 64, lut_prec=bad), ids, ds)
+            assert e.value.status == lc.LC_ERR_ARG and "lut_prec" in e.value.message
     finally:
         lc.lc_free(h)
 
